@@ -1,0 +1,373 @@
+"""Pins of the FP64 oracle against facts fixed by the paper and by mathematics.
+
+Nothing here re-types an oracle formula or re-calls the library routine the oracle uses for
+the same step: each expected value comes from an independent construction (a brute-force
+DFT sum, an analytic Haar basis, a closed form, a grid search, an algebraic identity of the
+iteration).
+"""
+import numpy as np
+import pytest
+
+from oracle import lps_oracle as O
+from paper_1411_6206_gb300 import phantom as P
+
+RNG = np.random.default_rng(12345)
+
+
+def crandn(*shape, rng=RNG):
+    return rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+
+
+def rand_mask(ny, nz, frac, rng=RNG):
+    m = (rng.random((nz, ny)) < frac).astype(np.uint8)
+    m[0, 0] = 1
+    return m
+
+
+# ---------------------------------------------------------------- acquisition operator
+
+def brute_E(x, coils, mask, fft_z):
+    """d[c][l][kx] = sum_{z,x,y} C x exp(-2 pi i (kx x/nx + ky y/ny [+ kz z/nz])) / sqrt(N)."""
+    ncoil, nz, nx, ny = coils.shape
+    lines = np.argwhere(mask)          # raster order over [first][ky]
+    out = np.zeros((ncoil, len(lines), nx), complex)
+    zz, xx, yy = np.meshgrid(np.arange(nz), np.arange(nx), np.arange(ny), indexing="ij")
+    for c in range(ncoil):
+        img = coils[c] * x
+        for l, (a, ky) in enumerate(lines):
+            for kx in range(nx):
+                if fft_z:
+                    ph = np.exp(-2j * np.pi * (kx * xx / nx + ky * yy / ny + a * zz / nz))
+                    out[c, l, kx] = (img * ph).sum() / np.sqrt(nx * ny * nz)
+                else:
+                    ph = np.exp(-2j * np.pi * (kx * xx[a] / nx + ky * yy[a] / ny))
+                    out[c, l, kx] = (img[a] * ph).sum() / np.sqrt(nx * ny)
+    return out
+
+
+@pytest.mark.parametrize("fft_z", [1, 0])
+def test_E_matches_brute_force_dft(fft_z):
+    nz, nx, ny, nc = 3, 4, 6, 2
+    x = crandn(nz, nx, ny)
+    coils = crandn(nc, nz, nx, ny)
+    mask = rand_mask(ny, nz, 0.5)
+    got = O.E(x, coils, mask, fft_z)
+    ref = brute_E(x, coils, mask, fft_z)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("fft_z", [1, 0])
+@pytest.mark.parametrize("shape", [(4, 8, 8, 3), (5, 6, 10, 1), (8, 16, 12, 4)])
+def test_adjoint_identity(fft_z, shape):
+    nz, nx, ny, nc = shape
+    coils = crandn(nc, nz, nx, ny)
+    mask = rand_mask(ny, nz, 0.4)
+    x = crandn(nz, nx, ny)
+    y = crandn(nc, int(mask.sum()), nx)
+    lhs = np.vdot(O.E(x, coils, mask, fft_z), y)
+    rhs = np.vdot(x, O.EH(y, coils, mask, fft_z))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+
+
+def test_full_mask_sos_coils_is_identity():
+    nz, nx, ny, nc = 4, 8, 8, 3
+    coils = P.coil_maps(nx, ny, nz, nc, seed=3)
+    mask = np.ones((nz, ny), np.uint8)
+    x = crandn(nz, nx, ny)
+    assert np.abs(O.EH(O.E(x, coils, mask), coils, mask) - x).max() < 1e-12
+
+
+def test_line_order_is_raster():
+    mask = np.zeros((3, 4), np.uint8)
+    mask[2, 1] = mask[0, 3] = mask[1, 0] = 1
+    kz, ky = O.line_index(mask)
+    assert list(zip(kz, ky)) == [(0, 3), (1, 0), (2, 1)]
+
+
+# ---------------------------------------------------------------- Haar transform
+
+def haar_basis(nx, ny, J):
+    """Analytic orthonormal 2D Haar basis (Mallat positions) built from its definition:
+    level-j details are +-1 / 2^j on aligned 2^j x 2^j blocks (first half +, second half -),
+    the level-J approximation is 1 / 2^J on aligned 2^J x 2^J blocks."""
+    basis = {}
+    for j in range(1, J + 1):
+        b = 2 ** j
+        h = b // 2
+        for bi in range(nx // b):
+            for bj in range(ny // b):
+                sx = np.zeros(nx)
+                sx[bi * b: bi * b + h] = 1
+                sx[bi * b + h: bi * b + b] = -1
+                sy = np.zeros(ny)
+                sy[bj * b: bj * b + h] = 1
+                sy[bj * b + h: bj * b + b] = -1
+                ax = np.zeros(nx)
+                ax[bi * b: bi * b + b] = 1
+                ay = np.zeros(ny)
+                ay[bj * b: bj * b + b] = 1
+                basis[(bi, ny // b + bj)] = np.outer(ax, sy) / b          # x-low / y-high
+                basis[(nx // b + bi, bj)] = np.outer(sx, ay) / b          # x-high / y-low
+                basis[(nx // b + bi, ny // b + bj)] = np.outer(sx, sy) / b
+                if j == J:
+                    basis[(bi, bj)] = np.outer(ax, ay) / b
+    return basis
+
+
+@pytest.mark.parametrize("nx,ny,J", [(8, 8, 3), (16, 24, 3), (8, 16, 2), (4, 4, 1)])
+def test_haar_equals_analytic_basis(nx, ny, J):
+    x = crandn(nx, ny)
+    c = O.haar2(x, J)
+    basis = haar_basis(nx, ny, J)
+    assert len(basis) == nx * ny
+    for (i, j), f in basis.items():
+        assert abs(c[i, j] - (f * x).sum()) < 1e-12
+
+
+def test_haar_orthonormal_and_invertible():
+    x = crandn(5, 16, 24)
+    c = O.T(x, 3)
+    assert abs(np.linalg.norm(c) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.abs(O.Tinv(c, 3) - x).max() < 1e-12
+
+
+def test_haar_constant_block_single_coefficient():
+    x = np.zeros((1, 16, 16), complex)
+    x[0, 8:16, 0:8] = 2 - 1j
+    c = O.T(x, 3)
+    nzc = np.argwhere(np.abs(c) > 1e-12)
+    assert nzc.tolist() == [[0, 1, 0]]
+    assert abs(c[0, 1, 0] - 8 * (2 - 1j)) < 1e-12
+
+
+# ---------------------------------------------------------------- soft threshold
+
+def read_golden(name):
+    rows = []
+    with open(f"{__file__.rsplit('/', 1)[0]}/golden/{name}") as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append([float(v) for v in line.split()])
+    return np.array(rows)
+
+
+def test_soft_threshold_closed_forms():
+    g = read_golden("soft_threshold.txt")
+    for re_, im_, lam, ore, oim in g:
+        got = O.soft(np.array([re_ + 1j * im_]), lam)[0]
+        assert abs(got - (ore + 1j * oim)) < 1e-15
+
+
+def test_soft_threshold_is_prox_by_grid_search():
+    rng = np.random.default_rng(7)
+    grid = np.linspace(-3, 3, 601)
+    Zr, Zi = np.meshgrid(grid, grid, indexing="ij")
+    Zc = Zr + 1j * Zi
+    for _ in range(5):
+        cval = complex(*rng.uniform(-2, 2, 2))
+        lam = rng.uniform(0.1, 1.5)
+        f = 0.5 * np.abs(Zc - cval) ** 2 + lam * np.abs(Zc)
+        zbest = Zc.ravel()[np.argmin(f)]
+        assert abs(zbest - O.soft(np.array([cval]), lam)[0]) < 0.015
+
+
+def test_support_shrink_special_cases():
+    c = crandn(3, 8, 8)
+    lam = 0.7
+    assert np.array_equal(O.support_shrink(c, lam, None), O.soft(c, lam))
+    assert np.array_equal(O.support_shrink(c, lam, np.ones(c.shape, bool)), c)
+    keep = RNG.random(c.shape) < 0.3
+    out = O.support_shrink(c, lam, keep)
+    assert np.array_equal(out[keep], c[keep])
+    # off the support: the prox of lam*|.| (closed form checked above)
+    off = ~keep
+    a = np.abs(c[off])
+    assert np.allclose(np.abs(out[off]), np.maximum(a - lam, 0), atol=1e-14)
+
+
+# ---------------------------------------------------------------- SVT and prior pull
+
+def rand_unitary_cols(n, k, rng):
+    q, _ = np.linalg.qr(crandn(n, k, rng=rng))
+    return q
+
+
+def test_svt_closed_form():
+    rng = np.random.default_rng(1)
+    N, n = 40, 6
+    U = rand_unitary_cols(N, n, rng)
+    V = rand_unitary_cols(n, n, rng)
+    s = np.array([5.0, 3.0, 2.0, 1.0, 0.5, 0.1])
+    M = (U * s) @ V.conj().T
+    lam = 0.8
+    L, sig, s2 = O.svt(M, lam)
+    ref = (U * np.maximum(s - lam, 0)) @ V.conj().T
+    assert np.abs(L - ref).max() < 1e-12
+    assert np.allclose(sig, s, atol=1e-12)
+    # zero threshold is the identity
+    L0, _, _ = O.svt(M, 0.0)
+    assert np.abs(L0 - M).max() < 1e-12
+
+
+def test_svt_rectangular_diagonal_with_phases():
+    n = 4
+    ph = np.exp(1j * np.array([0.3, -1.2, 2.0, 0.7]))
+    s = np.array([4.0, 2.5, 1.0, 0.2])
+    M = np.zeros((7, n), complex)
+    M[np.arange(n), np.arange(n)] = s * ph
+    L, _, _ = O.svt(M, 0.5)
+    ref = np.zeros_like(M)
+    ref[np.arange(n), np.arange(n)] = np.maximum(s - 0.5, 0) * ph
+    assert np.abs(L - ref).max() < 1e-12
+
+
+def test_prior_pull_special_cases_and_linearity():
+    rng = np.random.default_rng(2)
+    N, n = 30, 5
+    U = rand_unitary_cols(N, n, rng)
+    V = rand_unitary_cols(n, n, rng)
+    s = np.array([6.0, 4.0, 3.0, 2.0, 1.5])
+    M = (U * s) @ V.conj().T
+    sp = np.array([5.0, 4.5, 2.0, 1.0, 0.0])
+    lam = 0.5
+    L0, _, a0 = O.svt(M, lam, 0.0, sp)
+    Lplain, _, _ = O.svt(M, lam)
+    assert np.abs(L0 - Lplain).max() < 1e-12                     # lambda_p = 0: plain SVT
+    L1, _, a1 = O.svt(M, lam, 1.0, sp)
+    assert np.allclose(a1, sp, atol=1e-12)                       # lambda_p = 1: sigma_prev
+    assert np.abs(L1 - (U * sp) @ V.conj().T).max() < 1e-12
+    Lh, _, _ = O.svt(M, lam, 0.3, sp)
+    assert np.abs(Lh - (0.7 * L0 + 0.3 * L1)).max() < 1e-12     # linear in lambda_p
+
+
+def test_rank_guard_drops_small_directions():
+    rng = np.random.default_rng(3)
+    U = rand_unitary_cols(20, 3, rng)
+    V = rand_unitary_cols(3, 3, rng)
+    s = np.array([1.0, 0.5, 1e-4])
+    M = (U * s) @ V.conj().T
+    _, _, s2 = O.svt(M, 0.0, 1.0, np.array([1.0, 0.5, 0.3]), tau=1e-3)
+    assert s2[2] == 0.0 and abs(s2[0] - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------- the whole iteration
+
+def small_problem(seed=0, nz=4, nx=16, ny=16, nc=2, frac=0.35, noise=0.0, full=False):
+    rng = np.random.default_rng(seed)
+    coils = P.coil_maps(nx, ny, nz, nc, seed=seed + 1)
+    Z, X, Y = np.meshgrid(np.arange(nz), np.arange(nx), np.arange(ny), indexing="ij")
+    bg = np.exp(-((X - nx / 2) ** 2 + (Y - ny / 2) ** 2) / (2 * (nx / 4) ** 2)) * (1 + 0.2 * Z)
+    x = bg * np.exp(0.3j * Y / ny) + 0.0j
+    x[:, 3:6, 5:9] += 0.8
+    x[1:3, 10:12, 2:4] += 0.6j
+    mask = np.ones((nz, ny), np.uint8) if full else rand_mask(ny, nz, frac, rng)
+    d = O.E(x, coils, mask)
+    if noise:
+        d = d + noise * crandn(*d.shape, rng=rng)
+    return x, coils, mask, d
+
+
+def test_exact_recovery_full_mask_zero_thresholds():
+    x, coils, mask, d = small_problem(full=True)
+    p = O.Params(lambda_L_rel=0.0, lambda_S_rel=0.0, lambda_p=0.0, rank_tau=0.0, max_iters=4)
+    r = O.priori_ls(d, coils, mask, p)
+    assert O.nrmse(r.recon, x) < 1e-12
+    for k in (1, 2, 3):
+        rk = O.priori_ls(d, coils, mask, p, iters=k)
+        assert O.nrmse(rk.recon, x) < 1e-12
+    assert np.abs(O.priori_ls(d, coils, mask, p, iters=1).S).max() == 0.0   # L_0 := X_0
+
+
+@pytest.mark.parametrize("with_support", [False, True])
+def test_objective_non_increasing(with_support):
+    x, coils, mask, d = small_problem(seed=4, noise=1e-3)
+    p = O.Params(lambda_L_rel=0.05, lambda_S_rel=0.02, lambda_p=0.0, rank_tau=1e-3,
+                 max_iters=25)
+    prior = None
+    if with_support:
+        sup = np.abs(O.T(x)) > 0.3
+        prior = O.Prior(support=sup, sigma=np.ones(x.shape[0]))
+    r = O.priori_ls(d, coils, mask, p, prior)
+    F = [h["objective"] for h in r.history]
+    for a, b in zip(F[1:], F[2:]):
+        assert b <= a * (1 + 1e-12), (a, b)
+    assert F[-1] < F[1]
+    # the monitored objective equals F(L, S) evaluated from scratch
+    keep = None if prior is None else prior.support
+    Fk = O.objective(r.L, r.S, d, coils, mask, r.lambda_L, r.lambda_S, keep, p)
+    assert abs(Fk - F[-1]) < 1e-10 * abs(Fk)
+
+
+def test_monotonicity_pin_catches_ascent_sign():
+    """A4 check: the printed sign of the residual (ascent) makes the objective grow."""
+    x, coils, mask, d = small_problem(seed=5, noise=1e-3)
+    X = O.EH(d, coils, mask)
+    L = X.copy()
+    S = np.zeros_like(X)
+    R = O.E(L + S, coils, mask) - d
+    descent = L + S - O.EH(R, coils, mask)
+    ascent = L + S + O.EH(R, coils, mask)
+    f = lambda Z: np.linalg.norm(O.E(Z, coils, mask) - d)
+    assert f(descent) < f(L + S) < f(ascent)
+
+
+def test_empty_prior_with_zero_pull_equals_plain_ls():
+    x, coils, mask, d = small_problem(seed=6, noise=1e-3)
+    p = O.Params(max_iters=8, lambda_p=0.0)
+    a = O.priori_ls(d, coils, mask, p)
+    b = O.priori_ls(d, coils, mask, p,
+                    O.Prior(support=np.zeros(x.shape, bool), sigma=np.full(x.shape[0], 3.0)))
+    assert np.array_equal(a.L, b.L) and np.array_equal(a.S, b.S)
+
+
+def test_lambda_p_one_pins_singular_values_to_prior():
+    x, coils, mask, d = small_problem(seed=7, noise=1e-3)
+    p = O.Params(max_iters=3, lambda_p=1.0, rank_tau=0.0)
+    sp = np.linspace(2.0, 0.5, x.shape[0])
+    r = O.priori_ls(d, coils, mask, p, O.Prior(support=None, sigma=sp))
+    s = np.linalg.svd(O.casorati(r.L), compute_uv=False)
+    assert np.allclose(np.sort(s)[::-1], sp, atol=1e-10)
+
+
+def test_recovery_improves_over_iterations():
+    x, coils, mask, d = small_problem(seed=8, frac=0.5, noise=1e-3)
+    p = O.Params(max_iters=40)
+    e0 = O.nrmse(O.EH(d, coils, mask), x)
+    r = O.priori_ls(d, coils, mask, p)
+    assert O.nrmse(r.recon, x) < 0.7 * e0
+
+
+def test_sequence_passes_prior():
+    w = P.SMALL
+    pr = P.problem(w, frames=2)
+    datas = [O.E(pr["x"][t], pr["coils"], pr["masks"][t]) + pr["noise"][t] for t in range(2)]
+    p = O.Params(max_iters=5)
+    seq = O.sequence(datas, pr["coils"], pr["masks"], p)
+    r1 = O.priori_ls(datas[0], pr["coils"], pr["masks"][0], p)
+    r2 = O.priori_ls(datas[1], pr["coils"], pr["masks"][1], p,
+                     O.Prior(support=r1.support, sigma=r1.sigma))
+    assert np.array_equal(seq[1].L, r2.L) and np.array_equal(seq[1].S, r2.S)
+    assert seq[0].support.any()
+
+
+def test_support_threshold_rule_and_ties():
+    c = np.array([[[1.0 + 0j, 0.5, 0.5000001, 0.0]]])
+    lam = 0.5
+    sup = np.abs(c) > lam
+    assert sup.tolist() == [[[True, False, True, False]]]
+
+
+@pytest.mark.parametrize("fft_z", [1, 0])
+def test_data_consistency_step_is_a_projection_for_one_unit_coil(fft_z):
+    """With C = 1, E^H E = F^H M F is a projection, so step (4) with unit step makes the
+    new estimate agree with the samples exactly: E(X_it) = d (pins the step length)."""
+    rng = np.random.default_rng(9)
+    nz, nx, ny = 4, 8, 16
+    coils = np.ones((1, nz, nx, ny), complex)
+    mask = rand_mask(ny, nz, 0.3, rng)
+    d = crandn(1, int(mask.sum()), nx, rng=rng)
+    p = O.Params(max_iters=1, fft_z=fft_z)
+    for k in (1, 2, 3):
+        r = O.priori_ls(d, coils, mask, p, iters=k)
+        assert np.abs(O.E(r.X, coils, mask, fft_z) - d).max() < 1e-12
