@@ -1,0 +1,427 @@
+#!/usr/bin/env python3
+"""Throughput of recursive Priori L+S reconstruction (arXiv:1411.6206) on one GB300.
+
+A step is one pass of the whole hot path over one batch of input: the 20-frame cardiac-shaped
+sequence (128 x 128 x 16 voxels, 8 coils, 8x variable-density ky-kz undersampling, frame 1
+at 50%, 50 iterations of Algorithm 1 per frame, support and singular values passed from frame
+to frame). Inputs (coil maps, k-space samples of every frame) are resident in HBM before the
+timed region; the per-frame masks are host arrays (the line table is built on the host).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line. `value` is whole-job frames/s; under torchrun every rank reconstructs
+its own sequence (independent sessions, weak scaling, no data-path collective) and the time
+is the maximum over ranks. `--impl reference` times the FP64 CPU oracle on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "recon frames/s and p50/p99 frame latency, served vs plain, at NRMSE≤1e-3"
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=None, help="frames per step (default: all 20)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-frames", type=int, default=2, help="oracle frames in the CPU baseline")
+    ap.add_argument("--profile", type=int, default=1, help="record kernel events in the frame graph")
+    return ap.parse_args()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), float(d.get("sm_max_mhz", 2070.0)), "measured"
+    except Exception:
+        return 6800.0, 2070.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clock and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(float(r[2]) for r in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+def dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ------------------------------------------------------------------------------------
+# workload
+# ------------------------------------------------------------------------------------
+
+def workload(frames):
+    from paper_1411_6206_gb300 import phantom as P
+    w = P.CARDIAC
+    T = w.frames if frames is None else min(frames, w.frames)
+    return w, T
+
+
+def dc_bytes_per_launch(w, m):
+    """Algorithmic HBM bytes of one data-consistency launch: coil maps and hybrid samples read,
+    L and S read, X written (complex64)."""
+    N = w.nx * w.ny * w.nz
+    return N * (8 * w.ncoil + 24) + w.nx * w.ncoil * m * 8
+
+
+def dc_flops_per_launch(w):
+    """Nominal real flops of one data-consistency launch: per coil a forward and an inverse
+    2D FFT of ny*nz points (5 n log2 n each), the coil multiply (6) and the conjugate-coil
+    accumulate (8) per voxel, and the plane Gram epilogue (4 (nc + 1) per voxel)."""
+    N = w.nx * w.ny * w.nz
+    P = w.ny * w.nz
+    return N * (w.ncoil * (10.0 * math.log2(P) + 14.0) + 4.0 * (w.nz + 1))
+
+
+def run_ours(args):
+    import torch
+    from paper_1411_6206_gb300 import lps, phantom as P
+
+    ws, rank, local = dist()
+    torch.cuda.set_device(local)
+    if ws > 1:
+        import torch.distributed as td
+        td.init_process_group("nccl")
+    w, T = workload(args.frames)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(device=dev)
+    lib = lps.load()
+
+    pr = P.problem(w, frames=T)
+    coils = torch.from_numpy(np.ascontiguousarray(pr["coils"].astype(np.complex64))).to(dev)
+    masks = [np.ascontiguousarray(m) for m in pr["masks"]]
+    plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1)
+    plan.set_coils(coils)
+    # k-space of every frame by the library's forward operator, plus the generator's noise
+    kdatas = []
+    with torch.cuda.stream(stream):
+        for t in range(T):
+            n = plan.set_mask(masks[t])
+            x = torch.from_numpy(np.ascontiguousarray(pr["x"][t].astype(np.complex64))).to(dev)
+            kd = torch.empty((w.ncoil, n, w.nx), dtype=torch.complex64, device=dev)
+            lps.forward(plan.handle, x, kd)
+            kd += torch.from_numpy(pr["noise"][t].astype(np.complex64)).to(dev)
+            kdatas.append(kd)
+    stream.synchronize()
+    nlines = [int(m.sum()) for m in masks]
+    recon = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    lps.set_profiling(plan.handle, bool(args.profile))
+
+    def sequence(fev=None):
+        plan.clear_prior()
+        for t in range(T):
+            if fev is not None:
+                fev[t][0].record(stream)
+            plan.set_mask(masks[t])
+            plan.set_data(kdatas[t])
+            plan.reconstruct_frame(recon=recon[t], stats=False)
+            if fev is not None:
+                fev[t][1].record(stream)
+
+    ktimes = []
+    step_ms = []
+    frame_ms = []
+    clocks = Clocks(local)
+    for s in range(args.warmup + args.steps):
+        timed = s >= args.warmup
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+        if timed and s == args.warmup:
+            clocks.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(T)]
+        e0.record(stream)
+        sequence(fev)
+        e1.record(stream)
+        stream.synchronize()
+        if timed:
+            step_ms.append(e0.elapsed_time(e1))
+            frame_ms += [a.elapsed_time(b) for a, b in fev]
+            if args.profile:
+                kt = lps.get_kernel_times(plan.handle)
+                ktimes.append(kt.as_dict())
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    total_ms = sum(step_ms)
+    if ws > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    frames_done = ws * T * args.steps
+    value = frames_done / (total_ms / 1e3)
+
+    # end to end through the C ABI with host buffers: pinned k-space in, pinned recon out
+    pin_k = [kd.cpu().pin_memory() for kd in kdatas]
+    pin_out = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64).pin_memory()
+    plan_h = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1)
+    plan_h.set_coils(coils)
+
+    def seq_host():
+        plan_h.clear_prior()
+        for t in range(T):
+            plan_h.set_mask(masks[t])
+            plan_h.set_data(pin_k[t])
+            plan_h.reconstruct_frame(recon=pin_out[t], stats=False)
+
+    for _ in range(max(1, args.warmup)):
+        seq_host()
+    stream.synchronize()
+    e2e_ms = []
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        stream.synchronize()
+        t0 = time.perf_counter()
+        seq_host()
+        stream.synchronize()
+        e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    h2d = sum(int(k.numel()) * 8 + w.ny * w.nz for k in pin_k)
+    d2h = T * w.nx * w.ny * w.nz * 8
+    e2e_tot = sum(e2e_ms)
+    if ws > 1:
+        t = torch.tensor([e2e_tot], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        e2e_tot = float(t.item())
+    e2e_value = ws * T * args.steps / (e2e_tot / 1e3)
+
+    out = None
+    if rank == 0:
+        hbm, sm_max, src = peaks()
+        alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
+        roof = None
+        launches_per_frame = 3 * w.iters + 5     # xfft, adjoint, haar-max, 3 per iteration, finalize, combine
+        if ktimes:
+            # dominant kernel class over the timed steps
+            tot = {k: sum(d[k]["ms"] for d in ktimes) for k in ktimes[0]}
+            dom = max(tot, key=tot.get)
+            n_l = sum(d[dom]["launches"] for d in ktimes)
+            avg_ms = tot[dom] / max(n_l, 1)
+            m_last = nlines[-1]
+            if dom == "data_consistency":
+                byts = dc_bytes_per_launch(w, m_last)
+                gbs = byts / (avg_ms * 1e-3) / 1e9
+                fl = dc_flops_per_launch(w) / (avg_ms * 1e-3) / 1e12
+                frac_hbm, frac_alu = gbs / hbm, fl / alu_peak
+                if frac_alu >= frac_hbm:
+                    roof = {"bound": "alu", "achieved": round(fl, 3), "peak": round(alu_peak, 2),
+                            "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": None}
+                else:
+                    roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                            "frac": round(frac_hbm, 4), "traffic": None}
+                roof["kernel"] = "k_dc (data consistency, step 4)"
+                roof["avg_launch_us"] = round(avg_ms * 1e3, 3)
+                roof["alt"] = {"hbm_frac": round(frac_hbm, 4), "hbm_gbs": round(gbs, 1),
+                               "alu_frac": round(frac_alu, 4), "alu_tflops": round(fl, 3)}
+                roof["peak_source"] = f"{src} (MEASURED_PEAKS.json hbm_gbs; FP32 = 152 SMs x 128 lanes x 2 x sm_max_mhz)"
+            else:
+                roof = {"bound": "latency", "kernel": dom, "avg_launch_us": round(avg_ms * 1e3, 3)}
+            roof["share"] = {k: round(v / sum(tot.values()), 4) for k, v in tot.items()}
+        ms_step = total_ms / args.steps
+        fl = sorted(frame_ms)
+        out = {
+            "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic: seeded beating-heart phantom, smooth SoS coil maps, VD ky-kz masks, "
+                    "CN noise; k-space made by the library's forward operator",
+            "config": {"workload": f"cardiac-shaped recursive sequence {w.nx}x{w.ny}x{w.nz} x {T} frames, "
+                                   f"{w.ncoil} coils, R={w.accel:g} (frame 1 at 50%), {w.iters} iterations/frame",
+                       "nx": w.nx, "ny": w.ny, "nz": w.nz, "ncoil": w.ncoil, "frames": T, "iters": w.iters,
+                       "mode": "plain (frame by frame, CUDA-graph replay per frame)",
+                       "l2": "256 MiB buffer written before every timed step (L2 flush)",
+                       "parallelism": "independent sequence per GPU" if ws > 1 else "single GPU"},
+            "frame_latency_ms": {"p50": round(float(np.percentile(fl, 50)), 4),
+                                 "p99": round(float(np.percentile(fl, 99)), 4)},
+            "roofline": roof,
+            "e2e": {"value": round(e2e_value, 2), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "ms_per_step": round(e2e_tot / args.steps, 4)},
+            "gpu_launches": launches_per_frame * T * args.steps,
+            "clocks": clk,
+        }
+    plan_h.close()
+    plan.close()
+    if ws > 1:
+        import torch.distributed as td
+        td.barrier()
+        td.destroy_process_group()
+    return out, (w, T)
+
+
+def cpu_baseline(args, w, with_gpu_parity=True):
+    """FP64 oracle on the host cores for a bounded sample of the workload (the first
+    `cpu_frames` frames of the sequence, all iterations), plus GPU parity on the same inputs."""
+    import scipy.fft as sfft
+    from oracle import lps_oracle as O
+    from paper_1411_6206_gb300 import phantom as P
+
+    F = max(1, args.cpu_frames)
+    pr = P.problem(w, frames=F)
+    coils64 = pr["coils"].astype(np.complex64)
+    datas = [(O.E(pr["x"][t], coils64.astype(np.complex128), pr["masks"][t]) + pr["noise"][t]).astype(np.complex64)
+             for t in range(F)]
+    p = O.Params(max_iters=w.iters)
+    cores = os.cpu_count() or 1
+    with sfft.set_workers(cores):
+        t0 = time.perf_counter()
+        refs = O.sequence([d.astype(np.complex128) for d in datas], coils64.astype(np.complex128), pr["masks"], p)
+        dt = time.perf_counter() - t0
+    res = {"value": round(F / dt, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
+           "sample": f"frames 1-{F} of the sequence, {w.iters} iterations each, FP64 NumPy/SciPy "
+                     f"(scipy.fft workers = {cores})", "seconds": round(dt, 2)}
+    nrmse = None
+    if with_gpu_parity:
+        import torch
+        from paper_1411_6206_gb300 import lps
+        plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, max_iters=w.iters, recursive=1)
+        plan.set_coils(torch.from_numpy(coils64).cuda())
+        errs = []
+        out = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+        for t in range(F):
+            plan.set_mask(pr["masks"][t])
+            plan.set_data(torch.from_numpy(datas[t]).cuda())
+            plan.reconstruct_frame(recon=out, stats=False)
+            errs.append(O.nrmse(out.cpu().numpy(), refs[t].recon))
+        plan.close()
+        nrmse = max(errs)
+    return res, nrmse
+
+
+def run_reference(args):
+    """The FP64 oracle as the reference arm: each step reconstructs the next frame of the
+    recursive sequence on the host cores."""
+    import scipy.fft as sfft
+    from oracle import lps_oracle as O
+    from paper_1411_6206_gb300 import phantom as P
+
+    ws, rank, _ = dist()
+    if rank != 0:
+        return None
+    w, T = workload(args.frames)
+    nsteps = args.warmup + args.steps
+    F = min(nsteps, w.frames)
+    pr = P.problem(w, frames=F)
+    coils = pr["coils"].astype(np.complex64).astype(np.complex128)
+    datas = [(O.E(pr["x"][t], coils, pr["masks"][t]) + pr["noise"][t]).astype(np.complex64).astype(np.complex128)
+             for t in range(F)]
+    p = O.Params(max_iters=w.iters)
+    cores = os.cpu_count() or 1
+    prior = None
+    times = []
+    with sfft.set_workers(cores):
+        for s in range(nsteps):
+            t = s % F
+            if t == 0:
+                prior = None
+            t0 = time.perf_counter()
+            r = O.priori_ls(datas[t], coils, pr["masks"][t], p, prior)
+            times.append(time.perf_counter() - t0)
+            prior = O.Prior(support=r.support, sigma=r.sigma)
+    tt = times[args.warmup:]
+    value = len(tt) / sum(tt)
+    fl = sorted(x * 1e3 for x in tt)
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "frames/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(sum(tt) / len(tt) * 1e3, 2), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic (same generator and seeds as the GPU arm)",
+        "config": {"workload": f"cardiac-shaped recursive sequence {w.nx}x{w.ny}x{w.nz}, {w.ncoil} coils, "
+                               f"R={w.accel:g}, {w.iters} iterations/frame; one frame per step",
+                   "nx": w.nx, "ny": w.ny, "nz": w.nz, "ncoil": w.ncoil, "iters": w.iters},
+        "frame_latency_ms": {"p50": round(float(np.percentile(fl, 50)), 2),
+                             "p99": round(float(np.percentile(fl, 99)), 2)},
+        "cpu_baseline": {"value": round(value, 4), "unit": "frames/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{len(tt)} frames of the recursive sequence, one per step"},
+        "e2e": {"value": round(value, 4), "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        out = run_reference(args)
+        if out is not None:
+            print(json.dumps(out), flush=True)
+        return
+    out, (w, T) = run_ours(args)
+    ws, rank, _ = dist()
+    if rank == 0:
+        if ws == 1 and not args.no_cpu_baseline:
+            cb, nr = cpu_baseline(args, w)
+            out["cpu_baseline"] = cb
+            out["nrmse_vs_oracle"] = nr
+        print(json.dumps(out), flush=True)
+
+
+if __name__ == "__main__":
+    main()

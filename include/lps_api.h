@@ -1,0 +1,214 @@
+/*
+ * lps_api.h — C ABI of the GB300 (sm_103a) Priori L+S reconstruction library (liblps.so).
+ *
+ * Method: Zonoobi, Faghih Roohi, Kassim, "Low-Rank and Sparse Matrix Decomposition with
+ * a-priori knowledge for Dynamic 3D MRI reconstruction" (arXiv:1411.6206).
+ *   - Each time instance t is a volume nx x ny x nz reshaped to the Casorati matrix
+ *     X^(t) in C^{(nx ny) x nz}, one column per slice (Sec. 2), decomposed as L + S.
+ *   - Acquisition: d = A(X) + eta (Sec. 2), here the multi-coil Cartesian encode
+ *     E = M F C: coil sensitivities C_c, orthonormal unshifted DFT F over (z, x, y) (or over
+ *     (x, y) per slice), and a line mask M on the (ky, kz) grid (kx fully sampled).
+ *   - Algorithm 1 (Sec. 3): (0) X_0 = E^H d, S_0 = 0; per iteration (1) singular-value
+ *     soft-thresholding of X - S, (2) pull of the singular values towards those of L^(t-1),
+ *     (3) soft-thresholding of the wavelet coefficients of S off the support of the previous
+ *     frame, (4) the data-consistency update X = L + S - E^H(E(L + S) - d).
+ *   - Recursion (Sec. 3, Fig. 2): frame 1 runs plain L+S (no prior), frame t >= 2 uses the
+ *     support and singular values of frame t-1.
+ *
+ * Conventions shared by every call:
+ *   - Every call returns int: LPS_OK (0) or a negative LPS_ERR_* code. No exceptions or
+ *     aborts cross this boundary; lps_status_string() names a code; lps_last_error() gives a
+ *     one-line description of the last failure in the calling thread.
+ *   - Array arguments are plain pointers to either host or device memory (CUDA unified
+ *     addressing decides which); they are owned by the caller. Input arrays are copied
+ *     into the plan, in stream order on the plan's stream, before the call returns; a
+ *     device input may be reused once that stream has passed the call. Host inputs are
+ *     copied synchronously. Outputs are written in stream order; to a host pointer the call
+ *     synchronises the stream before returning.
+ *   - complex64 = two float32 (re, im), interleaved (the layout of std::complex<float>,
+ *     cuComplex, torch.complex64).
+ *   - Image arrays are [nz][nx][ny] with y fastest. Coil maps are [ncoil][nz][nx][ny].
+ *     Masks are uint8 [nz][ny] (nonzero = sampled), indexed [kz][ky] for the 3D encode
+ *     (fft_z = 1) and [z][ky] for the per-slice 2D encode (fft_z = 0). Frequencies are
+ *     unshifted DFT indices. k-space samples are [ncoil][nlines][nx], line l being the l-th
+ *     nonzero mask entry in raster order (index kz*ny + ky ascending), each line one kx
+ *     readout of nx samples.
+ *   - Wavelet coefficients (support bitmaps): per slice z the orthonormal J-level 2D Haar
+ *     transform splits into independent aligned B x B blocks, B = 2^J <= 8. Coefficients are
+ *     numbered by 8 x 8 in-plane tiles:
+ *       ((z * (nx/8) + tx) * (ny/8) + ty) * 64 + u*8 + v
+ *     where (tx, ty) is the tile and (u, v) the position in the tile's 8 x 8 coefficient
+ *     array, in which every aligned B x B sub-block holds that block's own Mallat layout
+ *     (approximation at the block origin; the level-j details at offsets B/2^j along v
+ *     (x-low, y-high), along u (x-high, y-low) and both). For J = 3 a tile is one block.
+ *     Bit i of a bitmap is bit (i & 31) of 32-bit word i >> 5; lps_support_words() gives the
+ *     word count (nx*ny*nz/32).
+ *   - Work is issued on the plan's CUDA stream. Only calls that return host-visible results
+ *     (stats, host outputs, mask upload) synchronise it.
+ */
+#ifndef LPS_API_H
+#define LPS_API_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define LPS_OK               0
+#define LPS_ERR_INVALID_ARG -1   /* bad size, NULL where required, value out of range      */
+#define LPS_ERR_OOM         -2   /* device or pinned-host allocation failed                */
+#define LPS_ERR_CUDA        -3   /* a CUDA runtime call or kernel launch failed            */
+#define LPS_ERR_TIMEOUT     -4   /* a bounded device-side wait gave up                     */
+#define LPS_ERR_NONFINITE   -5   /* NaN/Inf met in the residual or the singular values     */
+#define LPS_ERR_ADMISSION   -6   /* refused by a memory budget                             */
+#define LPS_ERR_STATE       -7   /* call out of order (e.g. iterate before set_data)       */
+#define LPS_ERR_UNSUPPORTED -8   /* size or option this build does not implement           */
+
+/* ---- options ---------------------------------------------------------------------- */
+#define LPS_LAYOUT_SLICES      0  /* Casorati columns = the nz slices of a volume (Sec. 2) */
+
+#define LPS_FP32               0  /* every stage in float32 (Gram and reprojection on FMA) */
+
+#define LPS_EIG_FP32           0  /* Gram eigendecomposition by float32 Jacobi             */
+#define LPS_EIG_FP64           1  /* float32 Jacobi polished by float64 Jacobi sweeps      */
+
+#define LPS_SUPPORT_THRESHOLD  0  /* T^(t) = {i : |c_i| > lambda_S} of the last iteration  */
+#define LPS_SUPPORT_NONZERO    1  /* T^(t) = supp of the shrunk coefficients (literal)     */
+
+#define LPS_MAX_NC            32  /* largest Casorati column count (slices) supported      */
+
+typedef struct lps_plan lps_plan;   /* opaque; owns its device workspace */
+
+typedef struct lps_params {
+  int nx, ny, nz, ncoil;   /* volume size (nx: fully sampled readout axis) and coils       */
+  int layout;              /* LPS_LAYOUT_SLICES                                             */
+  int fft_z;               /* 1: 3D Fourier encode, (ky,kz) line mask; 0: 2D per slice     */
+  int wavelet_levels;      /* Haar levels J, 1..3 (nx, ny multiples of 2^J)                */
+  int max_iters;           /* iterations of Algorithm 1 per frame (1..4096)                */
+  double lambda_L_rel;     /* lambda_L = lambda_L_rel * sigma_max(X_0)                      */
+  double lambda_S_rel;     /* lambda_S = lambda_S_rel * max |T(X_0)|                        */
+  double lambda_p;         /* prior pull of step (2), in [0, 1]                             */
+  double rank_tau;         /* drop directions with sigma_i <= rank_tau * sigma_1            */
+  double tol;              /* stop when ||Z_k - Z_{k-1}|| / ||Z_{k-1}|| < tol (0 = never)   */
+  int precision;           /* LPS_FP32                                                      */
+  int eig_precision;       /* LPS_EIG_FP32 | LPS_EIG_FP64                                   */
+  int support_rule;        /* LPS_SUPPORT_THRESHOLD | LPS_SUPPORT_NONZERO                   */
+  int recursive;           /* 1: each lps_reconstruct_frame installs its support and sigma
+                              as the prior of the next call (the recursion of Sec. 3)        */
+  int reserved[8];         /* must be zero                                                  */
+} lps_params;
+
+typedef struct lps_stats {
+  int iters;               /* iterations run in the last frame / lps_iterate call          */
+  int rank;                /* number of sigma'' > 0 at the last iteration                  */
+  long long support_count; /* bits set in the output support                               */
+  double lambda_L, lambda_S;
+  double sigma_max;        /* sigma_1(X_0)                                                  */
+  double resid_norm2;      /* ||E(L + S) - d||^2 after the last iteration                   */
+  double nuclear;          /* sum of sigma'' (nuclear norm of L)                            */
+  double l1_off_support;   /* sum |c'_i| over coefficients off the prior support           */
+  double objective;        /* resid_norm2/2 + lambda_L*nuclear + lambda_S*l1_off_support    */
+  double rel_change;       /* ||Z_k - Z_{k-1}|| / ||Z_{k-1}||, Z = L + S                     */
+} lps_stats;
+
+/* Per-iteration record returned by lps_get_history (same meaning as lps_stats fields). */
+typedef struct lps_iter_record {
+  double resid_norm2, nuclear, l1_off_support, objective, rel_change;
+  int rank, pad;
+} lps_iter_record;
+
+/* Fill *p with the defaults: layout SLICES, fft_z 1, J 3, 50 iterations, lambda_L_rel 0.01,
+ * lambda_S_rel 0.005, lambda_p 0.5, rank_tau 1e-3, tol 0, FP32, threshold support rule,
+ * recursive 0. Sizes are left 0. */
+int lps_params_init(lps_params* p);
+
+/* Create a plan for one problem shape. Validates *p (LPS_ERR_INVALID_ARG /
+ * LPS_ERR_UNSUPPORTED), allocates the device workspace (LPS_ERR_OOM) and binds `stream`
+ * (a cudaStream_t; NULL = the legacy default stream). *out is NULL on failure. */
+int lps_plan_create(const lps_params* p, void* stream, lps_plan** out);
+int lps_plan_destroy(lps_plan* plan);
+int lps_set_stream(lps_plan* plan, void* stream);
+/* Device bytes the plan holds (workspace + copies of coils, data and state). */
+int lps_plan_device_bytes(const lps_plan* plan, size_t* bytes);
+/* Bytes lps_plan_create would allocate for *p, without allocating. */
+int lps_estimate_device_bytes(const lps_params* p, size_t* bytes);
+
+/* Acquisition operator pieces (Sec. 2). The mask [nz][ny] (host or device) fixes the line
+ * list; it synchronises the stream (the line count is needed on the host). A mask with no
+ * sampled entry is LPS_ERR_INVALID_ARG. Returns the number of lines via *nlines (nullable). */
+int lps_set_mask(lps_plan* plan, const uint8_t* mask, int* nlines);
+/* Coil sensitivity maps, complex64 [ncoil][nz][nx][ny]. */
+int lps_set_coils(lps_plan* plan, const void* coils);
+/* k-space samples y^(t) of the current mask, complex64 [ncoil][nlines][nx]; nlines must
+ * equal the count of the last lps_set_mask. Transformed once along kx into the plan's
+ * hybrid (x, ky, kz) copy. Resets the iteration state (the next iterate starts at step 0). */
+int lps_set_data(lps_plan* plan, const void* kdata, int nlines);
+/* Prior of Algorithm 1 from frame t-1: support bitmap of T(S^(t-1)) (lps_support_words
+ * words) and sigma'' of L^(t-1) (nz doubles, descending rank order). Either may be NULL:
+ * NULL support = empty T^(t-1); NULL sigma = no pull (step 2 skipped). lps_clear_prior()
+ * returns the plan to plain L+S (frame t = 1). */
+int lps_set_prior(lps_plan* plan, const uint32_t* support, const double* sigma_prev);
+int lps_clear_prior(lps_plan* plan);
+
+/* Run n iterations of Algorithm 1 on the resident state, starting with step (0) if the
+ * state was reset by lps_set_data. Stops early on the tol rule (stats->iters tells). */
+int lps_iterate(lps_plan* plan, int n_iters, lps_stats* stats /* nullable */);
+
+/* One full time instance: step (0), max_iters iterations (or until tol), outputs.
+ * out_recon = L + S, out_L, out_S: complex64 [nz][nx][ny]; out_support: bitmap words;
+ * out_sigma: nz doubles (sigma'' in rank order). All outputs nullable. The per-frame launch
+ * sequence is recorded once into a CUDA graph and replayed. */
+int lps_reconstruct_frame(lps_plan* plan, void* out_recon, void* out_L, void* out_S,
+                          uint32_t* out_support, double* out_sigma, lps_stats* stats);
+
+/* Per-iteration records of the last frame / iterate calls since lps_set_data
+ * (at most max records; *count = records written). Synchronises. */
+int lps_get_history(lps_plan* plan, lps_iter_record* out, int max, int* count);
+
+/* State access for tests and checkpoints: X (last step-4 output), L, S, complex64 images.
+ * lps_set_state loads X, S and L_prev (the L of the previous iteration; NULL = X) together
+ * with fixed lambda_L, lambda_S, as if `iters_done` iterations had run. */
+int lps_get_state(lps_plan* plan, void* X, void* L, void* S);
+/* Support bitmap T^(t) and sigma'' of the last iteration (the prior the next frame would
+ * receive); either output may be NULL. */
+int lps_get_support(lps_plan* plan, uint32_t* support, double* sigma);
+int lps_set_state(lps_plan* plan, const void* X, const void* S, const void* L_prev,
+                  double lambda_L, double lambda_S, int iters_done);
+
+/* Standalone operators with the current coils and mask (Sec. 2):
+ * forward: image -> k-space samples [ncoil][nlines][nx]; adjoint: samples -> image. */
+int lps_forward(lps_plan* plan, const void* image, void* kdata);
+int lps_adjoint(lps_plan* plan, const void* kdata, void* image);
+/* Step (4) alone on the resident data: X = Z - E^H(E Z - d); *resid_norm2 = ||E Z - d||^2
+ * (nullable). */
+int lps_data_consistency(lps_plan* plan, const void* Z, void* X, double* resid_norm2);
+
+/* Kernel timing of the per-frame graph. With profiling on, the graph records CUDA events
+ * around every kernel it launches; lps_get_kernel_times synchronises the stream and returns,
+ * for the last lps_reconstruct_frame, the launch count and summed device time of each class:
+ * [0] data consistency (step 4), [1] low-rank/sparse update (steps 1-3 on the Casorati
+ * matrix), [2] Gram eigendecomposition and singular-value steps, [3] step (0) kernels. */
+typedef struct lps_kernel_times {
+  int launches[4];
+  double ms[4];
+} lps_kernel_times;
+int lps_set_profiling(lps_plan* plan, int on);
+int lps_get_kernel_times(lps_plan* plan, lps_kernel_times* out);
+
+/* Checkpoint of the recursion state (prior support, prior sigma, L, S, lambdas) to a host
+ * buffer. With buf NULL, *bytes receives the size needed. */
+int lps_session_export(lps_plan* plan, void* buf, size_t* bytes);
+int lps_session_import(lps_plan* plan, const void* buf, size_t bytes);
+
+size_t lps_support_words(const lps_params* p);
+const char* lps_status_string(int status);
+const char* lps_last_error(void);
+int lps_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LPS_API_H */

@@ -1,0 +1,1036 @@
+// Host side of the C ABI declared in include/lps_api.h: plan lifetime, validation, device
+// buffers, the per-frame launch sequence of Algorithm 1 (Sec. 3) and its CUDA graph.
+#include "lps_api.h"
+#include "lps_internal.cuh"
+
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+using namespace lps;
+
+namespace lps {
+cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part,
+                              cudaStream_t st);
+cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long long n, cudaStream_t st);
+}  // namespace lps
+
+namespace {
+
+thread_local char g_err[512] = "";
+
+void set_err(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+
+#define CK(call)                                                                        \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess) {                                                            \
+      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return (e_ == cudaErrorMemoryAllocation) ? LPS_ERR_OOM : LPS_ERR_CUDA;              \
+    }                                                                                   \
+  } while (0)
+
+#define ARG(cond, ...)          \
+  do {                          \
+    if (!(cond)) {              \
+      set_err(__VA_ARGS__);     \
+      return LPS_ERR_INVALID_ARG; \
+    }                           \
+  } while (0)
+
+bool make_fft_plan(int n, FftPlan& p) {
+  p.n = n;
+  p.np = 0;
+  int r = n;
+  auto push = [&](int v) {
+    if (p.np >= kMaxPasses) return false;
+    p.r[p.np++] = v;
+    return true;
+  };
+  while (r % 16 == 0 && r != 32 && r != 64 && r != 128 && r != 512) {
+    if (!push(16)) return false;
+    r /= 16;
+  }
+  // remaining power of two: 32 = 8x4, 64 = 8x8, 128 = 16x8, 512 = 16x16x2 handled above
+  if (r % 128 == 0) {
+    if (!push(16) || !push(8)) return false;
+    r /= 128;
+  }
+  while (r % 8 == 0) {
+    if (!push(8)) return false;
+    r /= 8;
+  }
+  while (r % 4 == 0) {
+    if (!push(4)) return false;
+    r /= 4;
+  }
+  while (r % 2 == 0) {
+    if (!push(2)) return false;
+    r /= 2;
+  }
+  for (int f : {3, 5, 7}) {
+    while (r % f == 0) {
+      if (!push(f)) return false;
+      r /= f;
+    }
+  }
+  for (int f = 11; r > 1 && f <= 64; f += 2) {
+    while (r % f == 0) {
+      if (!push(f)) return false;
+      r /= f;
+    }
+  }
+  return r == 1;
+}
+
+std::vector<float2> twiddles(int n) {
+  std::vector<float2> t(n);
+  for (int q = 0; q < n; ++q) {
+    const double ang = 2.0 * M_PI * (double)q / (double)n;
+    t[q] = make_float2((float)std::cos(ang), (float)(-std::sin(ang)));
+  }
+  return t;
+}
+
+bool is_device_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+struct lps_plan {
+  lps_params p;
+  Geom g;
+  cudaStream_t st = nullptr;
+  cudaStream_t cap = nullptr;
+  // device state
+  float2 *X = nullptr, *L = nullptr, *S = nullptr, *R = nullptr, *coils = nullptr;
+  float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
+  float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
+  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
+  int* lines = nullptr;
+  float *dc_part = nullptr, *lrs_part = nullptr;
+  double *sigma_out = nullptr, *sigma_prev = nullptr;
+  uint32_t *sup_out = nullptr, *sup_prior = nullptr;
+  DevPersist* persist = nullptr;
+  DevCtrl* ctrl = nullptr;
+  IterRec* hist = nullptr;
+  // pinned host mirrors; h_persist and h_lines are the sources of stream-ordered uploads and
+  // are rewritten only after `upload_done` (recorded after the previous upload) completes
+  DevCtrl* h_ctrl = nullptr;
+  DevPersist* h_persist = nullptr;
+  int* h_lines = nullptr;
+  cudaEvent_t upload_done = nullptr;
+  bool upload_pending = false;
+  // host state
+  int nlines = 0, m_cap = 0;
+  bool have_mask = false, have_coils = false, have_data = false, state_ready = false;
+  int iters_done = 0;
+  size_t dev_bytes = 0;
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  // profiling: event pairs around every kernel of the frame graph, by kernel class
+  bool profiling = false;
+  std::vector<cudaEvent_t> ev;      // 2 per recorded launch
+  std::vector<int> ev_class;        // class of each pair
+  int ev_used = 0;
+};
+
+namespace {
+
+template <typename T>
+int dalloc(lps_plan* P, T** ptr, size_t count) {
+  const size_t b = count * sizeof(T);
+  CK(cudaMalloc((void**)ptr, b > 0 ? b : 16));
+  P->dev_bytes += b;
+  return LPS_OK;
+}
+
+int validate(const lps_params* p, Geom* gout) {
+  ARG(p != nullptr, "params is NULL");
+  for (int r : p->reserved) ARG(r == 0, "reserved fields must be zero");
+  ARG(p->nx >= 8 && p->ny >= 8 && p->nz >= 1, "sizes must be nx, ny >= 8, nz >= 1");
+  ARG(p->nx % 8 == 0 && p->ny % 8 == 0, "nx and ny must be multiples of 8");
+  ARG(p->nx <= 1024 && p->ny <= 1024, "nx, ny <= 1024");
+  ARG(p->ncoil >= 1 && p->ncoil <= 64, "ncoil must be in 1..64");
+  ARG(p->layout == LPS_LAYOUT_SLICES, "only LPS_LAYOUT_SLICES is implemented");
+  ARG(p->fft_z == 0 || p->fft_z == 1, "fft_z must be 0 or 1");
+  ARG(p->wavelet_levels >= 1 && p->wavelet_levels <= 3, "wavelet_levels must be 1..3");
+  ARG(p->max_iters >= 1 && p->max_iters <= 4096, "max_iters must be 1..4096");
+  ARG(std::isfinite(p->lambda_L_rel) && p->lambda_L_rel >= 0, "lambda_L_rel must be finite, >= 0");
+  ARG(std::isfinite(p->lambda_S_rel) && p->lambda_S_rel >= 0, "lambda_S_rel must be finite, >= 0");
+  ARG(p->lambda_p >= 0 && p->lambda_p <= 1, "lambda_p must be in [0, 1]");
+  ARG(p->rank_tau >= 0 && p->rank_tau < 1, "rank_tau must be in [0, 1)");
+  ARG(p->tol >= 0 && std::isfinite(p->tol), "tol must be finite, >= 0");
+  ARG(p->precision == LPS_FP32, "precision must be LPS_FP32");
+  ARG(p->eig_precision == LPS_EIG_FP32 || p->eig_precision == LPS_EIG_FP64, "bad eig_precision");
+  ARG(p->support_rule == 0 || p->support_rule == 1, "bad support_rule");
+  ARG(p->recursive == 0 || p->recursive == 1, "recursive must be 0 or 1");
+  if (p->nz > LPS_MAX_NC) {
+    set_err("nz = %d exceeds LPS_MAX_NC = %d", p->nz, LPS_MAX_NC);
+    return LPS_ERR_UNSUPPORTED;
+  }
+  Geom g{};
+  g.nx = p->nx;
+  g.ny = p->ny;
+  g.nz = p->nz;
+  g.ncoil = p->ncoil;
+  g.nc = p->nz;
+  g.plane = p->ny * p->nz;
+  g.nyp = p->ny + 1;
+  g.planeP = p->nz * g.nyp + ((p->nz * g.nyp) & 1);
+  g.fft_z = p->fft_z;
+  g.J = p->wavelet_levels;
+  g.ntiles = (p->nx / 8) * (p->ny / 8);
+  g.N = (long long)p->nx * p->ny * p->nz;
+  g.scale_yz = (float)(1.0 / std::sqrt((double)p->ny * (p->fft_z ? p->nz : 1)));
+  g.scale_x = (float)(1.0 / std::sqrt((double)p->nx));
+  if (!make_fft_plan(p->ny, g.py) || !make_fft_plan(p->nz, g.pz) || !make_fft_plan(p->nx, g.px)) {
+    set_err("FFT lengths need prime factors <= 64 and at most %d passes", kMaxPasses);
+    return LPS_ERR_UNSUPPORTED;
+  }
+  if (dc_ept(g) < 0 || dc_smem_bytes(g) > 227 * 1024) {
+    set_err("x-plane of %d x %d does not fit one CTA", p->ny, p->nz);
+    return LPS_ERR_UNSUPPORTED;
+  }
+  g.mpad = 0;
+  if (gout) *gout = g;
+  return LPS_OK;
+}
+
+int free_plan(lps_plan* P) {
+  if (!P) return LPS_OK;
+  if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  void* bufs[] = {P->X,        P->L,        P->S,       P->R,         P->coils,     P->dhyb,      P->kstage,
+                  P->hscratch, P->istage,   P->W,       P->V,         P->gram_part, P->tw_x,      P->tw_y,
+                  P->tw_z,     P->lines,    P->dc_part, P->lrs_part,  P->sigma_out, P->sigma_prev, P->sup_out,
+                  P->sup_prior, P->persist, P->ctrl,    P->hist};
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
+  if (P->h_persist) cudaFreeHost(P->h_persist);
+  if (P->h_lines) cudaFreeHost(P->h_lines);
+  if (P->upload_done) cudaEventDestroy(P->upload_done);
+  if (P->cap) cudaStreamDestroy(P->cap);
+  for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+  delete P;
+  return LPS_OK;
+}
+
+size_t support_words(const Geom& g) { return (size_t)(g.N / 32); }
+
+// Wait until the pinned upload sources may be rewritten (the previous upload has landed).
+int wait_upload(lps_plan* P) {
+  if (P->upload_pending) {
+    CK(cudaEventSynchronize(P->upload_done));
+    P->upload_pending = false;
+  }
+  return LPS_OK;
+}
+
+int upload_persist(lps_plan* P) {
+  CK(cudaMemcpyAsync(P->persist, P->h_persist, sizeof(DevPersist), cudaMemcpyHostToDevice, P->st));
+  CK(cudaEventRecord(P->upload_done, P->st));
+  P->upload_pending = true;
+  return LPS_OK;
+}
+
+// Grow the line-dependent buffers to hold m lines.
+int ensure_lines(lps_plan* P, int m) {
+  if (m <= P->m_cap) return LPS_OK;
+  const int cap = (m + 1) & ~1;
+  CK(cudaStreamSynchronize(P->st));
+  if (P->dhyb) cudaFree(P->dhyb);
+  if (P->kstage) cudaFree(P->kstage);
+  if (P->hscratch) cudaFree(P->hscratch);
+  P->dhyb = P->kstage = P->hscratch = nullptr;
+  const size_t hyb = (size_t)P->g.nx * P->g.ncoil * cap + 4;
+  int rc;
+  if ((rc = dalloc(P, &P->dhyb, hyb))) return rc;
+  if ((rc = dalloc(P, &P->kstage, (size_t)P->g.ncoil * cap * P->g.nx + 4))) return rc;
+  if ((rc = dalloc(P, &P->hscratch, hyb))) return rc;
+  P->m_cap = cap;
+  P->g.mpad = cap;
+  P->graph_valid = false;
+  return LPS_OK;
+}
+
+DcArgs dc_args(lps_plan* P) {
+  DcArgs a{};
+  a.g = P->g;
+  a.coils = P->coils;
+  a.dhyb = P->dhyb;
+  a.lines = P->lines;
+  a.tw_y = P->tw_y;
+  a.tw_z = P->tw_z;
+  a.persist = P->persist;
+  return a;
+}
+
+#define LK(call)                                                                      \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess) {                                                          \
+      set_err("launch %s failed: %s", #call, cudaGetErrorString(e_));                  \
+      return LPS_ERR_CUDA;                                                            \
+    }                                                                                 \
+  } while (0)
+
+// Event pair around one launch when profiling (only while building the frame graph).
+int prof_begin(lps_plan* P, int cls, cudaStream_t st) {
+  if (!P->profiling || st != P->cap) return LPS_OK;
+  const size_t need = 2 * (size_t)(P->ev_used + 1);
+  while (P->ev.size() < need) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    P->ev.push_back(e);
+  }
+  if (P->ev_class.size() < (size_t)P->ev_used + 1) P->ev_class.resize(P->ev_used + 1);
+  P->ev_class[P->ev_used] = cls;
+  CK(cudaEventRecord(P->ev[2 * P->ev_used], st));
+  return LPS_OK;
+}
+int prof_end(lps_plan* P, cudaStream_t st) {
+  if (!P->profiling || st != P->cap) return LPS_OK;
+  CK(cudaEventRecord(P->ev[2 * P->ev_used + 1], st));
+  ++P->ev_used;
+  return LPS_OK;
+}
+#define PROF(cls, stmt)                                  \
+  do {                                                   \
+    int prc_;                                            \
+    if ((prc_ = prof_begin(P, cls, st))) return prc_;    \
+    stmt;                                                \
+    if ((prc_ = prof_end(P, st))) return prc_;           \
+  } while (0)
+
+// Step (0): X_0 = E^H d, L_0 := X_0, S_0 = 0, Gram of X_0, max |T(X_0)|.
+int enqueue_init(lps_plan* P, cudaStream_t st) {
+  CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), st));
+  DcArgs a = dc_args(P);
+  a.X = P->X;
+  a.L_out = P->L;
+  a.S_out = P->S;
+  a.gram_part = P->gram_part;
+  a.ctrl = P->ctrl;
+  PROF(3, LK(launch_dc(a, kDcAdjoint, st)));
+  LrsArgs l{};
+  l.g = P->g;
+  l.X = P->X;
+  l.L = P->L;
+  l.S = P->S;
+  l.W = P->W;
+  l.lrs_part = P->lrs_part;
+  l.persist = P->persist;
+  l.ctrl = P->ctrl;
+  l.haar_max_only = 1;
+  PROF(3, LK(launch_lrs(l, st)));
+  return LPS_OK;
+}
+
+EigArgs eig_args(lps_plan* P, int iter, int finalize) {
+  EigArgs e{};
+  e.g = P->g;
+  e.gram_part = P->gram_part;
+  e.nparts = P->g.nx;
+  e.dc_part = P->dc_part;
+  e.lrs_part = P->lrs_part;
+  e.W = P->W;
+  e.V = P->V;
+  e.sigma_prev = P->sigma_prev;
+  e.sigma_out = P->sigma_out;
+  e.hist = P->hist;
+  e.persist = P->persist;
+  e.ctrl = P->ctrl;
+  e.lambda_L_rel = P->p.lambda_L_rel;
+  e.lambda_S_rel = P->p.lambda_S_rel;
+  e.lambda_p = P->p.lambda_p;
+  e.rank_tau = P->p.rank_tau;
+  e.tol = P->p.tol;
+  e.iter = iter;
+  e.finalize = finalize;
+  e.eig_fp64 = P->p.eig_precision == LPS_EIG_FP64;
+  return e;
+}
+
+// Iteration k: steps (1)-(2) (eig kernel), (3) (low-rank/sparse kernel), (4) (DC kernel).
+int enqueue_iter(lps_plan* P, int k, cudaStream_t st) {
+  PROF(2, LK(launch_eig(eig_args(P, k, 0), st)));
+  LrsArgs l{};
+  l.g = P->g;
+  l.X = P->X;
+  l.L = P->L;
+  l.S = P->S;
+  l.W = P->W;
+  l.sup_prior = P->sup_prior;
+  l.sup_out = P->sup_out;
+  l.lrs_part = P->lrs_part;
+  l.persist = P->persist;
+  l.ctrl = P->ctrl;
+  l.support_rule = P->p.support_rule;
+  PROF(1, LK(launch_lrs(l, st)));
+  DcArgs a = dc_args(P);
+  a.L = P->L;
+  a.S = P->S;
+  a.X = P->X;
+  a.gram_part = P->gram_part;
+  a.dc_part = P->dc_part;
+  a.ctrl = P->ctrl;
+  PROF(0, LK(launch_dc(a, kDcUpdate, st)));
+  return LPS_OK;
+}
+
+int enqueue_finalize(lps_plan* P, int k_last, cudaStream_t st) {
+  PROF(2, LK(launch_eig(eig_args(P, k_last + 1, 1), st)));
+  return LPS_OK;
+}
+
+int enqueue_frame(lps_plan* P, cudaStream_t st) {
+  int rc;
+  if ((rc = enqueue_init(P, st))) return rc;
+  for (int k = 1; k <= P->p.max_iters; ++k)
+    if ((rc = enqueue_iter(P, k, st))) return rc;
+  if ((rc = enqueue_finalize(P, P->p.max_iters, st))) return rc;
+  if (P->p.recursive) {
+    const size_t w = support_words(P->g);
+    CK(cudaMemcpyAsync(P->sup_prior, P->sup_out, w * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(P->sigma_prev, P->sigma_out, P->g.nc * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    // persist.has_sup / has_sigma: nonzero byte pattern
+    CK(cudaMemsetAsync(&P->persist->has_sup, 1, 2 * sizeof(int), st));
+  }
+  return LPS_OK;
+}
+
+int build_graph(lps_plan* P) {
+  if (P->graph_valid) return LPS_OK;
+  if (P->gexec) {
+    cudaGraphExecDestroy(P->gexec);
+    P->gexec = nullptr;
+  }
+  P->ev_used = 0;
+  CK(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeRelaxed));
+  int rc = enqueue_frame(P, P->cap);
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(P->cap, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  CK(e);
+  e = cudaGraphInstantiate(&P->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  CK(e);
+  P->graph_valid = true;
+  return LPS_OK;
+}
+
+int read_stats(lps_plan* P, lps_stats* s) {
+  CK(cudaMemcpyAsync(P->h_ctrl, P->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  const DevCtrl& c = *P->h_ctrl;
+  if (c.err & kErrTimeout) {
+    set_err("a bounded device wait gave up");
+    return LPS_ERR_TIMEOUT;
+  }
+  if (c.err & kErrNonfinite) {
+    set_err("non-finite residual or singular values");
+    return LPS_ERR_NONFINITE;
+  }
+  if (!s) return LPS_OK;
+  std::memset(s, 0, sizeof(*s));
+  s->iters = c.iters_done;
+  s->lambda_L = c.lambda_L;
+  s->lambda_S = c.lambda_S;
+  s->sigma_max = c.sigma_max;
+  if (c.iters_done >= 1) {
+    IterRec r;
+    CK(cudaMemcpy(&r, P->hist + (c.iters_done - 1), sizeof(IterRec), cudaMemcpyDeviceToHost));
+    s->rank = r.rank;
+    s->resid_norm2 = r.resid2;
+    s->nuclear = r.nuclear;
+    s->l1_off_support = r.l1;
+    s->objective = r.objective;
+    s->rel_change = r.rel_change;
+  }
+  // support count from the last low-rank/sparse partials
+  std::vector<float> part((size_t)P->g.ntiles * 4);
+  CK(cudaMemcpy(part.data(), P->lrs_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost));
+  long long cnt = 0;
+  for (int t = 0; t < P->g.ntiles; ++t) cnt += (long long)part[(size_t)t * 4 + 3];
+  s->support_count = cnt;
+  return LPS_OK;
+}
+
+int copy_out(lps_plan* P, void* dst, const void* src, size_t bytes, bool* host_dst) {
+  if (!dst) return LPS_OK;
+  CK(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, P->st));
+  if (!is_device_ptr(dst)) *host_dst = true;
+  return LPS_OK;
+}
+
+int need_ready(lps_plan* P) {
+  if (!P) {
+    set_err("plan is NULL");
+    return LPS_ERR_INVALID_ARG;
+  }
+  if (!P->have_coils || !P->have_mask || !P->have_data) {
+    set_err("set_coils, set_mask and set_data must precede iterations");
+    return LPS_ERR_STATE;
+  }
+  return LPS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lps_version(void) { return 1; }
+
+const char* lps_last_error(void) { return g_err; }
+
+const char* lps_status_string(int s) {
+  switch (s) {
+    case LPS_OK: return "LPS_OK";
+    case LPS_ERR_INVALID_ARG: return "LPS_ERR_INVALID_ARG";
+    case LPS_ERR_OOM: return "LPS_ERR_OOM";
+    case LPS_ERR_CUDA: return "LPS_ERR_CUDA";
+    case LPS_ERR_TIMEOUT: return "LPS_ERR_TIMEOUT";
+    case LPS_ERR_NONFINITE: return "LPS_ERR_NONFINITE";
+    case LPS_ERR_ADMISSION: return "LPS_ERR_ADMISSION";
+    case LPS_ERR_STATE: return "LPS_ERR_STATE";
+    case LPS_ERR_UNSUPPORTED: return "LPS_ERR_UNSUPPORTED";
+    default: return "LPS_ERR_UNKNOWN";
+  }
+}
+
+int lps_params_init(lps_params* p) {
+  if (!p) return LPS_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->layout = LPS_LAYOUT_SLICES;
+  p->fft_z = 1;
+  p->wavelet_levels = 3;
+  p->max_iters = 50;
+  p->lambda_L_rel = 0.01;
+  p->lambda_S_rel = 0.005;
+  p->lambda_p = 0.5;
+  p->rank_tau = 1e-3;
+  p->tol = 0.0;
+  p->precision = LPS_FP32;
+  p->eig_precision = LPS_EIG_FP32;
+  p->support_rule = LPS_SUPPORT_THRESHOLD;
+  p->recursive = 0;
+  return LPS_OK;
+}
+
+size_t lps_support_words(const lps_params* p) {
+  if (!p) return 0;
+  return (size_t)p->nx * p->ny * p->nz / 32;
+}
+
+int lps_estimate_device_bytes(const lps_params* p, size_t* bytes) {
+  Geom g;
+  int rc = validate(p, &g);
+  if (rc) return rc;
+  ARG(bytes != nullptr, "bytes is NULL");
+  const size_t N = (size_t)g.N;
+  const size_t m = (size_t)((g.plane / 2 + 1) & ~1);   // first frame at 50% of the lines
+  size_t b = 0;
+  b += 4 * N * 8;                              // X, L, S, recon
+  b += (size_t)g.ncoil * N * 8;                // coils
+  b += 3 * ((size_t)g.nx * g.ncoil * m + 4) * 8;   // hybrid data, k-space staging, scratch
+  b += (size_t)g.nx * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
+  b += (size_t)g.nx * 4 + (size_t)g.ntiles * 16 + 2 * N / 8;
+  b += (size_t)(p->max_iters + 2) * sizeof(IterRec) + 4096;
+  *bytes = b;
+  return LPS_OK;
+}
+
+int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
+  ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  Geom g;
+  int rc = validate(p, &g);
+  if (rc) return rc;
+  lps_plan* P = new lps_plan();
+  P->p = *p;
+  P->g = g;
+  P->st = (cudaStream_t)stream;
+  const size_t N = (size_t)g.N;
+  auto fail = [&](int r) {
+    free_plan(P);
+    return r;
+  };
+  if ((rc = dalloc(P, &P->X, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->L, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->S, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->R, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->istage, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->coils, N * g.ncoil))) return fail(rc);
+  if ((rc = dalloc(P, &P->W, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = dalloc(P, &P->V, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = dalloc(P, &P->gram_part, (size_t)g.nx * g.nc * g.nc))) return fail(rc);
+  if ((rc = dalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
+  if ((rc = dalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
+  if ((rc = dalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
+  if ((rc = dalloc(P, &P->lines, (size_t)g.plane))) return fail(rc);
+  if ((rc = dalloc(P, &P->dc_part, (size_t)g.nx))) return fail(rc);
+  if ((rc = dalloc(P, &P->lrs_part, (size_t)g.ntiles * 4))) return fail(rc);
+  if ((rc = dalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
+  if ((rc = dalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
+  if ((rc = dalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
+  if ((rc = dalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
+  if ((rc = dalloc(P, &P->persist, 1))) return fail(rc);
+  if ((rc = dalloc(P, &P->ctrl, 1))) return fail(rc);
+  if ((rc = dalloc(P, &P->hist, (size_t)p->max_iters + 2))) return fail(rc);
+  if (cudaMallocHost((void**)&P->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
+      cudaMallocHost((void**)&P->h_persist, sizeof(DevPersist)) != cudaSuccess ||
+      cudaMallocHost((void**)&P->h_lines, (size_t)g.plane * sizeof(int)) != cudaSuccess) {
+    set_err("pinned host allocation failed");
+    return fail(LPS_ERR_OOM);
+  }
+  std::memset(P->h_persist, 0, sizeof(DevPersist));
+  if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+    set_err("stream creation failed");
+    return fail(LPS_ERR_CUDA);
+  }
+  auto up = [&](float2* d, int n) -> int {
+    std::vector<float2> t = twiddles(n);
+    CK(cudaMemcpy(d, t.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
+    return LPS_OK;
+  };
+  if ((rc = up(P->tw_x, g.nx)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.nz))) return fail(rc);
+  if (cudaMemset(P->persist, 0, sizeof(DevPersist)) != cudaSuccess ||
+      cudaMemset(P->ctrl, 0, sizeof(DevCtrl)) != cudaSuccess ||
+      cudaMemset(P->dc_part, 0, g.nx * sizeof(float)) != cudaSuccess ||
+      cudaMemset(P->lrs_part, 0, g.ntiles * 4 * sizeof(float)) != cudaSuccess ||
+      cudaMemset(P->sup_prior, 0, support_words(g) * 4) != cudaSuccess ||
+      cudaMemset(P->sup_out, 0, support_words(g) * 4) != cudaSuccess) {
+    set_err("device memset failed");
+    return fail(LPS_ERR_CUDA);
+  }
+  *out = P;
+  return LPS_OK;
+}
+
+int lps_plan_destroy(lps_plan* P) {
+  if (!P) return LPS_OK;
+  if (P->st) cudaStreamSynchronize(P->st);
+  return free_plan(P);
+}
+
+int lps_set_stream(lps_plan* P, void* stream) {
+  ARG(P != nullptr, "plan is NULL");
+  P->st = (cudaStream_t)stream;
+  return LPS_OK;
+}
+
+int lps_plan_device_bytes(const lps_plan* P, size_t* bytes) {
+  ARG(P != nullptr && bytes != nullptr, "NULL argument");
+  *bytes = P->dev_bytes;
+  return LPS_OK;
+}
+
+int lps_set_coils(lps_plan* P, const void* coils) {
+  ARG(P != nullptr && coils != nullptr, "NULL argument");
+  CK(cudaMemcpyAsync(P->coils, coils, (size_t)P->g.N * P->g.ncoil * sizeof(float2), cudaMemcpyDefault,
+                     P->st));
+  P->have_coils = true;
+  return LPS_OK;
+}
+
+int lps_set_mask(lps_plan* P, const uint8_t* mask, int* nlines) {
+  ARG(P != nullptr && mask != nullptr, "NULL argument");
+  const int ny = P->g.ny, nz = P->g.nz;
+  std::vector<uint8_t> hbuf;
+  const uint8_t* h = mask;
+  if (is_device_ptr(mask)) {
+    hbuf.resize((size_t)ny * nz);
+    CK(cudaMemcpyAsync(hbuf.data(), mask, hbuf.size(), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+    h = hbuf.data();
+  }
+  int m = 0;
+  for (size_t i = 0; i < (size_t)ny * nz; ++i) m += h[i] != 0;
+  ARG(m > 0, "mask has no sampled entry");
+  int rc = ensure_lines(P, m);
+  if (rc) return rc;
+  if ((rc = wait_upload(P))) return rc;
+  int k = 0;
+  for (int a = 0; a < nz; ++a)
+    for (int ky = 0; ky < ny; ++ky)
+      if (h[(size_t)a * ny + ky]) P->h_lines[k++] = a * P->g.nyp + ky;
+  CK(cudaMemcpyAsync(P->lines, P->h_lines, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, P->st));
+  P->nlines = m;
+  P->h_persist->nlines = m;
+  if ((rc = upload_persist(P))) return rc;
+  P->have_mask = true;
+  P->have_data = false;
+  P->state_ready = false;
+  if (nlines) *nlines = m;
+  return LPS_OK;
+}
+
+int lps_set_data(lps_plan* P, const void* kdata, int nlines) {
+  ARG(P != nullptr && kdata != nullptr, "NULL argument");
+  if (!P->have_mask) {
+    set_err("set_mask must precede set_data");
+    return LPS_ERR_STATE;
+  }
+  ARG(nlines == P->nlines, "nlines %d does not match the mask (%d lines)", nlines, P->nlines);
+  const void* src = kdata;
+  if (!is_device_ptr(kdata)) {
+    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * nlines * P->g.nx * sizeof(float2),
+                       cudaMemcpyDefault, P->st));
+    src = P->kstage;
+  }
+  XfftArgs a{};
+  a.g = P->g;
+  a.in = (const float2*)src;
+  a.out = P->dhyb;
+  a.tw_x = P->tw_x;
+  a.persist = P->persist;
+  a.inverse = 1;
+  LK(launch_xfft(a, P->st));
+  P->have_data = true;
+  P->state_ready = false;
+  return LPS_OK;
+}
+
+int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev) {
+  ARG(P != nullptr, "plan is NULL");
+  if (support)
+    CK(cudaMemcpyAsync(P->sup_prior, support, support_words(P->g) * sizeof(uint32_t), cudaMemcpyDefault,
+                       P->st));
+  if (sigma_prev)
+    CK(cudaMemcpyAsync(P->sigma_prev, sigma_prev, P->g.nc * sizeof(double), cudaMemcpyDefault, P->st));
+  int rc = wait_upload(P);
+  if (rc) return rc;
+  P->h_persist->has_sup = support ? 1 : 0;
+  P->h_persist->has_sigma = sigma_prev ? 1 : 0;
+  return upload_persist(P);
+}
+
+int lps_clear_prior(lps_plan* P) { return lps_set_prior(P, nullptr, nullptr); }
+
+int lps_iterate(lps_plan* P, int n_iters, lps_stats* stats) {
+  int rc = need_ready(P);
+  if (rc) return rc;
+  ARG(n_iters >= 0 && P->iters_done + n_iters <= P->p.max_iters,
+      "n_iters out of range (done %d, max_iters %d)", P->iters_done, P->p.max_iters);
+  if (!P->state_ready) {
+    if ((rc = enqueue_init(P, P->st))) return rc;
+    P->iters_done = 0;
+    P->state_ready = true;
+  }
+  for (int i = 0; i < n_iters; ++i) {
+    ++P->iters_done;
+    if ((rc = enqueue_iter(P, P->iters_done, P->st))) return rc;
+  }
+  if (P->iters_done > 0 && (rc = enqueue_finalize(P, P->iters_done, P->st))) return rc;
+  return read_stats(P, stats);
+}
+
+int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S, uint32_t* out_support,
+                          double* out_sigma, lps_stats* stats) {
+  int rc = need_ready(P);
+  if (rc) return rc;
+  if ((rc = build_graph(P))) return rc;
+  CK(cudaGraphLaunch(P->gexec, P->st));
+  P->state_ready = true;
+  P->iters_done = P->p.max_iters;
+  if (P->p.recursive) {
+    if ((rc = wait_upload(P))) return rc;
+    P->h_persist->has_sup = 1;
+    P->h_persist->has_sigma = 1;
+  }
+  const size_t img = (size_t)P->g.N * sizeof(float2);
+  bool host = false;
+  if (out_recon) {
+    float2* dst = is_device_ptr(out_recon) ? (float2*)out_recon : P->R;
+    LK(launch_combine(P->L, P->S, dst, P->g.N, P->st));
+    if (dst == P->R && (rc = copy_out(P, out_recon, P->R, img, &host))) return rc;
+  }
+  if ((rc = copy_out(P, out_L, P->L, img, &host))) return rc;
+  if ((rc = copy_out(P, out_S, P->S, img, &host))) return rc;
+  if ((rc = copy_out(P, out_support, P->sup_out, support_words(P->g) * 4, &host))) return rc;
+  if ((rc = copy_out(P, out_sigma, P->sigma_out, P->g.nc * sizeof(double), &host))) return rc;
+  if (stats) {
+    if ((rc = read_stats(P, stats))) return rc;
+    P->iters_done = stats->iters;
+  } else if (host) {
+    CK(cudaStreamSynchronize(P->st));
+  }
+  return LPS_OK;
+}
+
+int lps_set_profiling(lps_plan* P, int on) {
+  ARG(P != nullptr, "plan is NULL");
+  if ((on != 0) != P->profiling) {
+    P->profiling = on != 0;
+    P->graph_valid = false;
+  }
+  return LPS_OK;
+}
+
+int lps_get_kernel_times(lps_plan* P, lps_kernel_times* out) {
+  ARG(P != nullptr && out != nullptr, "NULL argument");
+  std::memset(out, 0, sizeof(*out));
+  if (!P->profiling || !P->graph_valid) return LPS_OK;
+  CK(cudaStreamSynchronize(P->st));
+  for (int i = 0; i < P->ev_used; ++i) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, P->ev[2 * i], P->ev[2 * i + 1]));
+    out->launches[P->ev_class[i]] += 1;
+    out->ms[P->ev_class[i]] += ms;
+  }
+  return LPS_OK;
+}
+
+int lps_get_history(lps_plan* P, lps_iter_record* out, int max, int* count) {
+  ARG(P != nullptr && out != nullptr && count != nullptr && max >= 0, "bad argument");
+  CK(cudaMemcpyAsync(P->h_ctrl, P->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  const int n = std::min(max, P->h_ctrl->iters_done);
+  std::vector<IterRec> r(n > 0 ? n : 1);
+  if (n > 0) CK(cudaMemcpy(r.data(), P->hist, n * sizeof(IterRec), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < n; ++i) {
+    out[i].resid_norm2 = r[i].resid2;
+    out[i].nuclear = r[i].nuclear;
+    out[i].l1_off_support = r[i].l1;
+    out[i].objective = r[i].objective;
+    out[i].rel_change = r[i].rel_change;
+    out[i].rank = r[i].rank;
+    out[i].pad = 0;
+  }
+  *count = n;
+  return LPS_OK;
+}
+
+int lps_get_state(lps_plan* P, void* X, void* L, void* S) {
+  ARG(P != nullptr, "plan is NULL");
+  const size_t img = (size_t)P->g.N * sizeof(float2);
+  bool host = false;
+  int rc;
+  if ((rc = copy_out(P, X, P->X, img, &host))) return rc;
+  if ((rc = copy_out(P, L, P->L, img, &host))) return rc;
+  if ((rc = copy_out(P, S, P->S, img, &host))) return rc;
+  if (host) CK(cudaStreamSynchronize(P->st));
+  return LPS_OK;
+}
+
+int lps_get_support(lps_plan* P, uint32_t* support, double* sigma) {
+  ARG(P != nullptr, "plan is NULL");
+  bool host = false;
+  int rc;
+  if ((rc = copy_out(P, support, P->sup_out, support_words(P->g) * 4, &host))) return rc;
+  if ((rc = copy_out(P, sigma, P->sigma_out, P->g.nc * sizeof(double), &host))) return rc;
+  if (host) CK(cudaStreamSynchronize(P->st));
+  return LPS_OK;
+}
+
+int lps_set_state(lps_plan* P, const void* X, const void* S, const void* L_prev, double lambda_L,
+                  double lambda_S, int iters_done) {
+  ARG(P != nullptr && X != nullptr && S != nullptr, "NULL argument");
+  ARG(iters_done >= 0 && iters_done < P->p.max_iters, "iters_done out of range");
+  ARG(std::isfinite(lambda_L) && lambda_L >= 0 && std::isfinite(lambda_S) && lambda_S >= 0, "bad lambdas");
+  if (!P->have_coils || !P->have_mask || !P->have_data) {
+    set_err("set_coils, set_mask and set_data must precede set_state");
+    return LPS_ERR_STATE;
+  }
+  const size_t img = (size_t)P->g.N * sizeof(float2);
+  CK(cudaMemcpyAsync(P->X, X, img, cudaMemcpyDefault, P->st));
+  CK(cudaMemcpyAsync(P->S, S, img, cudaMemcpyDefault, P->st));
+  CK(cudaMemcpyAsync(P->L, L_prev ? L_prev : X, img, cudaMemcpyDefault, P->st));
+  CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), P->st));
+  CK(cudaMemsetAsync(P->dc_part, 0, P->g.nx * sizeof(float), P->st));
+  CK(cudaMemsetAsync(P->lrs_part, 0, P->g.ntiles * 4 * sizeof(float), P->st));
+  DevCtrl c{};
+  c.lambda_L = (float)lambda_L;
+  c.lambda_S = (float)lambda_S;
+  c.lambdas_set = 1;
+  c.sigma_max = 0.0;
+  *P->h_ctrl = c;
+  CK(cudaMemcpyAsync(P->ctrl, P->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, P->st));
+  LK(launch_gram_plane(P->X, P->S, P->g, P->gram_part, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  P->state_ready = true;
+  P->iters_done = iters_done;
+  return LPS_OK;
+}
+
+int lps_forward(lps_plan* P, const void* image, void* kdata) {
+  ARG(P != nullptr && image != nullptr && kdata != nullptr, "NULL argument");
+  if (!P->have_coils || !P->have_mask) {
+    set_err("set_coils and set_mask must precede lps_forward");
+    return LPS_ERR_STATE;
+  }
+  const size_t img = (size_t)P->g.N * sizeof(float2);
+  const float2* src = (const float2*)image;
+  if (!is_device_ptr(image)) {
+    CK(cudaMemcpyAsync(P->istage, image, img, cudaMemcpyDefault, P->st));
+    src = P->istage;
+  }
+  DcArgs a = dc_args(P);
+  a.L = src;
+  a.hyb_out = P->hscratch;
+  LK(launch_dc(a, kDcForward, P->st));
+  const bool dev = is_device_ptr(kdata);
+  XfftArgs x{};
+  x.g = P->g;
+  x.in = P->hscratch;
+  x.out = dev ? (float2*)kdata : P->kstage;
+  x.tw_x = P->tw_x;
+  x.persist = P->persist;
+  x.inverse = 0;
+  LK(launch_xfft(x, P->st));
+  if (!dev) {
+    CK(cudaMemcpyAsync(kdata, P->kstage, (size_t)P->g.ncoil * P->nlines * P->g.nx * sizeof(float2),
+                       cudaMemcpyDefault, P->st));
+    CK(cudaStreamSynchronize(P->st));
+  }
+  return LPS_OK;
+}
+
+int lps_adjoint(lps_plan* P, const void* kdata, void* image) {
+  ARG(P != nullptr && image != nullptr && kdata != nullptr, "NULL argument");
+  if (!P->have_coils || !P->have_mask) {
+    set_err("set_coils and set_mask must precede lps_adjoint");
+    return LPS_ERR_STATE;
+  }
+  const float2* src = (const float2*)kdata;
+  if (!is_device_ptr(kdata)) {
+    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * P->nlines * P->g.nx * sizeof(float2),
+                       cudaMemcpyDefault, P->st));
+    src = P->kstage;
+  }
+  XfftArgs x{};
+  x.g = P->g;
+  x.in = src;
+  x.out = P->hscratch;
+  x.tw_x = P->tw_x;
+  x.persist = P->persist;
+  x.inverse = 1;
+  LK(launch_xfft(x, P->st));
+  const bool dev = is_device_ptr(image);
+  DcArgs a = dc_args(P);
+  a.dhyb = P->hscratch;
+  a.X = dev ? (float2*)image : P->istage;
+  LK(launch_dc(a, kDcAdjoint, P->st));
+  if (!dev) {
+    CK(cudaMemcpyAsync(image, P->istage, (size_t)P->g.N * sizeof(float2), cudaMemcpyDefault, P->st));
+    CK(cudaStreamSynchronize(P->st));
+  }
+  return LPS_OK;
+}
+
+int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm2) {
+  ARG(P != nullptr && Z != nullptr && X != nullptr, "NULL argument");
+  int rc = need_ready(P);
+  if (rc) return rc;
+  const size_t img = (size_t)P->g.N * sizeof(float2);
+  const float2* src = (const float2*)Z;
+  if (!is_device_ptr(Z)) {
+    CK(cudaMemcpyAsync(P->istage, Z, img, cudaMemcpyDefault, P->st));
+    src = P->istage;
+  }
+  const bool dev = is_device_ptr(X);
+  float2* dst = dev ? (float2*)X : P->R;
+  DcArgs a = dc_args(P);
+  a.L = src;
+  a.S = nullptr;
+  a.X = dst;
+  a.dc_part = P->dc_part;
+  LK(launch_dc(a, kDcUpdate, P->st));
+  if (!dev) CK(cudaMemcpyAsync(X, P->R, img, cudaMemcpyDefault, P->st));
+  if (resid_norm2) {
+    std::vector<float> part(P->g.nx);
+    CK(cudaMemcpyAsync(part.data(), P->dc_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+    double s = 0;
+    for (float v : part) s += v;
+    *resid_norm2 = s;
+  } else if (!dev) {
+    CK(cudaStreamSynchronize(P->st));
+  }
+  P->state_ready = false;
+  return LPS_OK;
+}
+
+// Checkpoint layout: header, prior support words, prior sigma, L, S, X, lambdas.
+struct CkptHeader {
+  uint32_t magic, version;
+  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done;
+  double lambda_L, lambda_S;
+};
+
+int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
+  ARG(P != nullptr && bytes != nullptr, "NULL argument");
+  const size_t w = support_words(P->g), img = (size_t)P->g.N * sizeof(float2);
+  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img;
+  if (!buf) {
+    *bytes = need;
+    return LPS_OK;
+  }
+  ARG(*bytes >= need, "buffer too small (%zu < %zu)", *bytes, need);
+  CK(cudaMemcpyAsync(P->h_ctrl, P->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, P->st));
+  CK(cudaStreamSynchronize(P->st));
+  CkptHeader h{0x4c50531a, 1, P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.J, P->h_persist->has_sup,
+               P->h_persist->has_sigma, P->iters_done, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
+  unsigned char* o = (unsigned char*)buf;
+  std::memcpy(o, &h, sizeof(h));
+  o += sizeof(h);
+  CK(cudaMemcpy(o, P->sup_prior, w * 4, cudaMemcpyDeviceToHost));
+  o += w * 4;
+  CK(cudaMemcpy(o, P->sigma_prev, P->g.nc * sizeof(double), cudaMemcpyDeviceToHost));
+  o += P->g.nc * sizeof(double);
+  CK(cudaMemcpy(o, P->L, img, cudaMemcpyDeviceToHost));
+  o += img;
+  CK(cudaMemcpy(o, P->S, img, cudaMemcpyDeviceToHost));
+  o += img;
+  CK(cudaMemcpy(o, P->X, img, cudaMemcpyDeviceToHost));
+  *bytes = need;
+  return LPS_OK;
+}
+
+int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
+  ARG(P != nullptr && buf != nullptr, "NULL argument");
+  const size_t w = support_words(P->g), img = (size_t)P->g.N * sizeof(float2);
+  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img;
+  ARG(bytes >= need, "checkpoint too small");
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  ARG(h.magic == 0x4c50531a && h.version == 1, "not a checkpoint of this library");
+  ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J, "checkpoint shape mismatch");
+  const unsigned char* i = (const unsigned char*)buf + sizeof(h);
+  CK(cudaStreamSynchronize(P->st));
+  CK(cudaMemcpy(P->sup_prior, i, w * 4, cudaMemcpyHostToDevice));
+  i += w * 4;
+  CK(cudaMemcpy(P->sigma_prev, i, P->g.nc * sizeof(double), cudaMemcpyHostToDevice));
+  i += P->g.nc * sizeof(double);
+  CK(cudaMemcpy(P->L, i, img, cudaMemcpyHostToDevice));
+  i += img;
+  CK(cudaMemcpy(P->S, i, img, cudaMemcpyHostToDevice));
+  i += img;
+  CK(cudaMemcpy(P->X, i, img, cudaMemcpyHostToDevice));
+  int rc = wait_upload(P);
+  if (rc) return rc;
+  P->h_persist->has_sup = h.has_sup;
+  P->h_persist->has_sigma = h.has_sigma;
+  return upload_persist(P);
+}
+
+}  // extern "C"

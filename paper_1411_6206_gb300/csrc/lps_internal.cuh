@@ -1,0 +1,445 @@
+// Internal declarations shared by the kernels and the host side of liblps.so.
+// Device helpers: complex arithmetic, bounded mbarrier waits, 1D TMA bulk copies,
+// shared-memory Stockham FFT passes and deterministic block reductions.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace lps {
+
+constexpr int kThreads = 256;          // threads per CTA of the per-plane and per-tile kernels
+constexpr int kMaxPasses = 8;          // radix passes per transform length
+constexpr int kTile = 8;               // in-plane tile edge of the low-rank/sparse kernel
+constexpr int kMaxNc = 32;             // largest Casorati column count
+constexpr long long kSpinLimit = 1LL << 26;   // bounded waits: iterations before giving up
+
+// Status bits written by kernels into DevCtrl::err.
+constexpr int kErrTimeout = 1;
+constexpr int kErrNonfinite = 2;
+
+struct FftPlan {
+  int n;
+  int np;                   // number of passes
+  int r[kMaxPasses];        // radix of each pass, first to last
+};
+
+// Per-plan values that persist across frames (written by the host API).
+struct DevPersist {
+  int nlines;               // sampled lines of the current mask
+  int has_sup;              // prior support present (nonzero)
+  int has_sigma;            // prior singular values present (nonzero)
+  int pad;
+};
+
+// Per-frame control block (zeroed at the start of every frame).
+struct DevCtrl {
+  float lambda_L, lambda_S;
+  unsigned haar_max_bits;   // max |T(X_0)| as float bits (non-negative, order-preserving)
+  int lambdas_set;
+  int converged;
+  int iters_done;
+  int err;
+  int v_valid;              // warm-start eigenvectors available
+  int rank_cur;
+  int pad0;
+  double sigma_max;
+  double nuclear_cur;
+};
+
+struct IterRec {
+  double resid2, nuclear, l1, objective, rel_change;
+  int rank, pad;
+};
+
+struct Geom {
+  int nx, ny, nz, ncoil;
+  int nc;                   // Casorati columns (= nz)
+  int plane;                // ny*nz, elements of one x-plane
+  int nyp;                  // padded row stride of the FFT buffers (odd)
+  int planeP;               // nz*nyp rounded up to even
+  int mpad;                 // row stride (elements) of the hybrid data per (x, coil)
+  int fft_z;                // 3D (1) or per-slice 2D (0) encode
+  int J;                    // Haar levels
+  int ntiles;               // (nx/8)*(ny/8)
+  long long N;              // nx*ny*nz
+  float scale_yz;           // 1/sqrt(ny*nz) (fft_z) or 1/sqrt(ny)
+  float scale_x;            // 1/sqrt(nx)
+  FftPlan py, pz, px;
+};
+
+// ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
+enum DcMode { kDcUpdate = 0, kDcAdjoint = 1, kDcForward = 2 };
+
+struct DcArgs {
+  Geom g;
+  const float2* L;          // update: Z = L + S;  forward: image
+  const float2* S;          // update: S (Gram of X - S)
+  float2* X;                // update/adjoint: output X
+  float2* L_out;            // adjoint: also write X_0 here (L_0 := X_0)
+  float2* S_out;            // adjoint: zero S
+  float2* recon;            // update: optional copy of Z = L + S
+  const float2* coils;      // [ncoil][nz][nx][ny]
+  const float2* dhyb;       // [nx][ncoil][mpad] hybrid-space samples
+  float2* hyb_out;          // forward: [nx][ncoil][mpad]
+  const int* lines;         // padded in-plane position kz*nyp + ky of each line
+  const float2* tw_y;
+  const float2* tw_z;
+  float2* gram_part;        // [nx][nc][nc]; nullptr = skip
+  float* dc_part;           // [nx] residual-norm partials; nullptr = skip
+  const DevPersist* persist;
+  DevCtrl* ctrl;            // nullptr = no convergence gating
+};
+
+// ---- hybrid transform along x --------------------------------------------------------
+struct XfftArgs {
+  Geom g;
+  const float2* in;
+  float2* out;
+  const float2* tw_x;
+  const DevPersist* persist;
+  int inverse;              // 1: k-space [c][l][kx] -> hybrid [x][c][l]; 0: the reverse
+};
+
+// ---- low-rank reprojection + support-aware sparse step (one CTA per 8x8 tile) ------
+struct LrsArgs {
+  Geom g;
+  const float2* X;
+  float2* L;                // in: L_prev, out: L_new (in place)
+  float2* S;                // in: S_old, out: S_new (in place)
+  const float2* W;          // [nc][nc]
+  const uint32_t* sup_prior;
+  uint32_t* sup_out;        // nullptr = do not write the support bitmap
+  float* lrs_part;          // [ntiles][4]: l1 off-support, ||dZ||^2, ||Z_old||^2, support count
+  const DevPersist* persist;
+  DevCtrl* ctrl;
+  int support_rule;
+  int haar_max_only;        // 1: only max |T(X)| into ctrl->haar_max_bits
+};
+
+// ---- Gram reduction + eigendecomposition + SVT + prior pull (one CTA) --------------
+struct EigArgs {
+  Geom g;
+  const float2* gram_part;  // [nparts][nc][nc]
+  int nparts;
+  const float* dc_part;     // [nx]
+  const float* lrs_part;    // [ntiles][4]
+  float2* W;                // [nc][nc]
+  float2* V;                // [nc][nc] warm-start eigenvectors
+  const double* sigma_prev;
+  double* sigma_out;        // sigma'' in rank order
+  IterRec* hist;
+  const DevPersist* persist;
+  DevCtrl* ctrl;
+  double lambda_L_rel, lambda_S_rel, lambda_p, rank_tau, tol;
+  int iter;                 // iteration k whose SVT this launch computes (1-based)
+  int finalize;             // 1: only record the stats of iteration `iter`-1
+  int eig_fp64;
+};
+
+// Host-side launchers (return cudaGetLastError()).
+cudaError_t launch_dc(const DcArgs& a, int mode, cudaStream_t st);
+cudaError_t launch_xfft(const XfftArgs& a, cudaStream_t st);
+cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st);
+cudaError_t launch_eig(const EigArgs& a, cudaStream_t st);
+size_t dc_smem_bytes(const Geom& g);
+size_t xfft_smem_bytes(const Geom& g);
+int dc_ept(const Geom& g);
+
+}  // namespace lps
+
+#ifdef __CUDACC__
+namespace lps {
+
+// ---- complex helpers ---------------------------------------------------------------
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+// conj(a) * b
+__device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+  return make_float2(fmaf(a.x, b.x, a.y * b.y), fmaf(a.x, b.y, -a.y * b.x));
+}
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ float cabs2(float2 a) { return fmaf(a.x, a.x, a.y * a.y); }
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+// multiply by -i (forward) or +i (inverse)
+__device__ __forceinline__ float2 mul_mi(float2 a, bool inv) {
+  return inv ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// ---- shared-memory addresses, mbarriers and 1D bulk copies (TMA) ----------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: returns false (and records kErrTimeout) if the phase never completes.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (i > 64) __nanosleep(64);
+  }
+  if (err) atomicOr(err, kErrTimeout);
+  return false;
+}
+
+// ---- deterministic reductions -------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+// Sum over the block in a fixed order; result valid in thread 0. `red` holds >= 32 floats.
+__device__ __forceinline__ float block_sum(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_sum(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r += red[i];
+  }
+  return r;
+}
+__device__ __forceinline__ float block_max(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  v = warp_max(v);
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  if (threadIdx.x == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    for (int i = 0; i < nw; ++i) r = fmaxf(r, red[i]);
+  }
+  return r;
+}
+
+// ---- small DFTs in registers (forward: exp(-2 pi i rs/R), inverse: +) -----------------
+__device__ __forceinline__ void dft2(float2& a, float2& b) {
+  float2 t = a;
+  a = cadd(t, b);
+  b = csub(t, b);
+}
+__device__ __forceinline__ void dft4(float2* v, bool inv) {
+  float2 t0 = cadd(v[0], v[2]), t1 = csub(v[0], v[2]);
+  float2 t2 = cadd(v[1], v[3]), t3 = mul_mi(csub(v[1], v[3]), inv);
+  v[0] = cadd(t0, t2);
+  v[2] = csub(t0, t2);
+  v[1] = cadd(t1, t3);
+  v[3] = csub(t1, t3);
+}
+// v[0..7]: two radix-4 DFTs on even/odd samples and one radix-2 stage.
+__device__ __forceinline__ void dft8(float2* v, bool inv) {
+  const float h = 0.70710678118654752f;   // sqrt(2)/2
+  float2 e[4] = {v[0], v[2], v[4], v[6]};
+  float2 o[4] = {v[1], v[3], v[5], v[7]};
+  dft4(e, inv);
+  dft4(o, inv);
+  // twiddles w8^k, k = 0..3: 1, h(1 -+ i), -+i, h(-1 -+ i)
+  float2 o1 = inv ? make_float2(h * (o[1].x - o[1].y), h * (o[1].x + o[1].y))
+                  : make_float2(h * (o[1].x + o[1].y), h * (o[1].y - o[1].x));
+  float2 o2 = mul_mi(o[2], inv);
+  float2 o3 = inv ? make_float2(-h * (o[3].x + o[3].y), h * (o[3].x - o[3].y))
+                  : make_float2(h * (o[3].y - o[3].x), -h * (o[3].x + o[3].y));
+  v[0] = cadd(e[0], o[0]);
+  v[4] = csub(e[0], o[0]);
+  v[1] = cadd(e[1], o1);
+  v[5] = csub(e[1], o1);
+  v[2] = cadd(e[2], o2);
+  v[6] = csub(e[2], o2);
+  v[3] = cadd(e[3], o3);
+  v[7] = csub(e[3], o3);
+}
+// v[0..15]: two radix-8 DFTs on even/odd samples and one radix-2 stage with w16^k.
+__device__ __forceinline__ void dft16(float2* v, bool inv) {
+  float2 e[8], o[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    e[i] = v[2 * i];
+    o[i] = v[2 * i + 1];
+  }
+  dft8(e, inv);
+  dft8(o, inv);
+  // cos(k pi/8), sin(k pi/8) for k = 0..7
+  const float C[8] = {1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f,
+                      0.0f, -0.38268343236508977f, -0.70710678118654752f, -0.92387953251128674f};
+  const float S[8] = {0.0f, 0.38268343236508977f, 0.70710678118654752f, 0.92387953251128674f,
+                      1.0f, 0.92387953251128674f, 0.70710678118654752f, 0.38268343236508977f};
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    float2 w = make_float2(C[k], inv ? S[k] : -S[k]);
+    float2 t = cmul(o[k], w);
+    v[k] = cadd(e[k], t);
+    v[k + 8] = csub(e[k], t);
+  }
+}
+// Generic radix-R DFT, roots taken from the length-n table (R divides n).
+template <int R>
+__device__ __forceinline__ void dft_generic(float2* v, bool inv, const float2* tw, int n) {
+  float2 out[R];
+  const int st = n / R;
+#pragma unroll
+  for (int s = 0; s < R; ++s) {
+    float2 acc = v[0];
+#pragma unroll
+    for (int r = 1; r < R; ++r) {
+      float2 w = tw[((r * s) % R) * st];
+      if (inv) w.y = -w.y;
+      acc = cadd(acc, cmul(v[r], w));
+    }
+    out[s] = acc;
+  }
+#pragma unroll
+  for (int s = 0; s < R; ++s) v[s] = out[s];
+}
+
+template <int R>
+__device__ __forceinline__ void dft_reg(float2* v, bool inv, const float2* tw, int n) {
+  if constexpr (R == 2) {
+    dft2(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4(v, inv);
+  } else if constexpr (R == 8) {
+    dft8(v, inv);
+  } else if constexpr (R == 16) {
+    dft16(v, inv);
+  } else {
+    dft_generic<R>(v, inv, tw, n);
+  }
+}
+
+// One Stockham pass over `nb` transforms of length n held in shared memory.
+// Element i of transform b is at base[b*bs + i*es]. Ns = product of the radices of the
+// previous passes. Twiddle table tw[q] = exp(-2 pi i q / n). Batch index runs fastest
+// across threads.
+template <int R>
+__device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2* __restrict__ out, int n,
+                                           int Ns, int nb, int es, int bs, const float2* __restrict__ tw,
+                                           bool inv) {
+  const int nbf = n / R;
+  const int total = nb * nbf;
+  const int tws = n / (Ns * R);
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = t % nb;
+    const int j = t / nb;
+    const int k = j % Ns;
+    const float2* src = in + b * bs;
+    float2 v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[(j + r * nbf) * es];
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        float2 w = tw[r * k * tws];
+        if (inv) w.y = -w.y;
+        v[r] = cmul(v[r], w);
+      }
+    }
+    dft_reg<R>(v, inv, tw, n);
+    const int idxD = (j / Ns) * Ns * R + k;
+    float2* dst = out + b * bs;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];
+  }
+}
+
+// Pass with a radix that has no register specialisation: one thread per output element.
+__device__ __forceinline__ void fft_pass_any(const float2* __restrict__ in, float2* __restrict__ out, int n,
+                                             int Ns, int R, int nb, int es, int bs,
+                                             const float2* __restrict__ tw, bool inv) {
+  const int nbf = n / R;
+  const int total = nb * n;
+  const int tws = n / (Ns * R);
+  const int st = n / R;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int b = t % nb;
+    const int rest = t / nb;
+    const int j = rest % nbf;
+    const int s = rest / nbf;
+    const int k = j % Ns;
+    const float2* src = in + b * bs;
+    float2 acc = make_float2(0.f, 0.f);
+    for (int r = 0; r < R; ++r) {
+      float2 v = src[(j + r * nbf) * es];
+      float2 w = tw[r * k * tws];
+      float2 u = tw[((r * s) % R) * st];
+      if (inv) {
+        w.y = -w.y;
+        u.y = -u.y;
+      }
+      acc = cadd(acc, cmul(cmul(v, w), u));
+    }
+    const int idxD = (j / Ns) * Ns * R + k;
+    out[b * bs + (idxD + s * Ns) * es] = acc;
+  }
+}
+
+__device__ __forceinline__ void fft_pass(const float2* in, float2* out, int n, int Ns, int R, int nb, int es,
+                                         int bs, const float2* tw, bool inv) {
+  switch (R) {
+    case 2: fft_pass_r<2>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 3: fft_pass_r<3>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 4: fft_pass_r<4>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 5: fft_pass_r<5>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 7: fft_pass_r<7>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 8: fft_pass_r<8>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    case 16: fft_pass_r<16>(in, out, n, Ns, nb, es, bs, tw, inv); break;
+    default: fft_pass_any(in, out, n, Ns, R, nb, es, bs, tw, inv); break;
+  }
+}
+
+// Full transform: passes ping-pong between *src and *dst (swapped after each pass); on
+// return *src holds the result. A __syncthreads() follows every pass.
+__device__ __forceinline__ void fft_run(float2** src, float2** dst, const FftPlan& p, int nb, int es, int bs,
+                                        const float2* tw, bool inv) {
+  int Ns = 1;
+  for (int i = 0; i < p.np; ++i) {
+    const int R = p.r[i];
+    fft_pass(*src, *dst, p.n, Ns, R, nb, es, bs, tw, inv);
+    __syncthreads();
+    float2* t = *src;
+    *src = *dst;
+    *dst = t;
+    Ns *= R;
+  }
+}
+
+}  // namespace lps
+#endif  // __CUDACC__

@@ -1,0 +1,364 @@
+"""Thin Python binding of liblps.so (include/lps_api.h): argument marshalling only.
+
+Every function here has the name of the C entry point without the ``lps_`` prefix and
+forwards to it; array arguments may be torch tensors (CUDA or CPU) or numpy arrays and are
+passed as raw pointers (the library accepts host or device memory). Every step of the
+reconstruction runs in the library's CUDA kernels; a missing library raises ImportError
+and there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "liblps.so")
+
+OK = 0
+ERR_INVALID_ARG = -1
+ERR_OOM = -2
+ERR_CUDA = -3
+ERR_TIMEOUT = -4
+ERR_NONFINITE = -5
+ERR_ADMISSION = -6
+ERR_STATE = -7
+ERR_UNSUPPORTED = -8
+
+EIG_FP32, EIG_FP64 = 0, 1
+SUPPORT_THRESHOLD, SUPPORT_NONZERO = 0, 1
+MAX_NC = 32
+
+
+class Params(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int), ("ncoil", C.c_int),
+                ("layout", C.c_int), ("fft_z", C.c_int), ("wavelet_levels", C.c_int),
+                ("max_iters", C.c_int),
+                ("lambda_L_rel", C.c_double), ("lambda_S_rel", C.c_double),
+                ("lambda_p", C.c_double), ("rank_tau", C.c_double), ("tol", C.c_double),
+                ("precision", C.c_int), ("eig_precision", C.c_int), ("support_rule", C.c_int),
+                ("recursive", C.c_int), ("reserved", C.c_int * 8)]
+
+
+class Stats(C.Structure):
+    _fields_ = [("iters", C.c_int), ("rank", C.c_int), ("support_count", C.c_longlong),
+                ("lambda_L", C.c_double), ("lambda_S", C.c_double), ("sigma_max", C.c_double),
+                ("resid_norm2", C.c_double), ("nuclear", C.c_double),
+                ("l1_off_support", C.c_double), ("objective", C.c_double),
+                ("rel_change", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class IterRecord(C.Structure):
+    _fields_ = [("resid_norm2", C.c_double), ("nuclear", C.c_double),
+                ("l1_off_support", C.c_double), ("objective", C.c_double),
+                ("rel_change", C.c_double), ("rank", C.c_int), ("pad", C.c_int)]
+
+
+class KernelTimes(C.Structure):
+    _fields_ = [("launches", C.c_int * 4), ("ms", C.c_double * 4)]
+
+    CLASSES = ("data_consistency", "lowrank_sparse", "eig_svt", "init")
+
+    def as_dict(self):
+        return {n: {"launches": self.launches[i], "ms": self.ms[i]} for i, n in enumerate(self.CLASSES)}
+
+
+class LpsError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {status_string(code)} ({code}): {msg}")
+        self.code = code
+
+
+_lib = None
+_VP = C.c_void_p
+_SIGS = {
+    "lps_version": ([], C.c_int),
+    "lps_last_error": ([], C.c_char_p),
+    "lps_status_string": ([C.c_int], C.c_char_p),
+    "lps_params_init": ([C.POINTER(Params)], C.c_int),
+    "lps_support_words": ([C.POINTER(Params)], C.c_size_t),
+    "lps_estimate_device_bytes": ([C.POINTER(Params), C.POINTER(C.c_size_t)], C.c_int),
+    "lps_plan_create": ([C.POINTER(Params), _VP, C.POINTER(_VP)], C.c_int),
+    "lps_plan_destroy": ([_VP], C.c_int),
+    "lps_set_stream": ([_VP, _VP], C.c_int),
+    "lps_plan_device_bytes": ([_VP, C.POINTER(C.c_size_t)], C.c_int),
+    "lps_set_mask": ([_VP, _VP, C.POINTER(C.c_int)], C.c_int),
+    "lps_set_coils": ([_VP, _VP], C.c_int),
+    "lps_set_data": ([_VP, _VP, C.c_int], C.c_int),
+    "lps_set_prior": ([_VP, _VP, _VP], C.c_int),
+    "lps_clear_prior": ([_VP], C.c_int),
+    "lps_iterate": ([_VP, C.c_int, C.POINTER(Stats)], C.c_int),
+    "lps_reconstruct_frame": ([_VP, _VP, _VP, _VP, _VP, _VP, C.POINTER(Stats)], C.c_int),
+    "lps_get_history": ([_VP, C.POINTER(IterRecord), C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "lps_get_state": ([_VP, _VP, _VP, _VP], C.c_int),
+    "lps_get_support": ([_VP, _VP, _VP], C.c_int),
+    "lps_set_state": ([_VP, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int], C.c_int),
+    "lps_forward": ([_VP, _VP, _VP], C.c_int),
+    "lps_adjoint": ([_VP, _VP, _VP], C.c_int),
+    "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
+    "lps_set_profiling": ([_VP, C.c_int], C.c_int),
+    "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
+    "lps_session_export": ([_VP, _VP, C.POINTER(C.c_size_t)], C.c_int),
+    "lps_session_import": ([_VP, _VP, C.c_size_t], C.c_int),
+}
+
+
+def load(path: str = LIB_PATH):
+    """Load liblps.so (built by paper_1411_6206_gb300.build) and declare its signatures."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1411_6206_gb300.build`")
+    lib = C.CDLL(path)
+    for name, (args, res) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    return list(_SIGS)
+
+
+def status_string(code: int) -> str:
+    return load().lps_status_string(code).decode()
+
+
+def last_error() -> str:
+    return load().lps_last_error().decode()
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise LpsError(rc, where, last_error())
+    return rc
+
+
+def ptr(a) -> Optional[int]:
+    """Raw address of a contiguous torch tensor / numpy array (None passes NULL)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError(f"unsupported array type {type(a)}")
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return int(stream)
+
+
+# ---- entry points -------------------------------------------------------------------
+
+def version() -> int:
+    return load().lps_version()
+
+
+def params_init(**kw) -> Params:
+    p = Params()
+    _check(load().lps_params_init(C.byref(p)), "params_init")
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def support_words(p: Params) -> int:
+    return load().lps_support_words(C.byref(p))
+
+
+def estimate_device_bytes(p: Params) -> int:
+    b = C.c_size_t()
+    _check(load().lps_estimate_device_bytes(C.byref(p), C.byref(b)), "estimate_device_bytes")
+    return b.value
+
+
+def plan_create(p: Params, stream=None) -> int:
+    h = _VP()
+    _check(load().lps_plan_create(C.byref(p), _stream(stream), C.byref(h)), "plan_create")
+    return h.value
+
+
+def plan_destroy(plan: int):
+    _check(load().lps_plan_destroy(plan), "plan_destroy")
+
+
+def set_stream(plan: int, stream):
+    _check(load().lps_set_stream(plan, _stream(stream)), "set_stream")
+
+
+def plan_device_bytes(plan: int) -> int:
+    b = C.c_size_t()
+    _check(load().lps_plan_device_bytes(plan, C.byref(b)), "plan_device_bytes")
+    return b.value
+
+
+def set_mask(plan: int, mask) -> int:
+    n = C.c_int()
+    _check(load().lps_set_mask(plan, ptr(mask), C.byref(n)), "set_mask")
+    return n.value
+
+
+def set_coils(plan: int, coils):
+    _check(load().lps_set_coils(plan, ptr(coils)), "set_coils")
+
+
+def set_data(plan: int, kdata, nlines: int):
+    _check(load().lps_set_data(plan, ptr(kdata), nlines), "set_data")
+
+
+def set_prior(plan: int, support=None, sigma=None):
+    _check(load().lps_set_prior(plan, ptr(support), ptr(sigma)), "set_prior")
+
+
+def clear_prior(plan: int):
+    _check(load().lps_clear_prior(plan), "clear_prior")
+
+
+def iterate(plan: int, n_iters: int) -> Stats:
+    s = Stats()
+    _check(load().lps_iterate(plan, n_iters, C.byref(s)), "iterate")
+    return s
+
+
+def reconstruct_frame(plan: int, recon=None, L=None, S=None, support=None, sigma=None,
+                      stats: bool = True) -> Optional[Stats]:
+    s = Stats() if stats else None
+    _check(load().lps_reconstruct_frame(plan, ptr(recon), ptr(L), ptr(S), ptr(support), ptr(sigma),
+                                        C.byref(s) if s is not None else None),
+           "reconstruct_frame")
+    return s
+
+
+def get_history(plan: int, max_records: int = 4096):
+    buf = (IterRecord * max_records)()
+    n = C.c_int()
+    _check(load().lps_get_history(plan, buf, max_records, C.byref(n)), "get_history")
+    return [{k: getattr(buf[i], k) for k, _ in IterRecord._fields_ if k != "pad"}
+            for i in range(n.value)]
+
+
+def get_state(plan: int, X=None, L=None, S=None):
+    _check(load().lps_get_state(plan, ptr(X), ptr(L), ptr(S)), "get_state")
+
+
+def get_support(plan: int, support=None, sigma=None):
+    _check(load().lps_get_support(plan, ptr(support), ptr(sigma)), "get_support")
+
+
+def set_state(plan: int, X, S, L_prev, lambda_L: float, lambda_S: float, iters_done: int = 0):
+    _check(load().lps_set_state(plan, ptr(X), ptr(S), ptr(L_prev), lambda_L, lambda_S, iters_done),
+           "set_state")
+
+
+def forward(plan: int, image, kdata):
+    _check(load().lps_forward(plan, ptr(image), ptr(kdata)), "forward")
+
+
+def adjoint(plan: int, kdata, image):
+    _check(load().lps_adjoint(plan, ptr(kdata), ptr(image)), "adjoint")
+
+
+def data_consistency(plan: int, Z, X) -> float:
+    r = C.c_double()
+    _check(load().lps_data_consistency(plan, ptr(Z), ptr(X), C.byref(r)), "data_consistency")
+    return r.value
+
+
+def set_profiling(plan: int, on: bool):
+    _check(load().lps_set_profiling(plan, int(bool(on))), "set_profiling")
+
+
+def get_kernel_times(plan: int) -> KernelTimes:
+    t = KernelTimes()
+    _check(load().lps_get_kernel_times(plan, C.byref(t)), "get_kernel_times")
+    return t
+
+
+def session_export(plan: int) -> bytes:
+    n = C.c_size_t()
+    _check(load().lps_session_export(plan, None, C.byref(n)), "session_export")
+    buf = C.create_string_buffer(n.value)
+    _check(load().lps_session_export(plan, buf, C.byref(n)), "session_export")
+    return buf.raw[: n.value]
+
+
+def session_import(plan: int, blob: bytes):
+    buf = C.create_string_buffer(blob, len(blob))
+    _check(load().lps_session_import(plan, buf, len(blob)), "session_import")
+
+
+class Plan:
+    """Owning handle over lps_plan with the same calls as methods."""
+
+    def __init__(self, nx, ny, nz, ncoil, stream=None, **kw):
+        self.params = params_init(nx=nx, ny=ny, nz=nz, ncoil=ncoil, **kw)
+        self.handle = plan_create(self.params, stream)
+        self.nlines = 0
+
+    @property
+    def shape(self):
+        return (self.params.nz, self.params.nx, self.params.ny)
+
+    def close(self):
+        if self.handle:
+            plan_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def set_mask(self, mask):
+        self.nlines = set_mask(self.handle, mask)
+        return self.nlines
+
+    def set_coils(self, coils):
+        set_coils(self.handle, coils)
+
+    def set_data(self, kdata):
+        set_data(self.handle, kdata, self.nlines)
+
+    def set_prior(self, support=None, sigma=None):
+        set_prior(self.handle, support, sigma)
+
+    def clear_prior(self):
+        clear_prior(self.handle)
+
+    def iterate(self, n):
+        return iterate(self.handle, n)
+
+    def reconstruct_frame(self, **kw):
+        return reconstruct_frame(self.handle, **kw)
+
+    def history(self):
+        return get_history(self.handle)
+
+    def support_words(self):
+        return support_words(self.params)

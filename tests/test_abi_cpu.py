@@ -1,0 +1,98 @@
+"""Host-only checks of the C ABI: the library loads, exports every entry point that
+include/lps_api.h declares, and rejects bad parameters before touching a GPU."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import lps_oracle as O
+from tests.abi_layout import abi_to_mallat, bits_to_mallat, mallat_to_bits
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lps():
+    from paper_1411_6206_gb300 import build, lps as L
+    build.build()
+    L.load()
+    return L
+
+
+def header_symbols():
+    txt = open(os.path.join(ROOT, "include", "lps_api.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(lps_[a-z0-9_]+)\s*\(", txt)))
+
+
+def test_library_exports_every_declared_symbol(lps):
+    lib = lps.load()
+    syms = header_symbols()
+    assert len(syms) >= 20
+    for s in syms:
+        assert hasattr(lib, s), s
+    assert set(syms) == set(lps.exported_symbols())
+
+
+def test_params_defaults_and_status_strings(lps):
+    p = lps.params_init()
+    assert p.max_iters == 50 and p.wavelet_levels == 3 and p.fft_z == 1
+    assert abs(p.lambda_L_rel - 0.01) < 1e-15 and abs(p.lambda_S_rel - 0.005) < 1e-15
+    assert lps.status_string(0) == "LPS_OK"
+    assert lps.status_string(-1) == "LPS_ERR_INVALID_ARG"
+    assert lps.version() == 1
+
+
+@pytest.mark.parametrize("bad,code", [
+    (dict(nx=12), -1), (dict(ny=0), -1), (dict(ncoil=0), -1), (dict(wavelet_levels=4), -1),
+    (dict(lambda_p=1.5), -1), (dict(layout=1), -1), (dict(precision=3), -1),
+    (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1),
+])
+def test_plan_create_rejects_bad_params(lps, bad, code):
+    kw = dict(nx=32, ny=32, nz=8, ncoil=2)
+    kw.update(bad)
+    p = lps.params_init(**kw)
+    with pytest.raises(lps.LpsError) as e:
+        lps.plan_create(p)
+    assert e.value.code == code
+
+
+def test_estimate_device_bytes(lps):
+    p = lps.params_init(nx=128, ny=128, nz=16, ncoil=8)
+    b = lps.estimate_device_bytes(p)
+    N = 128 * 128 * 16
+    assert 8 * N * 12 < b < 8 * N * 40
+    assert lps.support_words(p) == N // 32
+
+
+@pytest.mark.parametrize("J", [1, 2, 3])
+def test_abi_coefficient_order_is_blockwise_mallat(J):
+    """The ABI order groups the coefficients of each 8x8 tile; inside it each 2^J block keeps
+    its own Mallat layout. Check against the oracle's whole-plane transform."""
+    rng = np.random.default_rng(0)
+    nz, nx, ny = 2, 16, 24
+    x = rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny))
+    c = O.T(x, J)
+    zz, ii, jj = abi_to_mallat(nz, nx, ny, J)
+    assert len(set(zip(zz, ii, jj))) == nz * nx * ny            # a permutation
+    vals = c[zz, ii, jj].reshape(nz, nx // 8, ny // 8, 8, 8)
+    B = 1 << J
+    for z in range(nz):
+        for tx in range(nx // 8):
+            for ty in range(ny // 8):
+                tile = x[z, tx * 8:(tx + 1) * 8, ty * 8:(ty + 1) * 8]
+                for su in range(8 // B):
+                    for sv in range(8 // B):
+                        blk = tile[su * B:(su + 1) * B, sv * B:(sv + 1) * B]
+                        ref = O.haar2(blk, J)
+                        got = vals[z, tx, ty, su * B:(su + 1) * B, sv * B:(sv + 1) * B]
+                        assert np.abs(got - ref).max() < 1e-12
+
+
+def test_bitmap_pack_roundtrip():
+    rng = np.random.default_rng(1)
+    sup = rng.random((3, 16, 8)) < 0.3
+    words = mallat_to_bits(sup, 3)
+    assert words.dtype == np.uint32 and words.size == 3 * 16 * 8 // 32
+    assert np.array_equal(bits_to_mallat(words, 3, 16, 8, 3), sup)

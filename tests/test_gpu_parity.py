@@ -1,0 +1,319 @@
+"""GPU parity of every stage of the hot path against the FP64 oracle, through the C ABI.
+
+Tolerances (stated by the specification of this path): operators <= 1e-5 relative L2;
+one iteration from a given state <= 1e-5 relative; end-to-end reconstruction NRMSE <= 1e-3
+against the oracle after the stated iteration count; support bitmaps identical except for
+coefficients within 1e-5 * max|c| of the threshold.
+"""
+import numpy as np
+import pytest
+
+from oracle import lps_oracle as O
+from tests.abi_layout import bits_to_mallat, mallat_to_bits
+from tests.gpu_cases import c64, make_case, oracle_params, rel, up
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+OP_TOL = 1e-5
+E2E_TOL = 1e-3
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1411_6206_gb300 import lps
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    lps.load()
+    return lps
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def plan_for(L, case, nz, nx, ny, ncoil, **kw):
+    pl = L.Plan(nx, ny, nz, ncoil, **kw)
+    pl.set_coils(dev(case["coils"]))
+    n = pl.set_mask(dev(case["mask"]))
+    assert n == case["nlines"]
+    pl.set_data(dev(case["d"]))
+    return pl
+
+
+SHAPES = [
+    # nz, nx, ny, ncoil, fft_z
+    (8, 32, 32, 1, 1),       # single coil, smallest workload
+    (5, 16, 24, 3, 1),       # prime nz (generic radix), ny = 8*3, odd column count
+    (16, 32, 80, 4, 1),      # radix-5 in y
+    (13, 24, 48, 2, 1),      # prime nz = 13
+    (12, 16, 16, 2, 0),      # per-slice 2D encode
+    (32, 16, 64, 2, 1),      # largest column count
+]
+
+
+@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES)
+def test_forward_adjoint_match_oracle(L, nz, nx, ny, nc, fz):
+    case = make_case(nz, nx, ny, nc, seed=nz + nx, fft_z=fz)
+    pl = plan_for(L, case, nz, nx, ny, nc, fft_z=fz)
+    rng = np.random.default_rng(1)
+    x = c64(rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny)))
+    kd = torch.empty((nc, case["nlines"], nx), dtype=torch.complex64, device="cuda")
+    L.forward(pl.handle, dev(x), kd)
+    ref = O.E(up(x), up(case["coils"]), case["mask"], fz)
+    assert rel(kd.cpu().numpy(), ref) < OP_TOL
+    y = c64(rng.standard_normal(ref.shape) + 1j * rng.standard_normal(ref.shape))
+    img = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    L.adjoint(pl.handle, dev(y), img)
+    refa = O.EH(up(y), up(case["coils"]), case["mask"], fz)
+    assert rel(img.cpu().numpy(), refa) < OP_TOL
+    # adjoint identity on the GPU operators
+    lhs = np.vdot(kd.cpu().numpy().astype(np.complex128), up(y))
+    rhs = np.vdot(up(x), img.cpu().numpy().astype(np.complex128))
+    assert abs(lhs - rhs) < OP_TOL * abs(lhs)
+    pl.close()
+
+
+@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES[:4])
+def test_data_consistency_step(L, nz, nx, ny, nc, fz):
+    case = make_case(nz, nx, ny, nc, seed=3, fft_z=fz)
+    pl = plan_for(L, case, nz, nx, ny, nc, fft_z=fz)
+    rng = np.random.default_rng(2)
+    Z = c64(rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny)))
+    X = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    r2 = L.data_consistency(pl.handle, dev(Z), X)
+    coils, d = up(case["coils"]), up(case["d"])
+    R = O.E(up(Z), coils, case["mask"], fz) - d
+    Xref = up(Z) - O.EH(R, coils, case["mask"], fz)
+    assert rel(X.cpu().numpy(), Xref) < OP_TOL
+    assert abs(r2 - np.vdot(R, R).real) < 1e-5 * np.vdot(R, R).real
+    pl.close()
+
+
+def one_iteration_case(L, nz, nx, ny, nc, with_prior, lam_p=0.5, seed=11, J=3, eig=0):
+    case = make_case(nz, nx, ny, nc, seed=seed)
+    pl = plan_for(L, case, nz, nx, ny, nc, lambda_p=lam_p, wavelet_levels=J, eig_precision=eig)
+    coils, d, mask = up(case["coils"]), up(case["d"]), case["mask"]
+    p = oracle_params(pl.params)
+    # a state from a few oracle iterations, rounded to complex64 (the GPU's input)
+    r0 = O.priori_ls(d, coils, mask, p, iters=3)
+    X, S, Lp = c64(r0.X), c64(r0.S), c64(r0.L)
+    lamL, lamS = np.float32(r0.lambda_L), np.float32(r0.lambda_S)
+    prior = None
+    sup_words = sig = None
+    if with_prior:
+        sup = np.abs(O.T(up(X) - up(Lp), J)) > 1.5 * lamS
+        sig = np.linspace(1.2, 0.2, nz) * float(np.linalg.svd(O.casorati(up(X)), compute_uv=False)[0])
+        prior = O.Prior(support=sup, sigma=sig)
+        sup_words = mallat_to_bits(sup, J)
+        pl.set_prior(dev(sup_words), dev(sig))
+    L.set_state(pl.handle, dev(X), dev(S), dev(Lp), float(lamL), float(lamS), 3)
+    pl.iterate(1)
+    Xg = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    Lg = torch.empty_like(Xg)
+    Sg = torch.empty_like(Xg)
+    L.get_state(pl.handle, Xg, Lg, Sg)
+    ref = O.priori_ls(d, coils, mask, p, prior, iters=1,
+                      state=(up(X), up(S), up(Lp), float(lamL), float(lamS)))
+    return pl, ref, Xg.cpu().numpy(), Lg.cpu().numpy(), Sg.cpu().numpy()
+
+
+@pytest.mark.parametrize("with_prior", [False, True])
+@pytest.mark.parametrize("nz,nx,ny,nc", [(8, 32, 32, 2), (5, 16, 24, 3), (32, 16, 32, 2)])
+def test_one_iteration_from_state(L, nz, nx, ny, nc, with_prior):
+    pl, ref, Xg, Lg, Sg = one_iteration_case(L, nz, nx, ny, nc, with_prior)
+    assert rel(Lg, ref.L) < OP_TOL
+    assert rel(Sg, ref.S) < 10 * OP_TOL or np.linalg.norm(ref.S) < 1e-6
+    assert rel(Xg, ref.X) < OP_TOL
+    pl.close()
+
+
+@pytest.mark.parametrize("J", [1, 2])
+def test_one_iteration_other_wavelet_levels(L, J):
+    pl, ref, Xg, Lg, Sg = one_iteration_case(L, 8, 16, 16, 2, True, J=J)
+    assert rel(Lg, ref.L) < OP_TOL
+    assert rel(Sg, ref.S) < 10 * OP_TOL
+    pl.close()
+
+
+def test_one_iteration_fp64_eig(L):
+    pl, ref, Xg, Lg, Sg = one_iteration_case(L, 16, 16, 32, 2, True, eig=1)
+    assert rel(Lg, ref.L) < OP_TOL
+    pl.close()
+
+
+def run_frame(L, case, nz, nx, ny, nc, iters, **kw):
+    pl = plan_for(L, case, nz, nx, ny, nc, max_iters=iters, **kw)
+    recon = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    Lg = torch.empty_like(recon)
+    Sg = torch.empty_like(recon)
+    sup = torch.empty(pl.support_words(), dtype=torch.int32, device="cuda")
+    sig = torch.empty(nz, dtype=torch.float64, device="cuda")
+    st = pl.reconstruct_frame(recon=recon, L=Lg, S=Sg, support=sup, sigma=sig)
+    return pl, st, recon.cpu().numpy(), Lg.cpu().numpy(), Sg.cpu().numpy(), \
+        sup.cpu().numpy().view(np.uint32), sig.cpu().numpy()
+
+
+def check_support(sup_words, ref, nz, nx, ny, J, band=1e-5):
+    got = bits_to_mallat(sup_words, nz, nx, ny, J)
+    diff = got != ref.support
+    if not diff.any():
+        return 0
+    cabs = np.abs(ref.c)
+    near = np.abs(cabs - ref.lambda_S) <= band * cabs.max()
+    assert not (diff & ~near).any(), f"{int((diff & ~near).sum())} support bits differ off the tie band"
+    return int(diff.sum())
+
+
+@pytest.mark.parametrize("nz,nx,ny,nc,iters", [(8, 32, 32, 1, 30), (5, 16, 24, 3, 20), (16, 32, 64, 4, 30)])
+def test_frame_end_to_end(L, nz, nx, ny, nc, iters):
+    case = make_case(nz, nx, ny, nc, seed=5, frac=0.3)
+    pl, st, recon, Lg, Sg, sup, sig = run_frame(L, case, nz, nx, ny, nc, iters)
+    p = oracle_params(pl.params)
+    ref = O.priori_ls(up(case["d"]), up(case["coils"]), case["mask"], p)
+    assert O.nrmse(recon, ref.recon) <= E2E_TOL
+    assert O.nrmse(Lg + Sg, ref.recon) <= E2E_TOL
+    assert st.iters == iters
+    assert abs(st.lambda_L - ref.lambda_L) < 1e-5 * ref.lambda_L
+    assert abs(st.lambda_S - ref.lambda_S) < 1e-5 * ref.lambda_S
+    np.testing.assert_allclose(sig, ref.sigma, rtol=1e-3, atol=1e-4 * ref.sigma.max())
+    pl.close()
+
+
+@pytest.mark.parametrize("rule", [0, 1])
+def test_support_and_sigma_after_one_iteration(L, rule):
+    """Support bits of one iteration from a common state differ only inside the tie band;
+    sigma'' matches the oracle's singular values after steps (1)-(2)."""
+    case = make_case(8, 32, 32, 2, seed=13)
+    pl = plan_for(L, case, 8, 32, 32, 2, lambda_p=0.5, support_rule=rule)
+    coils, d, mask = up(case["coils"]), up(case["d"]), case["mask"]
+    p = oracle_params(pl.params)
+    r0 = O.priori_ls(d, coils, mask, p, iters=4)
+    X, S, Lp = c64(r0.X), c64(r0.S), c64(r0.L)
+    lamL, lamS = float(np.float32(r0.lambda_L)), float(np.float32(r0.lambda_S))
+    sup = np.abs(O.T(up(X) - up(Lp))) > 2.0 * lamS
+    sig = np.linspace(1.0, 0.1, 8) * r0.sigma.max()
+    pl.set_prior(dev(mallat_to_bits(sup, 3)), dev(sig))
+    L.set_state(pl.handle, dev(X), dev(S), dev(Lp), lamL, lamS, 4)
+    pl.iterate(1)
+    words = np.empty(pl.support_words(), np.uint32)
+    sg = np.empty(8, np.float64)
+    L.get_support(pl.handle, words, sg)
+    ref = O.priori_ls(d, coils, mask, p, O.Prior(support=sup, sigma=sig), iters=1,
+                      state=(up(X), up(S), up(Lp), lamL, lamS))
+    check_support(words, ref, 8, 32, 32, 3)
+    np.testing.assert_allclose(sg, ref.sigma, rtol=1e-5, atol=1e-6 * ref.sigma.max())
+    pl.close()
+
+
+def test_objective_non_increasing_on_gpu(L):
+    case = make_case(8, 32, 32, 2, seed=9, frac=0.35)
+    pl = plan_for(L, case, 8, 32, 32, 2, lambda_p=0.0, max_iters=25)
+    pl.iterate(25)
+    h = pl.history()
+    F = [r["objective"] for r in h]
+    assert len(F) == 25
+    for a, b in zip(F[1:], F[2:]):
+        assert b <= a * (1 + 1e-6), (a, b)
+    assert F[-1] < F[1]
+    pl.close()
+
+
+def test_exact_recovery_full_mask(L):
+    case = make_case(8, 16, 16, 1, seed=2, full=True, noise=0.0)
+    pl, st, recon, *_ = run_frame(L, case, 8, 16, 16, 1, 4, lambda_L_rel=0.0, lambda_S_rel=0.0,
+                                  lambda_p=0.0, rank_tau=0.0)
+    assert O.nrmse(recon, case["x"]) < 1e-5
+    pl.close()
+
+
+def test_recursive_sequence_matches_oracle(L):
+    from paper_1411_6206_gb300 import phantom as P
+    w = P.SMALL
+    pr = P.problem(w, frames=4)
+    coils = c64(pr["coils"])
+    datas = [c64(O.E(pr["x"][t], up(coils), pr["masks"][t]) + pr["noise"][t]) for t in range(4)]
+    pl = L.Plan(w.nx, w.ny, w.nz, w.ncoil, max_iters=w.iters, recursive=1)
+    pl.set_coils(dev(coils))
+    p = oracle_params(pl.params)
+    refs = O.sequence([up(d) for d in datas], up(coils), pr["masks"], p)
+    recon = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+    for t in range(4):
+        pl.set_mask(dev(pr["masks"][t]))
+        pl.set_data(dev(datas[t]))
+        pl.reconstruct_frame(recon=recon)
+        err = O.nrmse(recon.cpu().numpy(), refs[t].recon)
+        assert err <= E2E_TOL, (t, err)
+    pl.close()
+
+
+def test_graph_replay_is_deterministic(L):
+    case = make_case(16, 32, 32, 4, seed=21)
+    pl, st, r1, *_ = run_frame(L, case, 16, 32, 32, 4, 10)
+    r2 = torch.empty((16, 32, 32), dtype=torch.complex64, device="cuda")
+    pl.set_data(dev(case["d"]))
+    pl.reconstruct_frame(recon=r2)
+    assert np.array_equal(r1, r2.cpu().numpy())
+    pl.close()
+
+
+def test_host_pointer_api_matches_device_api(L):
+    case = make_case(8, 32, 32, 2, seed=4)
+    pl, st, rdev, *_ = run_frame(L, case, 8, 32, 32, 2, 8)
+    pl2 = L.Plan(32, 32, 8, 2, max_iters=8)
+    pl2.set_coils(case["coils"])
+    pl2.set_mask(case["mask"])
+    pl2.set_data(case["d"])
+    rh = np.empty((8, 32, 32), np.complex64)
+    pl2.reconstruct_frame(recon=rh)
+    assert np.array_equal(rh, rdev)
+    pl.close()
+    pl2.close()
+
+
+def test_session_export_import_resumes_bitwise(L):
+    from paper_1411_6206_gb300 import phantom as P
+    w = P.SMALL
+    pr = P.problem(w, frames=3)
+    coils = c64(pr["coils"])
+    datas = [c64(O.E(pr["x"][t], up(coils), pr["masks"][t]) + pr["noise"][t]) for t in range(3)]
+
+    def mk():
+        pl = L.Plan(w.nx, w.ny, w.nz, 1, max_iters=10, recursive=1)
+        pl.set_coils(dev(coils))
+        return pl
+
+    a = mk()
+    outs = []
+    for t in range(3):
+        a.set_mask(dev(pr["masks"][t]))
+        a.set_data(dev(datas[t]))
+        r = np.empty((w.nz, w.nx, w.ny), np.complex64)
+        a.reconstruct_frame(recon=r)
+        outs.append(r)
+        if t == 1:
+            blob = L.session_export(a.handle)
+    b = mk()
+    L.session_import(b.handle, blob)
+    b.set_mask(dev(pr["masks"][2]))
+    b.set_data(dev(datas[2]))
+    r = np.empty((w.nz, w.nx, w.ny), np.complex64)
+    b.reconstruct_frame(recon=r)
+    assert np.array_equal(r, outs[2])
+    a.close()
+    b.close()
+
+
+def test_error_paths(L):
+    pl = L.Plan(16, 16, 8, 1)
+    with pytest.raises(L.LpsError) as e:
+        pl.iterate(1)
+    assert e.value.code == L.ERR_STATE
+    with pytest.raises(L.LpsError) as e:
+        pl.set_mask(np.zeros((8, 16), np.uint8))
+    assert e.value.code == L.ERR_INVALID_ARG
+    pl.set_mask(np.ones((8, 16), np.uint8))
+    with pytest.raises(L.LpsError) as e:
+        L.set_data(pl.handle, np.zeros((1, 3, 16), np.complex64), 3)
+    assert e.value.code == L.ERR_INVALID_ARG
+    pl.close()
