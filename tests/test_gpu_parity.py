@@ -103,7 +103,8 @@ def one_iteration_case(L, nz, nx, ny, nc, with_prior, lam_p=0.5, seed=11, J=3, e
     sup_words = sig = None
     if with_prior:
         sup = np.abs(O.T(up(X) - up(Lp), J)) > 1.5 * lamS
-        sig = np.linspace(1.2, 0.2, nz) * float(np.linalg.svd(O.casorati(up(X)), compute_uv=False)[0])
+        # singular values of a neighbouring frame: the current sigma'' drifted by a few percent
+        sig = r0.sigma * (1.0 + 0.04 * np.cos(np.arange(nz)))
         prior = O.Prior(support=sup, sigma=sig)
         sup_words = mallat_to_bits(sup, J)
         pl.set_prior(dev(sup_words), dev(sig))
@@ -192,7 +193,7 @@ def test_support_and_sigma_after_one_iteration(L, rule):
     X, S, Lp = c64(r0.X), c64(r0.S), c64(r0.L)
     lamL, lamS = float(np.float32(r0.lambda_L)), float(np.float32(r0.lambda_S))
     sup = np.abs(O.T(up(X) - up(Lp))) > 2.0 * lamS
-    sig = np.linspace(1.0, 0.1, 8) * r0.sigma.max()
+    sig = r0.sigma * (1.0 + 0.04 * np.sin(np.arange(8.0)))
     pl.set_prior(dev(mallat_to_bits(sup, 3)), dev(sig))
     L.set_state(pl.handle, dev(X), dev(S), dev(Lp), lamL, lamS, 4)
     pl.iterate(1)
