@@ -117,7 +117,8 @@ typedef struct lps_stats {
 /* Per-iteration record returned by lps_get_history (same meaning as lps_stats fields). */
 typedef struct lps_iter_record {
   double resid_norm2, nuclear, l1_off_support, objective, rel_change;
-  int rank, pad;
+  int rank;
+  int eig_sweeps;          /* Jacobi sweeps of the Gram eigendecomposition                */
 } lps_iter_record;
 
 /* Fill *p with the defaults: layout SLICES, fft_z 1, J 3, 50 iterations, lambda_L_rel 0.01,

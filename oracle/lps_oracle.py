@@ -241,6 +241,7 @@ class Result:
     history: list             # per iteration: dict(resid2, nuclear, l1, objective, rel_change)
     X: np.ndarray             # X of the last iteration (step 4 output)
     c: np.ndarray             # T(X_{K-1} - L_{K-1}) of the last iteration
+    sigma_in: np.ndarray = None   # singular values of X - S entering the last step (1)
 
     @property
     def recon(self):
@@ -286,6 +287,7 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
     it = 0
     L = Lp
     s2 = np.zeros(shape[0])
+    s = np.zeros(shape[0])
     for it in range(1, K + 1):
         Z_old = Lp + S
         # (1) singular-value soft-thresholding of X_{it-1} - S_{it-1}
@@ -315,7 +317,7 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
     else:
         sup = np.abs(c) > lamS
     return Result(L=L, S=S, support=sup, sigma=np.array(s2, np.float64), lambda_L=lamL,
-                  lambda_S=lamS, iters=it, history=hist, X=X, c=c)
+                  lambda_S=lamS, iters=it, history=hist, X=X, c=c, sigma_in=np.array(s, np.float64))
 
 
 def objective(L, S, d, coils, mask, lamL, lamS, keep, p: Params) -> float:

@@ -265,7 +265,12 @@ static cudaError_t launch_dc_m(const DcArgs& a, cudaStream_t st) {
   }
 }
 
+cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st);
+
+// Plane sizes with a compile-time specialisation go to k_dc_fixed; the rest to k_dc.
 cudaError_t launch_dc(const DcArgs& a, int mode, cudaStream_t st) {
+  const cudaError_t ef = launch_dc_fixed(a, mode, st);
+  if (ef != cudaErrorNotSupported) return ef;
   if (dc_smem_bytes(a.g) > 227 * 1024) return cudaErrorInvalidValue;
   switch (mode) {
     case kDcUpdate: return launch_dc_m<kDcUpdate>(a, st);

@@ -5,13 +5,15 @@
 //   1. records the statistics of the previous iteration (residual, nuclear norm, l1 off the
 //      prior support, objective, relative change) and applies the stopping rule (Sec. 3:
 //      stop when the relative change of the solution falls below the tolerance);
-//   2. sums the per-plane Gram partials in a fixed order (compensated float32);
-//   3. diagonalises G by cyclic two-sided Jacobi rotations in round-robin order (nc/2
-//      disjoint rotations per step, one barrier per step), warm-started from the previous
-//      iteration's eigenvectors; optionally polished by float64 Jacobi sweeps;
+//   2. sums the per-plane Gram partials in a fixed order (compensated float32, kSub
+//      interleaved sub-sums per entry combined in a fixed order);
+//   3. diagonalises G by cyclic two-sided Jacobi rotations in round-robin order, starting
+//      from A = V_prev^H G V_prev with the previous eigenvectors; each step computes the
+//      nc/2 disjoint rotations, then updates every element of A (J^H A J) and every column
+//      pair of V (V J) in parallel; optionally polished by float64 Jacobi sweeps;
 //   4. sigma = sqrt(lambda), step (1) sigma' = max(sigma - lambda_L, 0), step (2)
 //      sigma'' = sigma' - lambda_p (sigma' - sigma_prev) (matched by rank), rank guard
-//      sigma''_i = 0 where sigma_i <= tau sigma_1, in float64;
+//      sigma''_i = 0 where sigma_i <= tau sigma_1;
 //   5. writes W = V diag(sigma''/sigma) V^H so that L = M W = U diag(sigma'') V^H.
 // At the first iteration it also fixes lambda_L = rel_L sigma_1(X_0) and
 // lambda_S = rel_S max|T(X_0)|.
@@ -19,19 +21,21 @@
 
 namespace lps {
 
-constexpr int kEigThreads = 256;
+constexpr int kEigThreads = 512;
 constexpr int kLd = kMaxNc + 1;   // leading dimension of the shared matrices
+constexpr int kSub = 4;           // sub-sums per Gram entry
 
-template <typename R>
-struct Cx;
-template <>
-struct Cx<float> {
-  using T = float2;
-};
-template <>
-struct Cx<double> {
-  using T = double2;
-};
+#ifdef LPS_EIG_PHASE_TIMING
+__device__ unsigned long long g_eig_phase[4096][8];
+#define EIG_STAMP(k)                                                            \
+  do {                                                                          \
+    if (threadIdx.x == 0 && a.iter < 4096) g_eig_phase[a.iter][k] = clock64(); \
+  } while (0)
+#else
+#define EIG_STAMP(k) \
+  do {               \
+  } while (0)
+#endif
 
 __device__ __forceinline__ float2 mkc(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ double2 mkc(double x, double y) { return make_double2(x, y); }
@@ -48,135 +52,179 @@ __device__ __forceinline__ C scl_(C a, R s) { return mkc(a.x * s, a.y * s); }
 template <typename C>
 __device__ __forceinline__ C conj_(C a) { return mkc(a.x, -a.y); }
 
-// Round-robin pairing: at step s of a sweep over np (even) indices, pair k is (p, q).
-__device__ __forceinline__ void rr_pair(int np, int s, int k, int& p, int& q) {
-  const int m = np - 1;
-  if (k == 0) {
-    p = m;
-    q = s;
-  } else {
-    p = (s + k) % m;
-    q = (s - k + m) % m;
-  }
-}
-
 template <typename R>
-struct Rot {
-  R c, s;
-  typename Cx<R>::T e;   // unit phase of a_pq
-  R t, gabs;
-  bool on;
+struct Cx;
+template <>
+struct Cx<float> {
+  using T = float2;
+  using T4 = float4;
+};
+template <>
+struct Cx<double> {
+  using T = double2;
+  using T4 = double4_16a;
 };
 
+// Rotation of a pair (p, q): J = [[c, se], [-conj(se), c]] with se = s a_pq/|a_pq| and
+// t = tan(theta) from tau = (a_qq - a_pp)/(2|a_pq|), t = sign(tau)/(|tau| + sqrt(1 + tau^2))
+// (the smaller root). Packed as {c, se.x, se.y, t|a_pq|}; t|a_pq| = 0 means no rotation.
+// A pair is left alone when |a_pq| <= max(eps max(|a_pp|, |a_qq|), floor): below that a
+// rotation moves the eigenvalues by O(eps^2 a) and the vectors by O(eps), the rounding level
+// of the arithmetic; `floor` (about one unit in the last place of the trace) stops
+// rotations of pairs of near-zero eigenvalues that only exchange rounding noise.
 template <typename R>
-__device__ __forceinline__ Rot<R> rot_params(const typename Cx<R>::T* A, int p, int q, R eps_rel, R abs_floor) {
-  using C = typename Cx<R>::T;
-  Rot<R> r;
+__device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T* A, int p, int q, R eps,
+                                                         R floor_, R* relmax) {
   const R app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
-  const C apq = A[p * kLd + q];
-  const R g = sqrt(apq.x * apq.x + apq.y * apq.y);
-  const R lim = fmax(eps_rel * sqrt(fabs(app * aqq)), abs_floor);
-  r.on = g > lim;
-  if (r.on) {
-    const R tau = (aqq - app) / (R(2) * g);
-    const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-    r.c = R(1) / sqrt(R(1) + t * t);
-    r.s = t * r.c;
-    r.e = mkc(apq.x / g, apq.y / g);
-    r.t = t;
-    r.gabs = g;
-  } else {
-    r.c = R(1);
-    r.s = R(0);
-    r.e = mkc(R(1), R(0));
-    r.t = R(0);
-    r.gabs = g;
+  const auto apq = A[p * kLd + q];
+  const R g2 = apq.x * apq.x + apq.y * apq.y;
+  const R lim = fmax(eps * fmax(fabs(app), fabs(aqq)), floor_);
+  typename Cx<R>::T4 r;
+  r.x = R(1);
+  r.y = R(0);
+  r.z = R(0);
+  r.w = R(0);
+  *relmax = R(0);
+  if (g2 > lim * lim) {
+    if constexpr (sizeof(R) == 4) {
+      // approximate intrinsics: c and s are derived from one t, so c^2 + |s|^2 = 1 to
+      // float32 precision whatever the rounding of t; a slightly inexact t only leaves a
+      // residue in a_pq that the next sweep removes
+      const float ig = rsqrtf(g2);
+      const float g = g2 * ig;
+      const float tau = (aqq - app) * 0.5f * ig;
+      const float h = fmaf(tau, tau, 1.0f);
+      const float t = copysignf(1.0f, tau) * __fdividef(1.0f, fabsf(tau) + h * rsqrtf(h));
+      const float c = rsqrtf(fmaf(t, t, 1.0f));
+      const float sg = t * c * ig;
+      r.x = c;
+      r.y = sg * apq.x;
+      r.z = sg * apq.y;
+      r.w = t * g;
+      *relmax = g;
+    } else {
+      const R g = sqrt(g2);
+      const R tau = (aqq - app) / (R(2) * g);
+      const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+      const R c = R(1) / sqrt(R(1) + t * t);
+      const R sg = t * c / g;
+      r.x = c;
+      r.y = sg * apq.x;
+      r.z = sg * apq.y;
+      r.w = t * g;
+      *relmax = g;
+    }
   }
   return r;
 }
 
-// Cyclic Jacobi on the Hermitian n x n matrix in A[0] (padded to even np with a zero
-// row/column); eigenvectors accumulated into V. Returns the sweeps done.
+struct JacobiTables {
+  unsigned char pq[kMaxNc][kMaxNc];    // [step][2k], [step][2k+1]: indices p, q of pair k
+  unsigned char pos[kMaxNc][kMaxNc];   // [step][i]: (pair k << 1) | (i is the q of pair k)
+};
+
+// Round-robin (circle) schedule over np indices: step s pairs (np-1, s) and
+// ((s + k) mod (np-1), (s - k) mod (np-1)) for k = 1..np/2-1; over np-1 steps every pair
+// of indices meets once.
+__device__ void build_tables(JacobiTables* T, int np) {
+  const int m = np - 1, nh = np >> 1;
+  for (int t = threadIdx.x; t < m * nh; t += blockDim.x) {
+    const int s = t / nh, k = t - (t / nh) * nh;
+    int p, q;
+    if (k == 0) {
+      p = m;
+      q = s;
+    } else {
+      p = (s + k) % m;
+      q = (s - k + m) % m;
+    }
+    T->pq[s][2 * k] = (unsigned char)p;
+    T->pq[s][2 * k + 1] = (unsigned char)q;
+    T->pos[s][p] = (unsigned char)(k << 1);
+    T->pos[s][q] = (unsigned char)((k << 1) | 1);
+  }
+}
+
+// Cyclic Jacobi on the Hermitian n x n matrix in A0 (zero-padded to even np); the
+// eigenvectors are accumulated into V. Returns the sweeps done; *result points at the
+// diagonalised matrix. `relw` (>= np/2 + 1 entries) and flags[0] are shared scratch.
 template <typename R>
-__device__ int jacobi(typename Cx<R>::T* A0, typename Cx<R>::T* A1, typename Cx<R>::T* V, int n, R eps_rel,
-                      R abs_floor, int max_sweeps, int* flags, typename Cx<R>::T** result) {
+__device__ int jacobi(typename Cx<R>::T* A0, typename Cx<R>::T* A1, typename Cx<R>::T* V, int n, R eps, R floor_,
+                      int max_sweeps, const JacobiTables* T, typename Cx<R>::T4* rot, R* relw, int* flags,
+                      typename Cx<R>::T** result) {
   using C = typename Cx<R>::T;
+  using C4 = typename Cx<R>::T4;
   const int np = n + (n & 1);
   const int nh = np >> 1;
-  const int nblk = nh * (nh + 1) / 2;
-  const int ntask = nblk + np * nh;
+  const int nsq = np * np;
+  const int ntask = nsq + np * nh;
   C* Ac = A0;
   C* An = A1;
-  if (threadIdx.x == 0) flags[0] = flags[1] = flags[2] = 0;
-  __syncthreads();
   int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    if (threadIdx.x == 0) flags[(sweep + 1) % 3] = 0;
+  for (;;) {
+    // converged when no off-diagonal entry exceeds its rotation threshold
+    if (threadIdx.x == 0) flags[sweep & 1] = 0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+      const int p = t / n, q = t - (t / n) * n;
+      R rm;
+      if (p < q && rot_params<R>(Ac, p, q, eps, floor_, &rm).w != R(0)) flags[sweep & 1] = 1;
+    }
+    __syncthreads();
+    if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
+      if (threadIdx.x < nh) {
+        R rm;
+        rot[threadIdx.x] =
+            rot_params<R>(Ac, T->pq[st][2 * threadIdx.x], T->pq[st][2 * threadIdx.x + 1], eps, floor_, &rm);
+      }
+      __syncthreads();
       for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        if (t < nblk) {
-          // upper-triangular pair block (k1 <= k2)
-          int k1 = 0, rem = t;
-          while (rem >= nh - k1) {
-            rem -= nh - k1;
-            ++k1;
-          }
-          const int k2 = k1 + rem;
-          int p1, q1, p2, q2;
-          rr_pair(np, st, k1, p1, q1);
-          rr_pair(np, st, k2, p2, q2);
-          const Rot<R> r1 = rot_params<R>(Ac, p1, q1, eps_rel, abs_floor);
-          if (r1.on) flags[sweep % 3] = 1;
-          if (k1 == k2) {
-            if (r1.on) {
-              An[p1 * kLd + p1] = mkc(Ac[p1 * kLd + p1].x - r1.t * r1.gabs, R(0));
-              An[q1 * kLd + q1] = mkc(Ac[q1 * kLd + q1].x + r1.t * r1.gabs, R(0));
-              An[p1 * kLd + q1] = mkc(R(0), R(0));
-              An[q1 * kLd + p1] = mkc(R(0), R(0));
+        if (t < nsq) {
+          // element (i, j) of J^H A J from the 2x2 block of rows {ip, iq}, columns {jp, jq}
+          const int i = t / np, j = t - (t / np) * np;
+          const int pi = T->pos[st][i], pj = T->pos[st][j];
+          const C4 r1 = rot[pi >> 1];
+          C v;
+          if ((pi >> 1) == (pj >> 1)) {
+            // diagonal block: a_pp - t|a_pq|, a_qq + t|a_pq|, exact zeros off the diagonal
+            if (r1.w == R(0)) {
+              v = Ac[i * kLd + j];
+            } else if (i == j) {
+              v = mkc(Ac[i * kLd + i].x + ((pi & 1) ? r1.w : -r1.w), R(0));
             } else {
-              An[p1 * kLd + p1] = Ac[p1 * kLd + p1];
-              An[q1 * kLd + q1] = Ac[q1 * kLd + q1];
-              An[p1 * kLd + q1] = Ac[p1 * kLd + q1];
-              An[q1 * kLd + p1] = Ac[q1 * kLd + p1];
+              v = mkc(R(0), R(0));
             }
-            continue;
+          } else {
+            const C4 r2 = rot[pj >> 1];
+            const int ip = T->pq[st][pi & ~1], iq = T->pq[st][pi | 1];
+            const int jp = T->pq[st][pj & ~1], jq = T->pq[st][pj | 1];
+            const C se1 = mkc(r1.y, r1.z), se2 = mkc(r2.y, r2.z);
+            const C bp0 = Ac[ip * kLd + jp], bp1 = Ac[ip * kLd + jq];
+            const C bq0 = Ac[iq * kLd + jp], bq1 = Ac[iq * kLd + jq];
+            C r0, r1v;   // row i of J1^H B at columns jp, jq
+            if (pi & 1) {
+              r0 = add_(mulc_(se1, bp0), scl_<C, R>(bq0, r1.x));
+              r1v = add_(mulc_(se1, bp1), scl_<C, R>(bq1, r1.x));
+            } else {
+              r0 = sub_(scl_<C, R>(bp0, r1.x), mul_(se1, bq0));
+              r1v = sub_(scl_<C, R>(bp1, r1.x), mul_(se1, bq1));
+            }
+            v = (pj & 1) ? add_(mul_(r0, se2), scl_<C, R>(r1v, r2.x))
+                         : sub_(scl_<C, R>(r0, r2.x), mul_(r1v, conj_(se2)));
           }
-          const Rot<R> r2 = rot_params<R>(Ac, p2, q2, eps_rel, abs_floor);
-          const C bpp = Ac[p1 * kLd + p2], bpq = Ac[p1 * kLd + q2];
-          const C bqp = Ac[q1 * kLd + p2], bqq = Ac[q1 * kLd + q2];
-          // rows: J1^H B
-          const C se1 = scl_<C, R>(r1.e, r1.s);           // s1 e1
-          const C se1c = conj_(se1);                      // s1 conj(e1)
-          const C rpp = sub_(scl_<C, R>(bpp, r1.c), mul_(se1, bqp));
-          const C rpq = sub_(scl_<C, R>(bpq, r1.c), mul_(se1, bqq));
-          const C rqp = add_(mul_(se1c, bpp), scl_<C, R>(bqp, r1.c));
-          const C rqq = add_(mul_(se1c, bpq), scl_<C, R>(bqq, r1.c));
-          // columns: (J1^H B) J2
-          const C se2 = scl_<C, R>(r2.e, r2.s);
-          const C se2c = conj_(se2);
-          const C opp = sub_(scl_<C, R>(rpp, r2.c), mul_(rpq, se2c));
-          const C opq = add_(mul_(rpp, se2), scl_<C, R>(rpq, r2.c));
-          const C oqp = sub_(scl_<C, R>(rqp, r2.c), mul_(rqq, se2c));
-          const C oqq = add_(mul_(rqp, se2), scl_<C, R>(rqq, r2.c));
-          An[p1 * kLd + p2] = opp;
-          An[p1 * kLd + q2] = opq;
-          An[q1 * kLd + p2] = oqp;
-          An[q1 * kLd + q2] = oqq;
-          An[p2 * kLd + p1] = conj_(opp);
-          An[q2 * kLd + p1] = conj_(opq);
-          An[p2 * kLd + q1] = conj_(oqp);
-          An[q2 * kLd + q1] = conj_(oqq);
+          An[i * kLd + j] = v;
         } else {
-          const int vt = t - nblk;
+          // V J on the column pair of rotation k, row i (both entries read before written)
+          const int vt = t - nsq;
           const int i = vt / nh, k = vt - (vt / nh) * nh;
-          int p, q;
-          rr_pair(np, st, k, p, q);
-          const Rot<R> r = rot_params<R>(Ac, p, q, eps_rel, abs_floor);
-          if (r.on) {
+          const C4 r = rot[k];
+          if (r.w != R(0)) {
+            const int p = T->pq[st][2 * k], q = T->pq[st][2 * k + 1];
+            const C se = mkc(r.y, r.z);
             const C vp = V[i * kLd + p], vq = V[i * kLd + q];
-            const C se = scl_<C, R>(r.e, r.s);
-            V[i * kLd + p] = sub_(scl_<C, R>(vp, r.c), mul_(vq, conj_(se)));
-            V[i * kLd + q] = add_(mul_(vp, se), scl_<C, R>(vq, r.c));
+            V[i * kLd + p] = sub_(scl_<C, R>(vp, r.x), mul_(vq, conj_(se)));
+            V[i * kLd + q] = add_(mul_(vp, se), scl_<C, R>(vq, r.x));
           }
         }
       }
@@ -185,45 +233,34 @@ __device__ int jacobi(typename Cx<R>::T* A0, typename Cx<R>::T* A1, typename Cx<
       Ac = An;
       An = tmp;
     }
-    const int any = flags[sweep % 3];
-    if (!any) {
-      ++sweep;
-      break;
-    }
+    ++sweep;
   }
   *result = Ac;
   return sweep;
 }
 
-__device__ __forceinline__ double block_sum_d(double v, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double r = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += red[i];
-  __syncthreads();
-  if (threadIdx.x == 0) red[0] = r;
-  __syncthreads();
-  r = red[0];
-  __syncthreads();
-  return r;
-}
-
 struct alignas(16) EigShared {
-  float2 A0[kMaxNc * kLd];
+  float2 A0[kMaxNc * kLd];   // A0 and A1 are contiguous: the Gram sub-sums use both
   float2 A1[kMaxNc * kLd];
   float2 V[kMaxNc * kLd];
   float2 G[kMaxNc * kLd];
-  double lam[kMaxNc];
-  double f[kMaxNc];
+  JacobiTables tab;
+  float4 rot[kMaxNc / 2];
+  float relw[kMaxNc];
+  float sig[kMaxNc];       // sigma by rank
+  float f[kMaxNc];         // sigma''_i / sigma_i
+  double lam[kMaxNc];      // eigenvalues
+  double lams[kMaxNc];     // eigenvalues by rank
   int rank[kMaxNc];
   int flags[4];
-  double red[32];
-  float2* Aout;
+  float red[4][32];
+  double sprev[kMaxNc];    // sigma_prev
+  double s2[kMaxNc];       // sigma'' by rank
+  // control scalars read once at entry
+  double nuc_prev;
+  float sig_prev1;         // nuclear norm of the previous iteration as float (finiteness test)
+  float lamL, lamS, haar_max;
+  int lambdas_set, rank_prev, sweeps_prev, has_sigma, v_valid;
 };
 
 struct alignas(16) EigShared64 {
@@ -231,8 +268,32 @@ struct alignas(16) EigShared64 {
   double2 A1[kMaxNc * kLd];
   double2 V[kMaxNc * kLd];
   double2 T[kMaxNc * kLd];
-  double2* Aout;
+  double4_16a rot[kMaxNc / 2];
+  double relw[kMaxNc];
 };
+
+// Sum a per-thread float over the block in a fixed order; valid in every thread.
+__device__ __forceinline__ float block_sum_all(float v, float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  float r = 0.f;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) r += red[i];
+  return r;
+}
+
+__device__ __forceinline__ void tri_index(int e, int n, int& i, int& j) {
+  i = 0;
+  int rem = e;
+  while (rem >= n - i) {
+    rem -= n - i;
+    ++i;
+  }
+  j = i + rem;
+}
 
 __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -241,66 +302,109 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   if (ctrl->converged) return;
   const int tid = threadIdx.x;
   const int n = a.g.nc;
+  const int np = n + (n & 1);
+  EIG_STAMP(0);
+  // control scalars and the prior, loaded once in parallel (global latency is long)
+  switch (tid) {
+    case 0: {
+      sh.nuc_prev = ctrl->nuclear_cur;
+      sh.sig_prev1 = (float)sh.nuc_prev;
+    } break;
+    case 1: sh.lamL = ctrl->lambda_L; break;
+    case 2: sh.lamS = ctrl->lambda_S; break;
+    case 3: sh.haar_max = __uint_as_float(ctrl->haar_max_bits); break;
+    case 4: sh.lambdas_set = ctrl->lambdas_set; break;
+    case 5: sh.rank_prev = ctrl->rank_cur; break;
+    case 6: sh.sweeps_prev = ctrl->sweeps_cur; break;
+    case 7: sh.has_sigma = a.persist->has_sigma; break;
+    case 8: sh.v_valid = a.persist->v_valid; break;
+    default: break;
+  }
+  if (tid >= 32 && tid < 32 + n) sh.sprev[tid - 32] = a.sigma_prev[tid - 32];
 
-  // 1. statistics of iteration iter-1 and the stopping rule
+  // 1. statistics of iteration iter-1 and the stopping rule (float32 partial sums)
   if (a.iter > 1) {
-    double r2 = 0.0;
-    for (int i = tid; i < a.g.nx; i += kEigThreads) r2 += (double)a.dc_part[i];
-    double l1 = 0.0, dz2 = 0.0, z2 = 0.0;
-    for (int i = tid; i < a.g.ntiles; i += kEigThreads) {
-      l1 += (double)a.lrs_part[i * 4 + 0];
-      dz2 += (double)a.lrs_part[i * 4 + 1];
-      z2 += (double)a.lrs_part[i * 4 + 2];
+    float r2 = 0.f, l1 = 0.f, dz2 = 0.f, z2 = 0.f;
+    for (int i = tid; i < a.g.nx; i += kEigThreads) r2 += a.dc_part[i];
+    for (int i = tid; i < a.lrs_parts; i += kEigThreads) {
+      l1 += a.lrs_part[i * 4 + 0];
+      dz2 += a.lrs_part[i * 4 + 1];
+      z2 += a.lrs_part[i * 4 + 2];
     }
-    r2 = block_sum_d(r2, sh.red);
-    l1 = block_sum_d(l1, sh.red);
-    dz2 = block_sum_d(dz2, sh.red);
-    z2 = block_sum_d(z2, sh.red);
-    const double rel = sqrt(dz2 / fmax(z2, 1e-300));
-    const double nuc = ctrl->nuclear_cur;
-    const bool nonfinite = !isfinite(r2) || !isfinite(nuc) || !isfinite(l1);
+    r2 = block_sum_all(r2, sh.red[0]);
+    l1 = block_sum_all(l1, sh.red[1]);
+    dz2 = block_sum_all(dz2, sh.red[2]);
+    z2 = block_sum_all(z2, sh.red[3]);
+    // float32 on every thread (float64 issues at a small fraction of the float32 rate)
+    const float rel = sqrtf(dz2 / fmaxf(z2, 1e-30f));
+    const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
+    const bool stop = nonfinite || (a.tol > 0.0 && rel < (float)a.tol);
+    const double nuc = sh.nuc_prev;
     if (tid == 0) {
       IterRec& rec = a.hist[a.iter - 2];
       rec.resid2 = r2;
       rec.nuclear = nuc;
       rec.l1 = l1;
-      rec.objective = 0.5 * r2 + (double)ctrl->lambda_L * nuc + (double)ctrl->lambda_S * l1;
-      rec.rel_change = rel;
-      rec.rank = ctrl->rank_cur;
+      rec.objective = 0.5 * (double)r2 + (double)sh.lamL * nuc + (double)sh.lamS * (double)l1;
+      rec.rel_change = (double)rel;
+      rec.rank = sh.rank_prev;
+      rec.sweeps = sh.sweeps_prev;
       ctrl->iters_done = a.iter - 1;
-      if (nonfinite) {
-        ctrl->err |= kErrNonfinite;
-        ctrl->converged = 1;
-      } else if (a.tol > 0.0 && rel < a.tol) {
-        ctrl->converged = 1;
-      }
+      if (nonfinite) ctrl->err |= kErrNonfinite;
+      if (stop) ctrl->converged = 1;
     }
-    if (a.finalize || nonfinite || (a.tol > 0.0 && rel < a.tol)) return;
+    if (a.finalize || stop) return;
   }
   if (a.finalize) return;
+  EIG_STAMP(1);
 
-  // 2. Gram matrix from the per-plane partials (compensated sums, fixed order)
+  // 2. Gram matrix: kSub interleaved compensated sub-sums per upper-triangle entry, then a
+  //    fixed-order combination.
   const int nn = n * n;
-  for (int e = tid; e < nn; e += kEigThreads) {
+  const int nut = n * (n + 1) / 2;
+  float2* sub = sh.A0;   // scratch [kSub][nut], spans A0 and A1 (free until the Jacobi)
+  build_tables(&sh.tab, np);
+  for (int task = tid; task < kSub * nut; task += kEigThreads) {
+    const int e = task % nut, part = task / nut;
+    int i, j;
+    tri_index(e, n, i, j);
+    const float2* src = a.gram_part + i * n + j;
     float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
-    for (int p = 0; p < a.nparts; ++p) {
-      const float2 v = a.gram_part[(long long)p * nn + e];
-      const float yx = v.x - cx, yy = v.y - cy;
-      const float tx = sx + yx, ty = sy + yy;
-      cx = (tx - sx) - yx;
-      cy = (ty - sy) - yy;
-      sx = tx;
-      sy = ty;
+    constexpr int U = 16;
+    for (int p0 = part; p0 < a.nparts; p0 += kSub * U) {
+      float2 v[U];
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const int pp = p0 + q * kSub;
+        v[q] = pp < a.nparts ? src[(long long)pp * nn] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int q = 0; q < U; ++q) {
+        const float yx = v[q].x - cx, yy = v[q].y - cy;
+        const float tx = sx + yx, ty = sy + yy;
+        cx = (tx - sx) - yx;
+        cy = (ty - sy) - yy;
+        sx = tx;
+        sy = ty;
+      }
     }
-    const int i = e / n, j = e - (e / n) * n;
-    if (i == j) sy = 0.f;
-    sh.G[i * kLd + j] = make_float2(sx, sy);
+    sub[part * nut + e] = make_float2(sx, sy);
   }
   __syncthreads();
+  for (int e = tid; e < nut; e += kEigThreads) {
+    int i, j;
+    tri_index(e, n, i, j);
+    float2 s = sub[e];
+    for (int q = 1; q < kSub; ++q) s = cadd(s, sub[q * nut + e]);
+    if (i == j) s.y = 0.f;
+    sh.G[i * kLd + j] = s;
+    sh.G[j * kLd + i] = cconj(s);
+  }
+  __syncthreads();
+  EIG_STAMP(2);
 
   // 3. Jacobi, warm-started from the previous eigenvectors
-  const int np = n + (n & 1);
-  const bool warm = ctrl->v_valid != 0;
+  const bool warm = sh.v_valid != 0;
   for (int e = tid; e < np * np; e += kEigThreads) {
     const int i = e / np, j = e - (e / np) * np;
     float2 vv = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
@@ -309,29 +413,25 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   }
   __syncthreads();
   if (warm) {
-    // A1 = G V, then A0 = V^H A1
-    for (int e = tid; e < n * n; e += kEigThreads) {
+    // A1 = G V, then A0 = V^H A1 (upper triangle, mirrored: exactly Hermitian)
+    for (int e = tid; e < nn; e += kEigThreads) {
       const int i = e / n, j = e - (e / n) * n;
       float2 s = make_float2(0.f, 0.f);
       for (int k = 0; k < n; ++k) s = cadd(s, cmul(sh.G[i * kLd + k], sh.V[k * kLd + j]));
       sh.A1[i * kLd + j] = s;
     }
     __syncthreads();
-    for (int e = tid; e < n * n; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
+    for (int e = tid; e < nut; e += kEigThreads) {
+      int i, j;
+      tri_index(e, n, i, j);
       float2 s = make_float2(0.f, 0.f);
       for (int k = 0; k < n; ++k) s = cadd(s, cmulc(sh.V[k * kLd + i], sh.A1[k * kLd + j]));
+      if (i == j) s.y = 0.f;
       sh.A0[i * kLd + j] = s;
-    }
-    __syncthreads();
-    // exact Hermitian symmetry: keep the upper triangle, real diagonal
-    for (int e = tid; e < n * n; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
-      if (i < j) sh.A0[j * kLd + i] = cconj(sh.A0[i * kLd + j]);
-      if (i == j) sh.A0[i * kLd + i].y = 0.f;
+      sh.A0[j * kLd + i] = cconj(s);
     }
   } else {
-    for (int e = tid; e < n * n; e += kEigThreads) {
+    for (int e = tid; e < nn; e += kEigThreads) {
       const int i = e / n, j = e - (e / n) * n;
       sh.A0[i * kLd + j] = sh.G[i * kLd + j];
     }
@@ -341,10 +441,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     if (i >= n || j >= n) sh.A0[i * kLd + j] = make_float2(0.f, 0.f);
   }
   __syncthreads();
+  EIG_STAMP(3);
   float trace = 0.f;
   for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
   float2* Af = nullptr;
-  jacobi<float>(sh.A0, sh.A1, sh.V, n, 2.0e-7f, 1.0e-9f * trace, 16, sh.flags, &Af);
+  const int sweeps = jacobi<float>(sh.A0, sh.A1, sh.V, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, &sh.tab, sh.rot,
+                                   sh.relw, sh.flags, &Af);
   __syncthreads();
 
   if (a.eig_fp64) {
@@ -356,7 +458,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       d.V[i * kLd + j] = make_double2(v.x, v.y);
     }
     __syncthreads();
-    for (int e = tid; e < n * n; e += kEigThreads) {
+    for (int e = tid; e < nn; e += kEigThreads) {
       const int i = e / n, j = e - (e / n) * n;
       double2 s = make_double2(0.0, 0.0);
       for (int k = 0; k < n; ++k) {
@@ -368,22 +470,22 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     __syncthreads();
     for (int e = tid; e < np * np; e += kEigThreads) {
       const int i = e / np, j = e - (e / np) * np;
-      double2 s = make_double2(0.0, 0.0);
-      if (i < n && j < n)
-        for (int k = 0; k < n; ++k) s = add_(s, mulc_(d.V[k * kLd + i], d.T[k * kLd + j]));
-      d.A0[i * kLd + j] = s;
+      if (i >= n || j >= n) d.A0[i * kLd + j] = make_double2(0.0, 0.0);
     }
-    __syncthreads();
-    for (int e = tid; e < n * n; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
-      if (i < j) d.A0[j * kLd + i] = conj_(d.A0[i * kLd + j]);
-      if (i == j) d.A0[i * kLd + i].y = 0.0;
+    for (int e = tid; e < nut; e += kEigThreads) {
+      int i, j;
+      tri_index(e, n, i, j);
+      double2 s = make_double2(0.0, 0.0);
+      for (int k = 0; k < n; ++k) s = add_(s, mulc_(d.V[k * kLd + i], d.T[k * kLd + j]));
+      if (i == j) s.y = 0.0;
+      d.A0[i * kLd + j] = s;
+      d.A0[j * kLd + i] = conj_(s);
     }
     __syncthreads();
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += fabs(d.A0[i * kLd + i].x);
     double2* Ad = nullptr;
-    jacobi<double>(d.A0, d.A1, d.V, n, 1.0e-15, 1.0e-17 * tr, 8, sh.flags, &Ad);
+    jacobi<double>(d.A0, d.A1, d.V, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 8, &sh.tab, d.rot, d.relw, sh.flags, &Ad);
     __syncthreads();
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = Ad[i * kLd + i].x;
     for (int e = tid; e < np * np; e += kEigThreads) {
@@ -395,57 +497,96 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = (double)Af[i * kLd + i].x;
   }
   __syncthreads();
+  EIG_STAMP(4);
 
-  // 4. singular values, thresholds, prior pull, rank guard (float64 scalars)
-  double sig1 = 0.0;
-  for (int i = 0; i < n; ++i) sig1 = fmax(sig1, sqrt(fmax(sh.lam[i], 0.0)));
-  if (tid == 0 && a.iter == 1 && !ctrl->lambdas_set) {
-    ctrl->lambda_L = (float)(a.lambda_L_rel * sig1);
-    ctrl->lambda_S = (float)(a.lambda_S_rel * (double)__uint_as_float(ctrl->haar_max_bits));
+  // 4. singular values, thresholds, prior pull, rank guard: one thread per eigenvalue; in
+  //    float64 after the float64 eigendecomposition, in float32 otherwise (float64 issues at
+  //    a small fraction of the float32 rate on this part).
+  if (tid < n) {
+    int r = 0;
+    const double li = sh.lam[tid];
+    if (a.eig_fp64) {
+      for (int j = 0; j < n; ++j) {
+        const double lj = sh.lam[j];
+        r += (lj > li) || (lj == li && j < tid);
+      }
+    } else {
+      const float lf = (float)li;
+      for (int j = 0; j < n; ++j) {
+        const float lj = (float)sh.lam[j];
+        r += (lj > lf) || (lj == lf && j < tid);
+      }
+    }
+    sh.rank[tid] = r;
+    sh.lams[r] = li;
+    sh.sig[r] = sqrtf(fmaxf((float)li, 0.f));
+  }
+  __syncthreads();
+  if (tid == 0 && a.iter == 1 && !sh.lambdas_set) {
+    const double sig1 = a.eig_fp64 ? sqrt(fmax(sh.lams[0], 0.0)) : (double)sh.sig[0];
+    sh.lamL = (float)(a.lambda_L_rel * sig1);
+    sh.lamS = (float)(a.lambda_S_rel * (double)sh.haar_max);
+    ctrl->lambda_L = sh.lamL;
+    ctrl->lambda_S = sh.lamS;
     ctrl->sigma_max = sig1;
     ctrl->lambdas_set = 1;
   }
   __syncthreads();
-  const double lamL = (double)ctrl->lambda_L;
-  const bool has_sigma = a.persist->has_sigma != 0;
   if (tid < n) {
-    const int i = tid;
-    int r = 0;
-    for (int j = 0; j < n; ++j)
-      r += (sh.lam[j] > sh.lam[i]) || (sh.lam[j] == sh.lam[i] && j < i);
-    sh.rank[i] = r;
-    const double s = sqrt(fmax(sh.lam[i], 0.0));
-    const double s1 = fmax(s - lamL, 0.0);
-    double s2 = has_sigma ? s1 - a.lambda_p * (s1 - a.sigma_prev[r]) : s1;
-    if (s <= a.rank_tau * sig1) s2 = 0.0;
-    sh.f[i] = s > 0.0 ? s2 / s : 0.0;
-    a.sigma_out[r] = s2;
+    const int r = sh.rank[tid];
+    const bool has_sigma = sh.has_sigma != 0;
+    if (a.eig_fp64) {
+      const double s = sqrt(fmax(sh.lam[tid], 0.0));
+      const double sig1 = sqrt(fmax(sh.lams[0], 0.0));
+      const double s1 = fmax(s - (double)sh.lamL, 0.0);
+      double s2 = has_sigma ? s1 - a.lambda_p * (s1 - sh.sprev[r]) : s1;
+      if (s <= a.rank_tau * sig1) s2 = 0.0;
+      sh.s2[r] = s2;
+      sh.f[tid] = s > 0.0 ? (float)(s2 / s) : 0.f;
+    } else {
+      const float s = sh.sig[r];
+      const float sig1 = sh.sig[0];
+      const float s1 = fmaxf(s - sh.lamL, 0.f);
+      float s2 = has_sigma ? s1 - (float)a.lambda_p * (s1 - (float)sh.sprev[r]) : s1;
+      if (s <= (float)a.rank_tau * sig1) s2 = 0.f;
+      sh.s2[r] = (double)s2;
+      sh.f[tid] = s > 0.f ? s2 / s : 0.f;
+    }
   }
   __syncthreads();
-  if (tid == 0) {
+  if (tid < n) a.sigma_out[tid] = sh.s2[tid];
+  if (tid == 32) {
     double nuc = 0.0;
     int rk = 0;
     for (int r = 0; r < n; ++r) {
-      const double s2 = a.sigma_out[r];
-      nuc += s2;
-      rk += s2 > 0.0;
+      nuc += sh.s2[r];
+      rk += sh.s2[r] > 0.0;
     }
     ctrl->nuclear_cur = nuc;
     ctrl->rank_cur = rk;
-    ctrl->v_valid = 1;
+    ctrl->sweeps_cur = sweeps;
   }
+  EIG_STAMP(5);
   // 5. W = V diag(f) V^H and the eigenvectors for the next warm start
-  for (int e = tid; e < n * n; e += kEigThreads) {
+  for (int e = tid; e < nn; e += kEigThreads) {
     const int i = e / n, j = e - (e / n) * n;
     float2 s = make_float2(0.f, 0.f);
     for (int k = 0; k < n; ++k) {
-      const float fk = (float)sh.f[k];
+      const float fk = sh.f[k];
       if (fk != 0.f) s = cadd(s, cscale(cmul(sh.V[i * kLd + k], cconj(sh.V[j * kLd + k])), fk));
     }
     a.W[i * n + j] = s;
     a.V[i * n + j] = sh.V[i * kLd + j];
   }
+  if (tid == 0) a.persist->v_valid = 1;
+  EIG_STAMP(6);
 }
+
+#ifdef LPS_EIG_PHASE_TIMING
+extern "C" int lps_probe_eig_phases(unsigned long long* out, int n) {
+  return (int)cudaMemcpyFromSymbol(out, g_eig_phase, (size_t)n * 8 * sizeof(unsigned long long));
+}
+#endif
 
 cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(EigShared) + (a.eig_fp64 ? sizeof(EigShared64) : 0);

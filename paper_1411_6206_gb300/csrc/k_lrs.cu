@@ -19,197 +19,227 @@
 
 namespace lps {
 
-constexpr int kNQ = kMaxNc / 4;   // slices per thread
-
-// One Haar analysis level l (1-based) on D[z][64] for all nc slices, sub-block size B.
-__device__ __forceinline__ void haar_level_fwd(float2* D, int nc, int B, int l) {
-  const int a = B >> (l - 1), half = a >> 1;
-  const int gdim = 8 >> l;                 // groups per tile edge at this level
-  const int ng = gdim * gdim;
-  const int tasks = nc * ng;
-  float2 o[2][4];
-  int base[2];
-  int cnt = 0;
-  for (int t = threadIdx.x; t < tasks; t += blockDim.x, ++cnt) {
-    const int z = t / ng, gidx = t - (t / ng) * ng;
-    const int gu = gidx / gdim, gv = gidx - (gidx / gdim) * gdim;
-    const int su = gu / half, sv = gv / half, iu = gu - su * half, iv = gv - sv * half;
-    const int ou = su * B, ov = sv * B;
-    const float2* Dz = D + z * 64;
-    const float2 p00 = Dz[(ou + 2 * iu) * 8 + ov + 2 * iv];
-    const float2 p01 = Dz[(ou + 2 * iu) * 8 + ov + 2 * iv + 1];
-    const float2 p10 = Dz[(ou + 2 * iu + 1) * 8 + ov + 2 * iv];
-    const float2 p11 = Dz[(ou + 2 * iu + 1) * 8 + ov + 2 * iv + 1];
-    const float2 s0 = cadd(p00, p01), d0 = csub(p00, p01);   // along y
-    const float2 s1 = cadd(p10, p11), d1 = csub(p10, p11);
-    o[cnt][0] = cscale(cadd(s0, s1), 0.5f);   // approximation
-    o[cnt][1] = cscale(cadd(d0, d1), 0.5f);   // x-low / y-high
-    o[cnt][2] = cscale(csub(s0, s1), 0.5f);   // x-high / y-low
-    o[cnt][3] = cscale(csub(d0, d1), 0.5f);   // x-high / y-high
-    base[cnt] = z * 64 + (ou + iu) * 8 + ov + iv;
-  }
-  __syncthreads();
-  for (int i = 0; i < cnt; ++i) {
-    float2* Dz = D + base[i];
-    Dz[0] = o[i][0];
-    Dz[half] = o[i][1];
-    Dz[half * 8] = o[i][2];
-    Dz[half * 8 + half] = o[i][3];
-  }
-  __syncthreads();
+// Thread layout: 8 consecutive lanes own one (tile, slice z); lane u holds row u of the
+// slice's 8 x 8 tile as 8 complex registers v = 0..7. CTAs of 256 threads take
+// TPC = floor(32 / nc) tiles.
+__device__ __forceinline__ float2 shfl2(float2 v, int src) {
+  return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
 
-__device__ __forceinline__ void haar_level_inv(float2* D, int nc, int B, int l) {
-  const int a = B >> (l - 1), half = a >> 1;
-  const int gdim = 8 >> l;
-  const int ng = gdim * gdim;
-  const int tasks = nc * ng;
-  float2 o[2][4];
-  int base[2];
-  int cnt = 0;
-  for (int t = threadIdx.x; t < tasks; t += blockDim.x, ++cnt) {
-    const int z = t / ng, gidx = t - (t / ng) * ng;
-    const int gu = gidx / gdim, gv = gidx - (gidx / gdim) * gdim;
-    const int su = gu / half, sv = gv / half, iu = gu - su * half, iv = gv - sv * half;
-    const int ou = su * B, ov = sv * B;
-    const float2* Dz = D + z * 64 + (ou + iu) * 8 + ov + iv;
-    const float2 ll = Dz[0], hy = Dz[half], hx = Dz[half * 8], hh = Dz[half * 8 + half];
-    const float2 s0 = cadd(ll, hx), s1 = csub(ll, hx);   // undo x split
-    const float2 d0 = cadd(hy, hh), d1 = csub(hy, hh);
-    o[cnt][0] = cscale(cadd(s0, d0), 0.5f);   // (2iu, 2iv)
-    o[cnt][1] = cscale(csub(s0, d0), 0.5f);   // (2iu, 2iv+1)
-    o[cnt][2] = cscale(cadd(s1, d1), 0.5f);   // (2iu+1, 2iv)
-    o[cnt][3] = cscale(csub(s1, d1), 0.5f);   // (2iu+1, 2iv+1)
-    base[cnt] = z * 64 + (ou + 2 * iu) * 8 + ov + 2 * iv;
+// One analysis level l (1-based) of the orthonormal 2D Haar on every aligned B x B
+// sub-block (B = 2^J) of the 8 x 8 tile, in place in the Mallat layout of each sub-block.
+// A = B >> (l-1) is the edge of the current approximation region, H = A/2.
+template <int J, int L>
+__device__ __forceinline__ void haar_fwd_level(float2 (&r)[8], int u, int lane) {
+  constexpr int B = 1 << J, A = B >> (L - 1), H = A / 2;
+  const int su = u / B, ul = u - su * B;          // sub-block row, row inside it
+  const bool act = ul < A;
+  const int gi = ul < H ? ul : ul - H;            // group row
+  const int s0 = (lane & ~7) + su * B + 2 * gi;   // source lanes (rows 2gi, 2gi+1)
+  float2 e[8], o[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    e[v] = shfl2(r[v], s0);
+    o[v] = shfl2(r[v], s0 + 1);
   }
-  __syncthreads();
-  for (int i = 0; i < cnt; ++i) {
-    float2* Dz = D + base[i];
-    Dz[0] = o[i][0];
-    Dz[1] = o[i][1];
-    Dz[8] = o[i][2];
-    Dz[9] = o[i][3];
+  if (!act) return;
+  // x split: rows (2gi, 2gi+1) -> low (top half of the region) or high (bottom half)
+  float2 row[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) row[v] = ul < H ? cadd(e[v], o[v]) : csub(e[v], o[v]);
+  // y split inside every sub-block column range, scaled 1/2 (two 1/sqrt(2) factors)
+#pragma unroll
+  for (int sv = 0; sv < 8 / B; ++sv) {
+    float2 t[A];
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      t[q] = cscale(cadd(row[sv * B + 2 * q], row[sv * B + 2 * q + 1]), 0.5f);
+      t[q + H] = cscale(csub(row[sv * B + 2 * q], row[sv * B + 2 * q + 1]), 0.5f);
+    }
+#pragma unroll
+    for (int q = 0; q < A; ++q) r[sv * B + q] = t[q];
   }
-  __syncthreads();
 }
 
+template <int J, int L>
+__device__ __forceinline__ void haar_inv_level(float2 (&r)[8], int u, int lane) {
+  constexpr int B = 1 << J, A = B >> (L - 1), H = A / 2;
+  const int su = u / B, ul = u - su * B;
+  const bool act = ul < A;
+  const int gi = ul >> 1;
+  const int s_lo = (lane & ~7) + su * B + gi;      // approximation / x-low row
+  const int s_hi = s_lo + H;                       // x-high row
+  float2 lo[8], hi[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) {
+    lo[v] = shfl2(r[v], s_lo);
+    hi[v] = shfl2(r[v], s_hi);
+  }
+  if (!act) return;
+  float2 row[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) row[v] = (ul & 1) ? csub(lo[v], hi[v]) : cadd(lo[v], hi[v]);
+#pragma unroll
+  for (int sv = 0; sv < 8 / B; ++sv) {
+    float2 t[A];
+#pragma unroll
+    for (int q = 0; q < H; ++q) {
+      t[2 * q] = cscale(cadd(row[sv * B + q], row[sv * B + q + H]), 0.5f);
+      t[2 * q + 1] = cscale(csub(row[sv * B + q], row[sv * B + q + H]), 0.5f);
+    }
+#pragma unroll
+    for (int q = 0; q < A; ++q) r[sv * B + q] = t[q];
+  }
+}
+
+template <int J>
+__device__ __forceinline__ void haar_fwd(float2 (&r)[8], int u, int lane) {
+  haar_fwd_level<J, 1>(r, u, lane);
+  if constexpr (J >= 2) haar_fwd_level<J, 2>(r, u, lane);
+  if constexpr (J >= 3) haar_fwd_level<J, 3>(r, u, lane);
+}
+template <int J>
+__device__ __forceinline__ void haar_inv(float2 (&r)[8], int u, int lane) {
+  if constexpr (J >= 3) haar_inv_level<J, 3>(r, u, lane);
+  if constexpr (J >= 2) haar_inv_level<J, 2>(r, u, lane);
+  haar_inv_level<J, 1>(r, u, lane);
+}
+
+template <int J>
 __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
   if (a.ctrl->converged) return;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nc = g.nc, ncp = nc + 1;
-  float2* Msh = reinterpret_cast<float2*>(smem);   // [64][ncp]
-  float2* Dsh = Msh + 64 * ncp;                     // [nc][64]
-  float2* Wsh = Dsh + nc * 64;                      // [nc][nc]
+  const int nc = g.nc, ldm = nc + 1;
+  const int tpc = 32 / nc;                           // tiles per CTA
+  float2* Msh = reinterpret_cast<float2*>(smem);      // [tpc][8 v][8 u * ldm]: M = X - S
+  float2* Wsh = Msh + tpc * 64 * ldm;                 // [nc][nc]
   float* red = reinterpret_cast<float*>(Wsh + nc * nc);
 
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int u = tid & 7, grp = tid >> 3;
+  const int tl = grp / nc, z = grp - tl * nc;
   const int nty = g.ny >> 3;
-  const int tile = blockIdx.x;
-  const int tx = tile / nty, ty = tile - (tile / nty) * nty;
-  const int row = tid & 63, zg = tid >> 6;
-  const int u = row >> 3, v = row & 7;
+  const int tile = blockIdx.x * tpc + tl;
+  const bool act = tl < tpc && tile < g.ntiles;
+  const int tx = act ? tile / nty : 0, ty = act ? tile - (tile / nty) * nty : 0;
   const long long nxy = (long long)g.nx * g.ny;
-  const long long goff = (long long)(tx * 8 + u) * g.ny + ty * 8 + v;
-  const int B = 1 << g.J;
+  const long long rowoff = (long long)z * nxy + (long long)(tx * 8 + u) * g.ny + ty * 8;
   const bool maxonly = a.haar_max_only != 0;
 
-  float2 Lp[kNQ], So[kNQ];
+  float2 Xr[8], Lp[8], So[8];
 #pragma unroll
-  for (int q = 0; q < kNQ; ++q) {
-    const int z = zg + 4 * q;
-    Lp[q] = So[q] = make_float2(0.f, 0.f);
-    if (z < nc) {
-      const long long gi = z * nxy + goff;
-      const float2 Xv = a.X[gi];
-      if (maxonly) {
-        Dsh[z * 64 + row] = Xv;
-      } else {
-        const float2 Sv = a.S[gi], Lv = a.L[gi];
-        Msh[row * ncp + z] = csub(Xv, Sv);
-        Dsh[z * 64 + row] = csub(Xv, Lv);
-        Lp[q] = Lv;
-        So[q] = Sv;
+  for (int v = 0; v < 8; ++v) Xr[v] = Lp[v] = So[v] = make_float2(0.f, 0.f);
+  if (act) {
+    const float4* xs = reinterpret_cast<const float4*>(a.X + rowoff);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 q = xs[i];
+      Xr[2 * i] = make_float2(q.x, q.y);
+      Xr[2 * i + 1] = make_float2(q.z, q.w);
+    }
+    if (!maxonly) {
+      const float4* ls = reinterpret_cast<const float4*>(a.L + rowoff);
+      const float4* ss = reinterpret_cast<const float4*>(a.S + rowoff);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const float4 q = ls[i], w = ss[i];
+        Lp[2 * i] = make_float2(q.x, q.y);
+        Lp[2 * i + 1] = make_float2(q.z, q.w);
+        So[2 * i] = make_float2(w.x, w.y);
+        So[2 * i + 1] = make_float2(w.z, w.w);
       }
     }
   }
-  if (!maxonly)
-    for (int i = tid; i < nc * nc; i += kThreads) Wsh[i] = a.W[i];
-  __syncthreads();
-  for (int l = 1; l <= g.J; ++l) haar_level_fwd(Dsh, nc, B, l);
 
   if (maxonly) {
+    haar_fwd<J>(Xr, u, lane);
     float mx = 0.f;
-    for (int i = tid; i < nc * 64; i += kThreads) mx = fmaxf(mx, sqrtf(cabs2(Dsh[i])));
+#pragma unroll
+    for (int v = 0; v < 8; ++v) mx = fmaxf(mx, sqrtf(cabs2(Xr[v])));
     mx = block_max(mx, red);
     if (tid == 0) atomicMax(&a.ctrl->haar_max_bits, __float_as_uint(mx));
     return;
   }
 
-  // Reprojection L_new[row][z] = sum_i M[row][i] W[i][z].
-  float2 Ln[kNQ];
+  // M = X - S rows to shared memory for the reprojection; W to shared memory.
+  if (act) {
+    float2* mrow = Msh + tl * 64 * ldm + u * ldm + z;
 #pragma unroll
-  for (int q = 0; q < kNQ; ++q) Ln[q] = make_float2(0.f, 0.f);
-  for (int i = 0; i < nc; ++i) {
-    const float2 mv = Msh[row * ncp + i];
-#pragma unroll
-    for (int q = 0; q < kNQ; ++q) {
-      const int z = zg + 4 * q;
-      if (z < nc) {
-        const float2 w = Wsh[i * nc + z];
-        Ln[q].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Ln[q].x));
-        Ln[q].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Ln[q].y));
-      }
-    }
+    for (int v = 0; v < 8; ++v) mrow[v * 8 * ldm] = csub(Xr[v], So[v]);
   }
+  for (int i = tid; i < nc * nc; i += kThreads) Wsh[i] = a.W[i];
 
-  // Support-aware shrink of the coefficients (thread: slices z, coefficient `row`).
+  // Sparse step on D = X - L_prev: Haar analysis, support-aware shrink, synthesis.
+  float2 D[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) D[v] = csub(Xr[v], Lp[v]);
+  haar_fwd<J>(D, u, lane);
   const float lamS = a.ctrl->lambda_S;
   const bool has_sup = a.persist->has_sup != 0;
-  const int lane = tid & 31;
-  float l1 = 0.f, cnt = 0.f;
+  // this lane's 8 coefficients are bits [u*8, u*8+8) of the (z, tile) 64-bit group
+  const long long wbase = ((long long)(z * (g.nx >> 3) + tx) * nty + ty) * 2;
+  unsigned keepbits = 0;
+  if (act && has_sup) keepbits = (a.sup_prior[wbase + (u >> 2)] >> ((u & 3) * 8)) & 0xffu;
+  float l1 = 0.f;
+  unsigned sbits = 0;
 #pragma unroll
-  for (int q = 0; q < kNQ; ++q) {
-    const int z = zg + 4 * q;
-    if (z < nc) {   // uniform across the warp
-      const long long word = ((long long)(z * (g.nx >> 3) + tx) * nty + ty) * 2 + (row >> 5);
-      const float2 c = Dsh[z * 64 + row];
-      const bool keep = has_sup && ((a.sup_prior[word] >> (row & 31)) & 1u);
-      const float ab = sqrtf(cabs2(c));
-      float2 cs = c;
-      if (!keep) {
-        const float f = ab > lamS ? (ab - lamS) / ab : 0.f;
-        cs = cscale(c, f);
-        l1 += ab > lamS ? ab - lamS : 0.f;
+  for (int v = 0; v < 8; ++v) {
+    const float2 c = D[v];
+    const float ab = sqrtf(cabs2(c));
+    const bool keep = (keepbits >> v) & 1u;
+    float2 cs = c;
+    if (!keep) {
+      cs = cscale(c, ab > lamS ? (ab - lamS) / ab : 0.f);
+      l1 += ab > lamS ? ab - lamS : 0.f;
+    }
+    const bool bit = (a.support_rule == 0) ? (ab > lamS) : (cs.x != 0.f || cs.y != 0.f);
+    sbits |= (unsigned)bit << v;
+    D[v] = cs;
+  }
+  // gather the bytes of lanes u = 0..3 (word 0) and u = 4..7 (word 1)
+  unsigned word = sbits << ((u & 3) * 8);
+  word |= __shfl_xor_sync(0xffffffffu, word, 1);
+  word |= __shfl_xor_sync(0xffffffffu, word, 2);
+  if (act && (u & 3) == 0 && a.sup_out) a.sup_out[wbase + (u >> 2)] = word;
+  const float cnt = (act && (u & 3) == 0) ? (float)__popc(word) : 0.f;
+  if (!act) l1 = 0.f;
+  haar_inv<J>(D, u, lane);
+
+  __syncthreads();
+  // Reprojection L_new[(u, v)][z] = sum_i M[(u, v)][i] W[i][z].
+  float2 Ln[8];
+#pragma unroll
+  for (int v = 0; v < 8; ++v) Ln[v] = make_float2(0.f, 0.f);
+  if (act) {
+    const float2* mrow = Msh + tl * 64 * ldm + u * ldm;
+    for (int i = 0; i < nc; ++i) {
+      const float2 w = Wsh[i * nc + z];
+#pragma unroll
+      for (int v = 0; v < 8; ++v) {
+        const float2 mv = mrow[v * 8 * ldm + i];
+        Ln[v].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Ln[v].x));
+        Ln[v].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Ln[v].y));
       }
-      const bool bit = (a.support_rule == 0) ? (ab > lamS) : (cs.x != 0.f || cs.y != 0.f);
-      const unsigned bal = __ballot_sync(0xffffffffu, bit);
-      if (lane == 0) {
-        if (a.sup_out) a.sup_out[word] = bal;
-        cnt += (float)__popc(bal);
-      }
-      Dsh[z * 64 + row] = cs;
     }
   }
-  __syncthreads();
-  for (int l = g.J; l >= 1; --l) haar_level_inv(Dsh, nc, B, l);
-
   float dz2 = 0.f, z2 = 0.f;
+  if (act) {
+    float4* ld = reinterpret_cast<float4*>(a.L + rowoff);
+    float4* sd = reinterpret_cast<float4*>(a.S + rowoff);
 #pragma unroll
-  for (int q = 0; q < kNQ; ++q) {
-    const int z = zg + 4 * q;
-    if (z < nc) {
-      const long long gi = z * nxy + goff;
-      const float2 Sn = Dsh[z * 64 + row];
-      a.S[gi] = Sn;
-      a.L[gi] = Ln[q];
-      const float2 Zo = cadd(Lp[q], So[q]);
-      const float2 dZ = csub(cadd(Ln[q], Sn), Zo);
-      dz2 += cabs2(dZ);
+    for (int i = 0; i < 4; ++i) {
+      ld[i] = make_float4(Ln[2 * i].x, Ln[2 * i].y, Ln[2 * i + 1].x, Ln[2 * i + 1].y);
+      sd[i] = make_float4(D[2 * i].x, D[2 * i].y, D[2 * i + 1].x, D[2 * i + 1].y);
+    }
+#pragma unroll
+    for (int v = 0; v < 8; ++v) {
+      const float2 Zo = cadd(Lp[v], So[v]);
+      dz2 += cabs2(csub(cadd(Ln[v], D[v]), Zo));
       z2 += cabs2(Zo);
     }
   }
-  float* part = a.lrs_part + (long long)tile * 4;
+  float* part = a.lrs_part + (long long)blockIdx.x * 4;
   float r;
   r = block_sum(l1, red);
   if (tid == 0) part[0] = r;
@@ -263,18 +293,31 @@ cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long l
   return cudaGetLastError();
 }
 
+static int lrs_tpc(const Geom& g) { return 32 / g.nc; }
+
 static size_t lrs_smem(const Geom& g) {
-  return (size_t)(64 * (g.nc + 1) + g.nc * 64 + g.nc * g.nc) * sizeof(float2) + 32 * sizeof(float);
+  return (size_t)(lrs_tpc(g) * 64 * (g.nc + 1) + g.nc * g.nc) * sizeof(float2) + 32 * sizeof(float);
+}
+
+int lrs_blocks(const Geom& g) { return (g.ntiles + lrs_tpc(g) - 1) / lrs_tpc(g); }
+
+template <int J>
+static cudaError_t launch_lrs_j(const LrsArgs& a, cudaStream_t st) {
+  const size_t smem = lrs_smem(a.g);
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(k_lrs<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_lrs<J><<<lrs_blocks(a.g), kThreads, smem, st>>>(a);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
-  const size_t smem = lrs_smem(a.g);
-  if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_lrs, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
+  switch (a.g.J) {
+    case 1: return launch_lrs_j<1>(a, st);
+    case 2: return launch_lrs_j<2>(a, st);
+    default: return launch_lrs_j<3>(a, st);
   }
-  k_lrs<<<a.g.ntiles, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part,

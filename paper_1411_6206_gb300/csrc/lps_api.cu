@@ -4,6 +4,7 @@
 #include "lps_internal.cuh"
 
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -241,8 +242,11 @@ int wait_upload(lps_plan* P) {
   return LPS_OK;
 }
 
-int upload_persist(lps_plan* P) {
-  CK(cudaMemcpyAsync(P->persist, P->h_persist, sizeof(DevPersist), cudaMemcpyHostToDevice, P->st));
+// Host-owned fields: nlines, has_sup, has_sigma; v_valid is written by the eigen kernel and
+// uploaded only when the host resets or restores it.
+int upload_persist(lps_plan* P, bool with_v = false) {
+  const size_t n = with_v ? sizeof(DevPersist) : offsetof(DevPersist, v_valid);
+  CK(cudaMemcpyAsync(P->persist, P->h_persist, n, cudaMemcpyHostToDevice, P->st));
   CK(cudaEventRecord(P->upload_done, P->st));
   P->upload_pending = true;
   return LPS_OK;
@@ -300,12 +304,12 @@ int prof_begin(lps_plan* P, int cls, cudaStream_t st) {
   }
   if (P->ev_class.size() < (size_t)P->ev_used + 1) P->ev_class.resize(P->ev_used + 1);
   P->ev_class[P->ev_used] = cls;
-  CK(cudaEventRecord(P->ev[2 * P->ev_used], st));
+  CK(cudaEventRecordWithFlags(P->ev[2 * P->ev_used], st, cudaEventRecordExternal));
   return LPS_OK;
 }
 int prof_end(lps_plan* P, cudaStream_t st) {
   if (!P->profiling || st != P->cap) return LPS_OK;
-  CK(cudaEventRecord(P->ev[2 * P->ev_used + 1], st));
+  CK(cudaEventRecordWithFlags(P->ev[2 * P->ev_used + 1], st, cudaEventRecordExternal));
   ++P->ev_used;
   return LPS_OK;
 }
@@ -320,6 +324,9 @@ int prof_end(lps_plan* P, cudaStream_t st) {
 // Step (0): X_0 = E^H d, L_0 := X_0, S_0 = 0, Gram of X_0, max |T(X_0)|.
 int enqueue_init(lps_plan* P, cudaStream_t st) {
   CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), st));
+  // Each frame starts its eigendecomposition from scratch unless the plan reconstructs a
+  // sequence, where the previous frame's eigenvectors are the warm start.
+  if (!P->p.recursive) CK(cudaMemsetAsync(&P->persist->v_valid, 0, sizeof(int), st));
   DcArgs a = dc_args(P);
   a.X = P->X;
   a.L_out = P->L;
@@ -348,6 +355,7 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
   e.nparts = P->g.nx;
   e.dc_part = P->dc_part;
   e.lrs_part = P->lrs_part;
+  e.lrs_parts = lrs_blocks(P->g);
   e.W = P->W;
   e.V = P->V;
   e.sigma_prev = P->sigma_prev;
@@ -466,10 +474,11 @@ int read_stats(lps_plan* P, lps_stats* s) {
     s->rel_change = r.rel_change;
   }
   // support count from the last low-rank/sparse partials
-  std::vector<float> part((size_t)P->g.ntiles * 4);
+  const int nb = lrs_blocks(P->g);
+  std::vector<float> part((size_t)nb * 4);
   CK(cudaMemcpy(part.data(), P->lrs_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost));
   long long cnt = 0;
-  for (int t = 0; t < P->g.ntiles; ++t) cnt += (long long)part[(size_t)t * 4 + 3];
+  for (int t = 0; t < nb; ++t) cnt += (long long)part[(size_t)t * 4 + 3];
   s->support_count = cnt;
   return LPS_OK;
 }
@@ -724,13 +733,22 @@ int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev
   return upload_persist(P);
 }
 
-int lps_clear_prior(lps_plan* P) { return lps_set_prior(P, nullptr, nullptr); }
+int lps_clear_prior(lps_plan* P) {
+  ARG(P != nullptr, "plan is NULL");
+  int rc = wait_upload(P);
+  if (rc) return rc;
+  P->h_persist->v_valid = 0;
+  P->h_persist->has_sup = 0;
+  P->h_persist->has_sigma = 0;
+  return upload_persist(P, true);
+}
 
 int lps_iterate(lps_plan* P, int n_iters, lps_stats* stats) {
   int rc = need_ready(P);
   if (rc) return rc;
-  ARG(n_iters >= 0 && P->iters_done + n_iters <= P->p.max_iters,
-      "n_iters out of range (done %d, max_iters %d)", P->iters_done, P->p.max_iters);
+  const int done = P->state_ready ? P->iters_done : 0;
+  ARG(n_iters >= 0 && done + n_iters <= P->p.max_iters, "n_iters out of range (done %d, max_iters %d)", done,
+      P->p.max_iters);
   if (!P->state_ready) {
     if ((rc = enqueue_init(P, P->st))) return rc;
     P->iters_done = 0;
@@ -814,7 +832,7 @@ int lps_get_history(lps_plan* P, lps_iter_record* out, int max, int* count) {
     out[i].objective = r[i].objective;
     out[i].rel_change = r[i].rel_change;
     out[i].rank = r[i].rank;
-    out[i].pad = 0;
+    out[i].eig_sweeps = r[i].sweeps;
   }
   *count = n;
   return LPS_OK;
@@ -973,23 +991,26 @@ int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm
 // Checkpoint layout: header, prior support words, prior sigma, L, S, X, lambdas.
 struct CkptHeader {
   uint32_t magic, version;
-  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done;
+  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done, v_valid, pad;
   double lambda_L, lambda_S;
 };
 
 int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
   ARG(P != nullptr && bytes != nullptr, "NULL argument");
   const size_t w = support_words(P->g), img = (size_t)P->g.N * sizeof(float2);
-  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img;
+  const size_t vb = (size_t)P->g.nc * P->g.nc * sizeof(float2);
+  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img + vb;
   if (!buf) {
     *bytes = need;
     return LPS_OK;
   }
   ARG(*bytes >= need, "buffer too small (%zu < %zu)", *bytes, need);
   CK(cudaMemcpyAsync(P->h_ctrl, P->ctrl, sizeof(DevCtrl), cudaMemcpyDeviceToHost, P->st));
+  DevPersist dp;
+  CK(cudaMemcpyAsync(&dp, P->persist, sizeof(DevPersist), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
-  CkptHeader h{0x4c50531a, 1, P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.J, P->h_persist->has_sup,
-               P->h_persist->has_sigma, P->iters_done, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
+  CkptHeader h{0x4c50531a, 2, P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.J, dp.has_sup,
+               dp.has_sigma, P->iters_done, dp.v_valid, 0, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
   unsigned char* o = (unsigned char*)buf;
   std::memcpy(o, &h, sizeof(h));
   o += sizeof(h);
@@ -1002,6 +1023,8 @@ int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
   CK(cudaMemcpy(o, P->S, img, cudaMemcpyDeviceToHost));
   o += img;
   CK(cudaMemcpy(o, P->X, img, cudaMemcpyDeviceToHost));
+  o += img;
+  CK(cudaMemcpy(o, P->V, vb, cudaMemcpyDeviceToHost));
   *bytes = need;
   return LPS_OK;
 }
@@ -1009,11 +1032,12 @@ int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
 int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
   ARG(P != nullptr && buf != nullptr, "NULL argument");
   const size_t w = support_words(P->g), img = (size_t)P->g.N * sizeof(float2);
-  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img;
+  const size_t vb = (size_t)P->g.nc * P->g.nc * sizeof(float2);
+  const size_t need = sizeof(CkptHeader) + w * 4 + P->g.nc * sizeof(double) + 3 * img + vb;
   ARG(bytes >= need, "checkpoint too small");
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
-  ARG(h.magic == 0x4c50531a && h.version == 1, "not a checkpoint of this library");
+  ARG(h.magic == 0x4c50531a && h.version == 2, "not a checkpoint of this library");
   ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J, "checkpoint shape mismatch");
   const unsigned char* i = (const unsigned char*)buf + sizeof(h);
   CK(cudaStreamSynchronize(P->st));
@@ -1026,11 +1050,14 @@ int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
   CK(cudaMemcpy(P->S, i, img, cudaMemcpyHostToDevice));
   i += img;
   CK(cudaMemcpy(P->X, i, img, cudaMemcpyHostToDevice));
+  i += img;
+  CK(cudaMemcpy(P->V, i, vb, cudaMemcpyHostToDevice));
   int rc = wait_upload(P);
   if (rc) return rc;
   P->h_persist->has_sup = h.has_sup;
   P->h_persist->has_sigma = h.has_sigma;
-  return upload_persist(P);
+  P->h_persist->v_valid = h.v_valid;
+  return upload_persist(P, true);
 }
 
 }  // extern "C"

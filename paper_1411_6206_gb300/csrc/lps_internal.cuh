@@ -29,7 +29,7 @@ struct DevPersist {
   int nlines;               // sampled lines of the current mask
   int has_sup;              // prior support present (nonzero)
   int has_sigma;            // prior singular values present (nonzero)
-  int pad;
+  int v_valid;              // eigenvectors from an earlier eigendecomposition are available
 };
 
 // Per-frame control block (zeroed at the start of every frame).
@@ -40,16 +40,15 @@ struct DevCtrl {
   int converged;
   int iters_done;
   int err;
-  int v_valid;              // warm-start eigenvectors available
   int rank_cur;
-  int pad0;
+  int sweeps_cur;           // Jacobi sweeps of the current eigendecomposition
   double sigma_max;
   double nuclear_cur;
 };
 
 struct IterRec {
   double resid2, nuclear, l1, objective, rel_change;
-  int rank, pad;
+  int rank, sweeps;
 };
 
 struct Geom {
@@ -110,7 +109,7 @@ struct LrsArgs {
   const float2* W;          // [nc][nc]
   const uint32_t* sup_prior;
   uint32_t* sup_out;        // nullptr = do not write the support bitmap
-  float* lrs_part;          // [ntiles][4]: l1 off-support, ||dZ||^2, ||Z_old||^2, support count
+  float* lrs_part;          // [CTAs][4]: l1 off-support, ||dZ||^2, ||Z_old||^2, support count
   const DevPersist* persist;
   DevCtrl* ctrl;
   int support_rule;
@@ -123,13 +122,14 @@ struct EigArgs {
   const float2* gram_part;  // [nparts][nc][nc]
   int nparts;
   const float* dc_part;     // [nx]
-  const float* lrs_part;    // [ntiles][4]
+  const float* lrs_part;    // [lrs_parts][4]
+  int lrs_parts;            // CTAs of the low-rank/sparse kernel
   float2* W;                // [nc][nc]
   float2* V;                // [nc][nc] warm-start eigenvectors
   const double* sigma_prev;
   double* sigma_out;        // sigma'' in rank order
   IterRec* hist;
-  const DevPersist* persist;
+  DevPersist* persist;      // v_valid is set once eigenvectors exist
   DevCtrl* ctrl;
   double lambda_L_rel, lambda_S_rel, lambda_p, rank_tau, tol;
   int iter;                 // iteration k whose SVT this launch computes (1-based)
@@ -145,6 +145,7 @@ cudaError_t launch_eig(const EigArgs& a, cudaStream_t st);
 size_t dc_smem_bytes(const Geom& g);
 size_t xfft_smem_bytes(const Geom& g);
 int dc_ept(const Geom& g);
+int lrs_blocks(const Geom& g);
 
 }  // namespace lps
 

@@ -56,7 +56,7 @@ class Stats(C.Structure):
 class IterRecord(C.Structure):
     _fields_ = [("resid_norm2", C.c_double), ("nuclear", C.c_double),
                 ("l1_off_support", C.c_double), ("objective", C.c_double),
-                ("rel_change", C.c_double), ("rank", C.c_int), ("pad", C.c_int)]
+                ("rel_change", C.c_double), ("rank", C.c_int), ("eig_sweeps", C.c_int)]
 
 
 class KernelTimes(C.Structure):
@@ -252,7 +252,7 @@ def get_history(plan: int, max_records: int = 4096):
     buf = (IterRecord * max_records)()
     n = C.c_int()
     _check(load().lps_get_history(plan, buf, max_records, C.byref(n)), "get_history")
-    return [{k: getattr(buf[i], k) for k, _ in IterRecord._fields_ if k != "pad"}
+    return [{k: getattr(buf[i], k) for k, _ in IterRecord._fields_}
             for i in range(n.value)]
 
 
