@@ -20,6 +20,8 @@ namespace lps {
 template <int EPT, int MODE>
 __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   const Geom& g = a.g;
+  pdl_trigger();
+  pdl_wait();
   if (a.ctrl && a.ctrl->converged) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int ny = g.ny, nz = g.nz, nx = g.nx, nyp = g.nyp;
@@ -248,8 +250,8 @@ static cudaError_t launch_dc_t(const DcArgs& a, cudaStream_t st) {
     attr_set = true;
     attr_bytes = 227 * 1024;
   }
-  k_dc<EPT, MODE><<<a.g.nx, kThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_dc<EPT, MODE>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int MODE>

@@ -101,7 +101,6 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   constexpr int NYP = Lay::NYP, PLANE = Lay::PLANE, PLANEP = Lay::PLANEP, EPT = Lay::EPT;
   constexpr int NTH = NCG * NT;
   const Geom& g = a.g;
-  if (a.ctrl && a.ctrl->converged) return;
   extern __shared__ __align__(16) unsigned char smem[];
   float2* base = reinterpret_cast<float2*>(smem);
   float2* twy = base + NCG * Lay::GROUP;
@@ -120,17 +119,7 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   const int x = blockIdx.x;
   const int nx = g.nx, ncoil = g.ncoil;
   const long long xy = (long long)nx * NY;
-  const int m = a.persist->nlines;
   int* errp = a.ctrl ? &a.ctrl->err : nullptr;
-
-  for (int i = tid; i < NY; i += NTH) twy[i] = a.tw_y[i];
-  for (int i = tid; i < NZ; i += NTH) twz[i] = a.tw_z[i];
-  if (gtid == 0) {
-    mbar_init(&gbar[0], 1);
-    mbar_init(&gbar[1], 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
   constexpr unsigned kRowBytes = NY * sizeof(float2);
   auto issue = [&](int c, float2* slot, uint64_t* b) {
     mbar_arrive_expect_tx(b, kRowBytes * NZ);
@@ -138,9 +127,14 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
 #pragma unroll 4
     for (int z = 0; z < NZ; ++z) bulk_g2s(slot + z * NY, src + z * xy, kRowBytes, b);
   };
+  // The first two coil planes of each group are requested before anything else; the
+  // control flag and the other global inputs are loaded while they are in flight.
   unsigned inflight = 0;   // slots with a copy in flight (thread gtid == 0 of each group)
   unsigned phase = 0;      // parity of the next phase to wait for, per slot
   if (gtid == 0) {
+    mbar_init(&gbar[0], 1);
+    mbar_init(&gbar[1], 1);
+    fence_mbar_init();
     if (grp < ncoil) {
       issue(grp, coilS0, &gbar[0]);
       inflight |= 1u;
@@ -150,6 +144,12 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
       inflight |= 2u;
     }
   }
+  for (int i = tid; i < NY; i += NTH) twy[i] = a.tw_y[i];
+  for (int i = tid; i < NZ; i += NTH) twz[i] = a.tw_z[i];
+  pdl_trigger();
+  pdl_wait();   // L, S, the control block and the line count come from earlier work
+  const int conv = a.ctrl ? a.ctrl->converged : 0;
+  const int m = a.persist->nlines;
 
   float2 Zr[EPT], acc[EPT];
 #pragma unroll
@@ -164,6 +164,14 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
       if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
       Zr[k] = v;
     }
+  }
+  __syncthreads();
+  if (conv) {
+    // converged earlier in this frame: let the copies land, then leave
+    if (gtid == 0)
+      for (int s = 0; s < 2; ++s)
+        if (inflight & (1u << s)) mbar_wait_bounded(&gbar[s], 0u, nullptr);
+    return;
   }
 
   const float sc = g.scale_yz;
@@ -346,8 +354,8 @@ static cudaError_t launch_fixed(const DcArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  k_dc_fixed<NY, NZ, NCG, NT, MODE><<<a.g.nx, NCG * NT, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_dc_fixed<NY, NZ, NCG, NT, MODE>, dim3(a.g.nx), dim3(NCG * NT), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 template <int NY, int NZ, int NCG, int NT>

@@ -254,6 +254,8 @@ struct alignas(16) EigShared {
   int rank[kMaxNc];
   int flags[4];
   float red[4][32];
+  float4 red4[32];
+  unsigned char tri[2][kMaxNc * (kMaxNc + 1) / 2];   // (i, j) of upper-triangle entry e
   double sprev[kMaxNc];    // sigma_prev
   double s2[kMaxNc];       // sigma'' by rank
   // control scalars read once at entry
@@ -272,40 +274,43 @@ struct alignas(16) EigShared64 {
   double relw[kMaxNc];
 };
 
-// Sum a per-thread float over the block in a fixed order; valid in every thread.
-__device__ __forceinline__ float block_sum_all(float v, float* red) {
+// Sum four per-thread floats over the block in a fixed order; valid in every thread.
+__device__ __forceinline__ float4 block_sum4(float4 v, float4* red) {
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
+    v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
+    v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
+  }
   if (lane == 0) red[w] = v;
   __syncthreads();
-  float r = 0.f;
+  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
   const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) r += red[i];
-  return r;
-}
-
-__device__ __forceinline__ void tri_index(int e, int n, int& i, int& j) {
-  i = 0;
-  int rem = e;
-  while (rem >= n - i) {
-    rem -= n - i;
-    ++i;
+  for (int i = 0; i < nw; ++i) {
+    const float4 q = red[i];
+    r.x += q.x;
+    r.y += q.y;
+    r.z += q.z;
+    r.w += q.w;
   }
-  j = i + rem;
+  return r;
 }
 
 __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EigShared& sh = *reinterpret_cast<EigShared*>(smem_raw);
   DevCtrl* ctrl = a.ctrl;
-  if (ctrl->converged) return;
   const int tid = threadIdx.x;
   const int n = a.g.nc;
   const int np = n + (n & 1);
+  pdl_trigger();
+  pdl_wait();   // the Gram partials, statistics and control block come from earlier kernels
   EIG_STAMP(0);
   // control scalars and the prior, loaded once in parallel (global latency is long)
   switch (tid) {
+    case 9: sh.flags[2] = ctrl->converged; break;
     case 0: {
       sh.nuc_prev = ctrl->nuclear_cur;
       sh.sig_prev1 = (float)sh.nuc_prev;
@@ -321,20 +326,21 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     default: break;
   }
   if (tid >= 32 && tid < 32 + n) sh.sprev[tid - 32] = a.sigma_prev[tid - 32];
+  __syncthreads();
+  if (sh.flags[2]) return;
 
   // 1. statistics of iteration iter-1 and the stopping rule (float32 partial sums)
   if (a.iter > 1) {
-    float r2 = 0.f, l1 = 0.f, dz2 = 0.f, z2 = 0.f;
-    for (int i = tid; i < a.g.nx; i += kEigThreads) r2 += a.dc_part[i];
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int i = tid; i < a.g.nx; i += kEigThreads) acc.x += a.dc_part[i];
     for (int i = tid; i < a.lrs_parts; i += kEigThreads) {
-      l1 += a.lrs_part[i * 4 + 0];
-      dz2 += a.lrs_part[i * 4 + 1];
-      z2 += a.lrs_part[i * 4 + 2];
+      const float4 q = reinterpret_cast<const float4*>(a.lrs_part)[i];
+      acc.y += q.x;
+      acc.z += q.y;
+      acc.w += q.z;
     }
-    r2 = block_sum_all(r2, sh.red[0]);
-    l1 = block_sum_all(l1, sh.red[1]);
-    dz2 = block_sum_all(dz2, sh.red[2]);
-    z2 = block_sum_all(z2, sh.red[3]);
+    acc = block_sum4(acc, sh.red4);
+    const float r2 = acc.x, l1 = acc.y, dz2 = acc.z, z2 = acc.w;
     // float32 on every thread (float64 issues at a small fraction of the float32 rate)
     const float rel = sqrtf(dz2 / fmaxf(z2, 1e-30f));
     const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
@@ -358,18 +364,25 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   if (a.finalize) return;
   EIG_STAMP(1);
 
-  // 2. Gram matrix: kSub interleaved compensated sub-sums per upper-triangle entry, then a
-  //    fixed-order combination.
+  // 2. Gram matrix: kSub interleaved float32 chunk sums per upper-triangle entry (loads of a
+  //    chunk issued together), then a fixed-order combination.
   const int nn = n * n;
   const int nut = n * (n + 1) / 2;
   float2* sub = sh.A0;   // scratch [kSub][nut], spans A0 and A1 (free until the Jacobi)
   build_tables(&sh.tab, np);
+  if (tid < n) {
+    int e = tid * n - tid * (tid - 1) / 2;
+    for (int j = tid; j < n; ++j, ++e) {
+      sh.tri[0][e] = (unsigned char)tid;
+      sh.tri[1][e] = (unsigned char)j;
+    }
+  }
+  __syncthreads();
   for (int task = tid; task < kSub * nut; task += kEigThreads) {
-    const int e = task % nut, part = task / nut;
-    int i, j;
-    tri_index(e, n, i, j);
+    const int part = task / nut, e = task - part * nut;
+    const int i = sh.tri[0][e], j = sh.tri[1][e];
     const float2* src = a.gram_part + i * n + j;
-    float sx = 0.f, sy = 0.f, cx = 0.f, cy = 0.f;
+    float sx = 0.f, sy = 0.f;
     constexpr int U = 16;
     for (int p0 = part; p0 < a.nparts; p0 += kSub * U) {
       float2 v[U];
@@ -380,20 +393,15 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       }
 #pragma unroll
       for (int q = 0; q < U; ++q) {
-        const float yx = v[q].x - cx, yy = v[q].y - cy;
-        const float tx = sx + yx, ty = sy + yy;
-        cx = (tx - sx) - yx;
-        cy = (ty - sy) - yy;
-        sx = tx;
-        sy = ty;
+        sx += v[q].x;
+        sy += v[q].y;
       }
     }
     sub[part * nut + e] = make_float2(sx, sy);
   }
   __syncthreads();
   for (int e = tid; e < nut; e += kEigThreads) {
-    int i, j;
-    tri_index(e, n, i, j);
+    const int i = sh.tri[0][e], j = sh.tri[1][e];
     float2 s = sub[e];
     for (int q = 1; q < kSub; ++q) s = cadd(s, sub[q * nut + e]);
     if (i == j) s.y = 0.f;
@@ -422,8 +430,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
     __syncthreads();
     for (int e = tid; e < nut; e += kEigThreads) {
-      int i, j;
-      tri_index(e, n, i, j);
+      const int i = sh.tri[0][e], j = sh.tri[1][e];
       float2 s = make_float2(0.f, 0.f);
       for (int k = 0; k < n; ++k) s = cadd(s, cmulc(sh.V[k * kLd + i], sh.A1[k * kLd + j]));
       if (i == j) s.y = 0.f;
@@ -473,8 +480,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       if (i >= n || j >= n) d.A0[i * kLd + j] = make_double2(0.0, 0.0);
     }
     for (int e = tid; e < nut; e += kEigThreads) {
-      int i, j;
-      tri_index(e, n, i, j);
+      const int i = sh.tri[0][e], j = sh.tri[1][e];
       double2 s = make_double2(0.0, 0.0);
       for (int k = 0; k < n; ++k) s = add_(s, mulc_(d.V[k * kLd + i], d.T[k * kLd + j]));
       if (i == j) s.y = 0.0;
@@ -597,8 +603,8 @@ cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     set_for = sizeof(EigShared) + sizeof(EigShared64);
   }
-  k_eig<<<1, kEigThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_eig, dim3(1), dim3(kEigThreads), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace lps

@@ -108,7 +108,6 @@ __device__ __forceinline__ void haar_inv(float2 (&r)[8], int u, int lane) {
 template <int J>
 __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
-  if (a.ctrl->converged) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int nc = g.nc, ldm = nc + 1;
   const int tpc = 32 / nc;                           // tiles per CTA
@@ -126,7 +125,16 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const long long nxy = (long long)g.nx * g.ny;
   const long long rowoff = (long long)z * nxy + (long long)(tx * 8 + u) * g.ny + ty * 8;
   const bool maxonly = a.haar_max_only != 0;
+  // this lane's 8 coefficients are bits [u*8, u*8+8) of the (z, tile) 64-bit group
+  const long long wbase = ((long long)(z * (g.nx >> 3) + tx) * nty + ty) * 2;
 
+  pdl_trigger();
+  pdl_wait();   // X, L, S, W and the control block come from the preceding kernels
+  // Every independent global load is issued up front: their latencies overlap.
+  const int conv = a.ctrl->converged;
+  const float lamS = a.ctrl->lambda_S;
+  const int has_sup = a.persist->has_sup;
+  const unsigned prior_word = (act && !maxonly) ? a.sup_prior[wbase + (u >> 2)] : 0u;
   float2 Xr[8], Lp[8], So[8];
 #pragma unroll
   for (int v = 0; v < 8; ++v) Xr[v] = Lp[v] = So[v] = make_float2(0.f, 0.f);
@@ -151,6 +159,9 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
       }
     }
   }
+  if (!maxonly)
+    for (int i = tid; i < nc * nc; i += kThreads) Wsh[i] = a.W[i];
+  if (conv) return;
 
   if (maxonly) {
     haar_fwd<J>(Xr, u, lane);
@@ -168,19 +179,13 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
 #pragma unroll
     for (int v = 0; v < 8; ++v) mrow[v * 8 * ldm] = csub(Xr[v], So[v]);
   }
-  for (int i = tid; i < nc * nc; i += kThreads) Wsh[i] = a.W[i];
 
   // Sparse step on D = X - L_prev: Haar analysis, support-aware shrink, synthesis.
   float2 D[8];
 #pragma unroll
   for (int v = 0; v < 8; ++v) D[v] = csub(Xr[v], Lp[v]);
   haar_fwd<J>(D, u, lane);
-  const float lamS = a.ctrl->lambda_S;
-  const bool has_sup = a.persist->has_sup != 0;
-  // this lane's 8 coefficients are bits [u*8, u*8+8) of the (z, tile) 64-bit group
-  const long long wbase = ((long long)(z * (g.nx >> 3) + tx) * nty + ty) * 2;
-  unsigned keepbits = 0;
-  if (act && has_sup) keepbits = (a.sup_prior[wbase + (u >> 2)] >> ((u & 3) * 8)) & 0xffu;
+  const unsigned keepbits = has_sup ? (prior_word >> ((u & 3) * 8)) & 0xffu : 0u;
   float l1 = 0.f;
   unsigned sbits = 0;
 #pragma unroll
@@ -308,8 +313,8 @@ static cudaError_t launch_lrs_j(const LrsArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_lrs<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_lrs<J><<<lrs_blocks(a.g), kThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  cudaError_t e = launch_pdl(k_lrs<J>, dim3(lrs_blocks(a.g)), dim3(kThreads), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {

@@ -129,6 +129,11 @@ struct lps_plan {
   DevPersist* persist = nullptr;
   DevCtrl* ctrl = nullptr;
   IterRec* hist = nullptr;
+  // The small per-plan buffers (control block, statistics, Gram partials, W, V, sigma,
+  // bitmaps, line table, twiddles) live in one contiguous allocation so that a kernel
+  // starting on any SM touches few address-translation pages.
+  unsigned char* arena = nullptr;
+  size_t arena_bytes = 0, arena_used = 0;
   // pinned host mirrors; h_persist and h_lines are the sources of stream-ordered uploads and
   // are rewritten only after `upload_done` (recorded after the previous upload) completes
   DevCtrl* h_ctrl = nullptr;
@@ -158,6 +163,33 @@ int dalloc(lps_plan* P, T** ptr, size_t count) {
   CK(cudaMalloc((void**)ptr, b > 0 ? b : 16));
   P->dev_bytes += b;
   return LPS_OK;
+}
+
+// Carve `count` elements from the plan's arena (256-byte aligned).
+template <typename T>
+int aalloc(lps_plan* P, T** ptr, size_t count) {
+  const size_t b = ((count * sizeof(T) + 255) / 256) * 256;
+  if (P->arena_used + b > P->arena_bytes) {
+    set_err("internal arena overflow");
+    return LPS_ERR_OOM;
+  }
+  *ptr = reinterpret_cast<T*>(P->arena + P->arena_used);
+  P->arena_used += b;
+  return LPS_OK;
+}
+
+size_t arena_size(const Geom& g, int max_iters) {
+  auto r = [](size_t b) { return ((b + 255) / 256) * 256; };
+  size_t s = 0;
+  s += r((size_t)g.nx * g.nc * g.nc * sizeof(float2));   // gram partials
+  s += 2 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V
+  s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
+  s += r((size_t)g.plane * sizeof(int));                  // line table
+  s += r((size_t)g.nx * sizeof(float)) + r((size_t)g.ntiles * 4 * sizeof(float));
+  s += 2 * r((size_t)g.nc * sizeof(double));
+  s += 2 * r((size_t)(g.N / 32) * sizeof(uint32_t));
+  s += r(sizeof(DevPersist)) + r(sizeof(DevCtrl)) + r((size_t)(max_iters + 2) * sizeof(IterRec));
+  return s;
 }
 
 int validate(const lps_params* p, Geom* gout) {
@@ -215,10 +247,7 @@ int validate(const lps_params* p, Geom* gout) {
 int free_plan(lps_plan* P) {
   if (!P) return LPS_OK;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
-  void* bufs[] = {P->X,        P->L,        P->S,       P->R,         P->coils,     P->dhyb,      P->kstage,
-                  P->hscratch, P->istage,   P->W,       P->V,         P->gram_part, P->tw_x,      P->tw_y,
-                  P->tw_z,     P->lines,    P->dc_part, P->lrs_part,  P->sigma_out, P->sigma_prev, P->sup_out,
-                  P->sup_prior, P->persist, P->ctrl,    P->hist};
+  void* bufs[] = {P->X, P->L, P->S, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
@@ -588,22 +617,24 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = dalloc(P, &P->R, N))) return fail(rc);
   if ((rc = dalloc(P, &P->istage, N))) return fail(rc);
   if ((rc = dalloc(P, &P->coils, N * g.ncoil))) return fail(rc);
-  if ((rc = dalloc(P, &P->W, (size_t)g.nc * g.nc))) return fail(rc);
-  if ((rc = dalloc(P, &P->V, (size_t)g.nc * g.nc))) return fail(rc);
-  if ((rc = dalloc(P, &P->gram_part, (size_t)g.nx * g.nc * g.nc))) return fail(rc);
-  if ((rc = dalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
-  if ((rc = dalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
-  if ((rc = dalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
-  if ((rc = dalloc(P, &P->lines, (size_t)g.plane))) return fail(rc);
-  if ((rc = dalloc(P, &P->dc_part, (size_t)g.nx))) return fail(rc);
-  if ((rc = dalloc(P, &P->lrs_part, (size_t)g.ntiles * 4))) return fail(rc);
-  if ((rc = dalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
-  if ((rc = dalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
-  if ((rc = dalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
-  if ((rc = dalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
-  if ((rc = dalloc(P, &P->persist, 1))) return fail(rc);
-  if ((rc = dalloc(P, &P->ctrl, 1))) return fail(rc);
-  if ((rc = dalloc(P, &P->hist, (size_t)p->max_iters + 2))) return fail(rc);
+  P->arena_bytes = arena_size(g, p->max_iters);
+  if ((rc = dalloc(P, &P->arena, P->arena_bytes))) return fail(rc);
+  if ((rc = aalloc(P, &P->ctrl, 1))) return fail(rc);
+  if ((rc = aalloc(P, &P->persist, 1))) return fail(rc);
+  if ((rc = aalloc(P, &P->W, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->V, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx))) return fail(rc);
+  if ((rc = aalloc(P, &P->lrs_part, (size_t)g.ntiles * 4))) return fail(rc);
+  if ((rc = aalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
+  if ((rc = aalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
+  if ((rc = aalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
+  if ((rc = aalloc(P, &P->lines, (size_t)g.plane))) return fail(rc);
+  if ((rc = aalloc(P, &P->hist, (size_t)p->max_iters + 2))) return fail(rc);
+  if ((rc = aalloc(P, &P->gram_part, (size_t)g.nx * g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
+  if ((rc = aalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
   if (cudaMallocHost((void**)&P->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMallocHost((void**)&P->h_persist, sizeof(DevPersist)) != cudaSuccess ||
       cudaMallocHost((void**)&P->h_lines, (size_t)g.plane * sizeof(int)) != cudaSuccess) {
@@ -794,6 +825,15 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
   }
   return LPS_OK;
 }
+
+#ifdef LPS_EIG_PHASE_TIMING
+// probe-only: launch the eigen kernel `reps` times back to back (iteration ids 4000 + r)
+int lps_probe_eig_repeat(lps_plan* P, int reps) {
+  for (int r = 0; r < reps; ++r) LK(launch_eig(eig_args(P, 4000 + r, 0), P->st));
+  CK(cudaStreamSynchronize(P->st));
+  return LPS_OK;
+}
+#endif
 
 int lps_set_profiling(lps_plan* P, int on) {
   ARG(P != nullptr, "plan is NULL");
