@@ -204,6 +204,27 @@ int lps_get_kernel_times(lps_plan* plan, lps_kernel_times* out);
 int lps_session_export(lps_plan* plan, void* buf, size_t* bytes);
 int lps_session_import(lps_plan* plan, const void* buf, size_t bytes);
 
+/* Adjoint operator E^H without any device allocation. The paper has no counterpart: this
+ * entry point exists for callers that cannot allocate device memory when they need the
+ * operator -- code running while another component owns the device memory pool, real-time
+ * loops that forbid allocation after start-up, callers that must not risk the device-wide
+ * synchronisation an allocation can cause. It needs no plan and calls no allocating routine:
+ * its scratch (line table, twiddles, samples moved to hybrid space) is one file-scope device
+ * array of LPS_NOALLOC_SCRATCH_BYTES, reserved on every GPU that loads the library until the
+ * process exits. Sizes whose scratch would exceed it return LPS_ERR_UNSUPPORTED.
+ *   mask   host   uint8 [nz][ny] (nonzero = sampled), as for lps_set_mask
+ *   coils  device complex64 [ncoil][nz][nx][ny]
+ *   kdata  device complex64 [ncoil][nlines][nx], nlines = set entries of mask
+ *   image  device complex64 [nz][nx][ny], written
+ *   stream cudaStream_t (NULL = legacy default stream); the work is enqueued there.
+ * The first call on a device looks up the array's device address once (with that device
+ * current); make that first call before any stream capture. All calls share the array and
+ * it keeps the last call's contents: calls whose work overlaps on the GPU (other streams or
+ * other host threads) race on it and must be ordered by the caller. */
+#define LPS_NOALLOC_SCRATCH_BYTES (16u << 20)
+int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z, const uint8_t* mask, const void* coils,
+                        const void* kdata, int nlines, void* image, void* stream);
+
 size_t lps_support_words(const lps_params* p);
 const char* lps_status_string(int status);
 const char* lps_last_error(void);

@@ -533,6 +533,11 @@ int need_ready(lps_plan* P) {
 
 }  // namespace
 
+namespace lps {
+// Validated geometry of a parameter set (used by entry points that run without a plan).
+int make_geom(const lps_params* p, Geom* g) { return validate(p, g); }
+}  // namespace lps
+
 extern "C" {
 
 int lps_version(void) { return 1; }

@@ -30,6 +30,7 @@ ERR_UNSUPPORTED = -8
 EIG_FP32, EIG_FP64 = 0, 1
 SUPPORT_THRESHOLD, SUPPORT_NONZERO = 0, 1
 MAX_NC = 32
+NOALLOC_SCRATCH_BYTES = 16 << 20
 
 
 class Params(C.Structure):
@@ -103,6 +104,8 @@ _SIGS = {
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
+    "lps_adjoint_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_int, _VP, _VP],
+                            C.c_int),
     "lps_session_export": ([_VP, _VP, C.POINTER(C.c_size_t)], C.c_int),
     "lps_session_import": ([_VP, _VP, C.c_size_t], C.c_int),
 }
@@ -291,6 +294,14 @@ def get_kernel_times(plan: int) -> KernelTimes:
     t = KernelTimes()
     _check(load().lps_get_kernel_times(plan, C.byref(t)), "get_kernel_times")
     return t
+
+
+def adjoint_noalloc(nx: int, ny: int, nz: int, ncoil: int, mask, coils, kdata, nlines: int, image,
+                    fft_z: int = 1, stream=None):
+    """E^H without any device allocation (scratch in a fixed device array of the library);
+    for callers that cannot allocate device memory at the point of use."""
+    _check(load().lps_adjoint_noalloc(nx, ny, nz, ncoil, fft_z, ptr(mask), ptr(coils), ptr(kdata), nlines,
+                                      ptr(image), _stream(stream)), "adjoint_noalloc")
 
 
 def session_export(plan: int) -> bytes:
