@@ -8,7 +8,15 @@
 //   - the plane Gram epilogue assigns one warp per (i <= j) column pair, lanes across y.
 #include "lps_internal.cuh"
 
+#include <cooperative_groups.h>
+
+namespace cg = cooperative_groups;
+
 namespace lps {
+
+// CTAs (x-planes) per cluster: their plane Grams are summed through distributed shared
+// memory, so the eigen kernel reads nx / kGramCluster partials instead of nx.
+constexpr int kGramCluster = 4;
 
 __host__ __device__ constexpr int ct_radix(int rem) {
   return (rem % 16 == 0 && rem != 32) ? 16
@@ -304,11 +312,11 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   }
   __syncthreads();
   if (a.gram_part) {
-    // one warp per column pair (i <= j); lanes across y; shuffle reduction
+    // Plane Gram into shared memory: one warp per column pair (i <= j), lanes across y.
     constexpr int NPAIR = NZ * (NZ + 1) / 2;
     constexpr int NW = NTH / 32;
     const int w = tid >> 5, lane = tid & 31;
-    float2* gp = a.gram_part + (long long)x * NZ * NZ;
+    float2* gsm = base + PLANEP;   // group 0's second FFT buffer is free now
     for (int pr = w; pr < NPAIR; pr += NW) {
       int i = 0, rem = pr;
       while (rem >= NZ - i) {
@@ -331,10 +339,23 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
         si += __shfl_xor_sync(0xffffffffu, si, o);
       }
       if (lane == 0) {
-        gp[i * NZ + j] = make_float2(sr, si);
-        if (i != j) gp[j * NZ + i] = make_float2(sr, -si);
+        gsm[i * NZ + j] = make_float2(sr, si);
+        if (i != j) gsm[j * NZ + i] = make_float2(sr, -si);
       }
     }
+    // Cluster sum in a fixed rank order: CTA `rank` adds entries e = rank (mod cluster) over
+    // the cluster's planes and writes the cluster's partial.
+    cg::cluster_group cl = cg::this_cluster();
+    cl.sync();
+    const int rank = (int)cl.block_rank();
+    float2* gp = a.gram_part + (long long)(x / kGramCluster) * NZ * NZ;
+    for (int e = rank + kGramCluster * tid; e < NZ * NZ; e += kGramCluster * NTH) {
+      float2 acc2 = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int r = 0; r < kGramCluster; ++r) acc2 = cadd(acc2, cl.map_shared_rank(gsm, r)[e]);
+      gp[e] = acc2;
+    }
+    cl.sync();   // no CTA leaves while another still reads its shared memory
   }
   if (MODE == kDcUpdate && a.dc_part) {
     const float tot = block_sum(resid, red);
@@ -347,14 +368,28 @@ static cudaError_t launch_fixed(const DcArgs& a, cudaStream_t st) {
   using Lay = DcFixedLayout<NY, NZ, NCG, NT>;
   constexpr size_t smem = Lay::bytes();
   static_assert(smem <= 227 * 1024, "plane does not fit shared memory");
-  static bool attr = false;
-  if (!attr) {
+  static bool attr_set = false;
+  if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_dc_fixed<NY, NZ, NCG, NT, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    attr = true;
+    attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_dc_fixed<NY, NZ, NCG, NT, MODE>, dim3(a.g.nx), dim3(NCG * NT), smem, st, a);
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(a.g.nx);
+  cfg.blockDim = dim3(NCG * NT);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = kGramCluster;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dc_fixed<NY, NZ, NCG, NT, MODE>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -367,10 +402,19 @@ static cudaError_t launch_fixed_mode(const DcArgs& a, int mode, cudaStream_t st)
   }
 }
 
+static bool has_fixed(const Geom& g) {
+  if (g.nx % kGramCluster != 0) return false;   // the grid is made of whole clusters (nx % 8 == 0 anyway)
+  return (g.ny == 128 && g.nz == 16) || (g.ny == 192 && g.nz == 32) || (g.ny == 32 && g.nz == 8);
+}
+
+// Number of Gram partials the data-consistency step leaves for the eigen kernel.
+int dc_gram_parts(const Geom& g) { return has_fixed(g) ? g.nx / kGramCluster : g.nx; }
+
 // Returns cudaErrorNotSupported when no specialisation matches (the caller falls back to the
 // runtime-sized kernel).
 cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st) {
   const Geom& g = a.g;
+  if (!has_fixed(g)) return cudaErrorNotSupported;
   if (g.ny == 128 && g.nz == 16) return launch_fixed_mode<128, 16, 2, 256>(a, mode, st);
   if (g.ny == 192 && g.nz == 32) return launch_fixed_mode<192, 32, 1, 512>(a, mode, st);
   if (g.ny == 32 && g.nz == 8) return launch_fixed_mode<32, 8, 1, 256>(a, mode, st);

@@ -5,8 +5,8 @@
 //   1. records the statistics of the previous iteration (residual, nuclear norm, l1 off the
 //      prior support, objective, relative change) and applies the stopping rule (Sec. 3:
 //      stop when the relative change of the solution falls below the tolerance);
-//   2. sums the per-plane Gram partials in a fixed order (compensated float32, kSub
-//      interleaved sub-sums per entry combined in a fixed order);
+//   2. sums the Gram partials of the data-consistency step in float32 (one or two
+//      interleaved chunk sums per entry, combined in a fixed order);
 //   3. diagonalises G by cyclic two-sided Jacobi rotations in round-robin order, starting
 //      from A = V_prev^H G V_prev with the previous eigenvectors; each step computes the
 //      nc/2 disjoint rotations, then updates every element of A (J^H A J) and every column
@@ -23,7 +23,6 @@ namespace lps {
 
 constexpr int kEigThreads = 512;
 constexpr int kLd = kMaxNc + 1;   // leading dimension of the shared matrices
-constexpr int kSub = 4;           // sub-sums per Gram entry
 
 #ifdef LPS_EIG_PHASE_TIMING
 __device__ unsigned long long g_eig_phase[4096][8];
@@ -298,6 +297,32 @@ __device__ __forceinline__ float4 block_sum4(float4 v, float4* red) {
   return r;
 }
 
+// One chunk sum of a Gram entry over the partials: task = part * nn + e sums partials
+// part, part + ksub, part + 2 ksub, ... of entry e, sixteen loads in flight at a time.
+// Every partial holds an exactly Hermitian matrix and all entries are summed in the same
+// order, so the result is exactly Hermitian too.
+__device__ __forceinline__ float2 gram_chunk(const float2* __restrict__ gram_part, int task, int nn, int ksub,
+                                             int nparts) {
+  const int part = task / nn, e = task - part * nn;
+  const float2* src = gram_part + e;
+  constexpr int U = 16;
+  float sx = 0.f, sy = 0.f;
+  for (int p0 = part; p0 < nparts; p0 += ksub * U) {
+    float2 v[U];
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      const int pp = p0 + q * ksub;
+      v[q] = pp < nparts ? src[(long long)pp * nn] : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int q = 0; q < U; ++q) {
+      sx += v[q].x;
+      sy += v[q].y;
+    }
+  }
+  return make_float2(sx, sy);
+}
+
 __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EigShared& sh = *reinterpret_cast<EigShared*>(smem_raw);
@@ -308,7 +333,11 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   pdl_trigger();
   pdl_wait();   // the Gram partials, statistics and control block come from earlier kernels
   EIG_STAMP(0);
-  // control scalars and the prior, loaded once in parallel (global latency is long)
+  const int nn = n * n;
+  const int nut = n * (n + 1) / 2;
+  const bool tol_on = a.tol > 0.0;
+  // Every independent global load of the kernel is issued before the first barrier: control
+  // scalars, the prior, the previous eigenvectors, the Gram partials and the statistics.
   switch (tid) {
     case 9: sh.flags[2] = ctrl->converged; break;
     case 0: {
@@ -326,27 +355,56 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     default: break;
   }
   if (tid >= 32 && tid < 32 + n) sh.sprev[tid - 32] = a.sigma_prev[tid - 32];
+  if (!a.finalize)
+    for (int e = tid; e < nn; e += kEigThreads) sh.V[(e / n) * kLd + e % n] = a.V[e];
+  // statistics of iteration iter-1: the last warp
+  const int sw = (kEigThreads >> 5) - 1;
+  float4 st4 = make_float4(0.f, 0.f, 0.f, 0.f);
+  if ((tid >> 5) == sw && a.iter > 1) {
+    const int lane = tid & 31;
+    for (int i = lane; i < a.g.nx; i += 32) st4.x += a.dc_part[i];
+    for (int i = lane; i < a.lrs_parts; i += 32) {
+      const float4 q = reinterpret_cast<const float4*>(a.lrs_part)[i];
+      st4.y += q.x;
+      st4.z += q.y;
+      st4.w += q.z;
+    }
+  }
+  // Gram partials: all n x n entries, ksub interleaved chunks per entry
+  const int ksub = nn <= kEigThreads / 2 ? 2 : 1;
+  float2* sub = sh.A0;   // scratch [ksub][nn], spans A0 and A1 (free until the Jacobi)
+  // at most two tasks per thread: ksub * nn <= 2 * kEigThreads (n <= 32)
+  float2 gacc0 = make_float2(0.f, 0.f), gacc1 = make_float2(0.f, 0.f);
+  if (!a.finalize) {
+    gacc0 = gram_chunk(a.gram_part, tid, nn, ksub, a.nparts);
+    if (tid + kEigThreads < ksub * nn) gacc1 = gram_chunk(a.gram_part, tid + kEigThreads, nn, ksub, a.nparts);
+  }
+  build_tables(&sh.tab, np);
+  if (tid < n) {
+    int e = tid * n - tid * (tid - 1) / 2;
+    for (int j = tid; j < n; ++j, ++e) {
+      sh.tri[0][e] = (unsigned char)tid;
+      sh.tri[1][e] = (unsigned char)j;
+    }
+  }
   __syncthreads();
   if (sh.flags[2]) return;
 
-  // 1. statistics of iteration iter-1 and the stopping rule (float32 partial sums)
-  if (a.iter > 1) {
-    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int i = tid; i < a.g.nx; i += kEigThreads) acc.x += a.dc_part[i];
-    for (int i = tid; i < a.lrs_parts; i += kEigThreads) {
-      const float4 q = reinterpret_cast<const float4*>(a.lrs_part)[i];
-      acc.y += q.x;
-      acc.z += q.y;
-      acc.w += q.z;
+  // 1. statistics record and the stopping rule
+  if (a.iter > 1 && (tid >> 5) == sw) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      st4.x += __shfl_xor_sync(0xffffffffu, st4.x, o);
+      st4.y += __shfl_xor_sync(0xffffffffu, st4.y, o);
+      st4.z += __shfl_xor_sync(0xffffffffu, st4.z, o);
+      st4.w += __shfl_xor_sync(0xffffffffu, st4.w, o);
     }
-    acc = block_sum4(acc, sh.red4);
-    const float r2 = acc.x, l1 = acc.y, dz2 = acc.z, z2 = acc.w;
-    // float32 on every thread (float64 issues at a small fraction of the float32 rate)
-    const float rel = sqrtf(dz2 / fmaxf(z2, 1e-30f));
-    const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
-    const bool stop = nonfinite || (a.tol > 0.0 && rel < (float)a.tol);
-    const double nuc = sh.nuc_prev;
-    if (tid == 0) {
+    if ((tid & 31) == 0) {
+      const float r2 = st4.x, l1 = st4.y;
+      const float rel = sqrtf(st4.z / fmaxf(st4.w, 1e-30f));
+      const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
+      const bool stop = nonfinite || (tol_on && rel < (float)a.tol);
+      const double nuc = sh.nuc_prev;
       IterRec& rec = a.hist[a.iter - 2];
       rec.resid2 = r2;
       rec.nuclear = nuc;
@@ -358,68 +416,41 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       ctrl->iters_done = a.iter - 1;
       if (nonfinite) ctrl->err |= kErrNonfinite;
       if (stop) ctrl->converged = 1;
+      sh.flags[3] = stop;
     }
-    if (a.finalize || stop) return;
   }
   if (a.finalize) return;
+  if (tol_on && a.iter > 1) {
+    __syncthreads();
+    if (sh.flags[3]) return;
+  }
   EIG_STAMP(1);
 
-  // 2. Gram matrix: kSub interleaved float32 chunk sums per upper-triangle entry (loads of a
-  //    chunk issued together), then a fixed-order combination.
-  const int nn = n * n;
-  const int nut = n * (n + 1) / 2;
-  float2* sub = sh.A0;   // scratch [kSub][nut], spans A0 and A1 (free until the Jacobi)
-  build_tables(&sh.tab, np);
-  if (tid < n) {
-    int e = tid * n - tid * (tid - 1) / 2;
-    for (int j = tid; j < n; ++j, ++e) {
-      sh.tri[0][e] = (unsigned char)tid;
-      sh.tri[1][e] = (unsigned char)j;
+  // 2. Gram matrix: combine the chunk sums in a fixed order; exact Hermitian symmetry
+  if (tid < ksub * nn) sub[tid] = gacc0;
+  if (tid + kEigThreads < ksub * nn) sub[tid + kEigThreads] = gacc1;
+  const bool warm = sh.v_valid != 0;
+  if (!warm)
+    for (int e = tid; e < nn; e += kEigThreads) {
+      const int i = e / n, j = e - i * n;
+      sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
     }
+  for (int e = tid; e < np * np; e += kEigThreads) {
+    const int i = e / np, j = e - (e / np) * np;
+    if (i >= n || j >= n) sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
   }
   __syncthreads();
-  for (int task = tid; task < kSub * nut; task += kEigThreads) {
-    const int part = task / nut, e = task - part * nut;
-    const int i = sh.tri[0][e], j = sh.tri[1][e];
-    const float2* src = a.gram_part + i * n + j;
-    float sx = 0.f, sy = 0.f;
-    constexpr int U = 16;
-    for (int p0 = part; p0 < a.nparts; p0 += kSub * U) {
-      float2 v[U];
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        const int pp = p0 + q * kSub;
-        v[q] = pp < a.nparts ? src[(long long)pp * nn] : make_float2(0.f, 0.f);
-      }
-#pragma unroll
-      for (int q = 0; q < U; ++q) {
-        sx += v[q].x;
-        sy += v[q].y;
-      }
-    }
-    sub[part * nut + e] = make_float2(sx, sy);
-  }
-  __syncthreads();
-  for (int e = tid; e < nut; e += kEigThreads) {
-    const int i = sh.tri[0][e], j = sh.tri[1][e];
+  for (int e = tid; e < nn; e += kEigThreads) {
+    const int i = e / n, j = e - i * n;
     float2 s = sub[e];
-    for (int q = 1; q < kSub; ++q) s = cadd(s, sub[q * nut + e]);
+    for (int q = 1; q < ksub; ++q) s = cadd(s, sub[q * nn + e]);
     if (i == j) s.y = 0.f;
     sh.G[i * kLd + j] = s;
-    sh.G[j * kLd + i] = cconj(s);
   }
   __syncthreads();
   EIG_STAMP(2);
 
   // 3. Jacobi, warm-started from the previous eigenvectors
-  const bool warm = sh.v_valid != 0;
-  for (int e = tid; e < np * np; e += kEigThreads) {
-    const int i = e / np, j = e - (e / np) * np;
-    float2 vv = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-    if (warm && i < n && j < n) vv = a.V[i * n + j];
-    sh.V[i * kLd + j] = vv;
-  }
-  __syncthreads();
   if (warm) {
     // A1 = G V, then A0 = V^H A1 (upper triangle, mirrored: exactly Hermitian)
     for (int e = tid; e < nn; e += kEigThreads) {
@@ -438,9 +469,11 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       sh.A0[j * kLd + i] = cconj(s);
     }
   } else {
-    for (int e = tid; e < nn; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
-      sh.A0[i * kLd + j] = sh.G[i * kLd + j];
+    for (int e = tid; e < nut; e += kEigThreads) {
+      const int i = sh.tri[0][e], j = sh.tri[1][e];
+      const float2 g = sh.G[i * kLd + j];
+      sh.A0[i * kLd + j] = g;
+      sh.A0[j * kLd + i] = cconj(g);
     }
   }
   for (int e = tid; e < np * np; e += kEigThreads) {

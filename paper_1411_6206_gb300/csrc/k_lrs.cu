@@ -256,32 +256,45 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   if (tid == 0) part[3] = r;
 }
 
-// Plane share of the Casorati Gram (X - S)^H (X - S) straight from global memory; used
-// when the state is loaded from outside rather than produced by the data-consistency step.
+// Partials of the Casorati Gram (X - S)^H (X - S) straight from global memory; used when
+// the state is loaded from outside rather than produced by the data-consistency step. CTA p
+// sums the planes x = p q .. p q + q - 1 (q = nx / nparts), so the eigen kernel finds the
+// same number of partials as the data-consistency step leaves.
 __global__ void __launch_bounds__(kThreads) k_gram_plane(const float2* X, const float2* S, Geom g,
-                                                         float2* gram_part) {
+                                                         float2* gram_part, int nparts) {
   extern __shared__ __align__(16) unsigned char smem[];
   float2* M = reinterpret_cast<float2*>(smem);   // [nz][nyp]
-  const int x = blockIdx.x, ny = g.ny, nyp = g.nyp, nc = g.nc;
+  const int ny = g.ny, nyp = g.nyp, nc = g.nc;
+  const int q = g.nx / nparts;
   const long long nxy = (long long)g.nx * ny;
-  for (int e = threadIdx.x; e < g.plane; e += kThreads) {
-    const int z = e / ny, y = e - (e / ny) * ny;
-    const long long gi = z * nxy + (long long)x * ny + y;
-    M[z * nyp + y] = csub(X[gi], S[gi]);
-  }
-  __syncthreads();
-  float2* gp = gram_part + (long long)x * nc * nc;
-  for (int t = threadIdx.x; t < nc * nc; t += kThreads) {
-    const int i = t / nc, j = t - (t / nc) * nc;
-    if (i > j) continue;
-    float sr = 0.f, si = 0.f;
-    for (int y = 0; y < ny; ++y) {
-      const float2 p = M[i * nyp + y], q = M[j * nyp + y];
-      sr = fmaf(p.x, q.x, fmaf(p.y, q.y, sr));
-      si = fmaf(p.x, q.y, fmaf(-p.y, q.x, si));
+  float2* gp = gram_part + (long long)blockIdx.x * nc * nc;
+  for (int x = blockIdx.x * q; x < (int)(blockIdx.x + 1) * q; ++x) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < g.plane; e += kThreads) {
+      const int z = e / ny, y = e - (e / ny) * ny;
+      const long long gi = z * nxy + (long long)x * ny + y;
+      M[z * nyp + y] = csub(X[gi], S[gi]);
     }
-    gp[i * nc + j] = make_float2(sr, si);
-    if (i != j) gp[j * nc + i] = make_float2(sr, -si);
+    __syncthreads();
+    const bool first = x == (int)blockIdx.x * q;
+    // each thread owns its entries across the planes, so the running sums need no barrier
+    for (int t = threadIdx.x; t < nc * nc; t += kThreads) {
+      const int i = t / nc, j = t - (t / nc) * nc;
+      if (i > j) continue;
+      float sr = 0.f, si = 0.f;
+      for (int y = 0; y < ny; ++y) {
+        const float2 u = M[i * nyp + y], v = M[j * nyp + y];
+        sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
+        si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
+      }
+      if (!first) {
+        const float2 o = gp[i * nc + j];
+        sr += o.x;
+        si += o.y;
+      }
+      gp[i * nc + j] = make_float2(sr, si);
+      if (i != j) gp[j * nc + i] = make_float2(sr, -si);
+    }
   }
 }
 
@@ -325,15 +338,16 @@ cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
   }
 }
 
-cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part,
+cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part, int nparts,
                               cudaStream_t st) {
+  if (nparts <= 0 || g.nx % nparts != 0) return cudaErrorInvalidValue;
   const size_t smem = (size_t)g.planeP * sizeof(float2);
   if (smem > 48 * 1024) {
     cudaError_t e =
         cudaFuncSetAttribute(k_gram_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  k_gram_plane<<<g.nx, kThreads, smem, st>>>(X, S, g, gram_part);
+  k_gram_plane<<<nparts, kThreads, smem, st>>>(X, S, g, gram_part, nparts);
   return cudaGetLastError();
 }
 

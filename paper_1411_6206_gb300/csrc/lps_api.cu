@@ -13,7 +13,7 @@
 using namespace lps;
 
 namespace lps {
-cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part,
+cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part, int nparts,
                               cudaStream_t st);
 cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long long n, cudaStream_t st);
 }  // namespace lps
@@ -134,13 +134,18 @@ struct lps_plan {
   // starting on any SM touches few address-translation pages.
   unsigned char* arena = nullptr;
   size_t arena_bytes = 0, arena_used = 0;
-  // pinned host mirrors; h_persist and h_lines are the sources of stream-ordered uploads and
-  // are rewritten only after `upload_done` (recorded after the previous upload) completes
+  // Host-owned persistent fields; the device copy is refreshed by stream-ordered uploads.
+  DevPersist hp{};
+  // Pinned upload sources, a ring of kSlots: an upload takes the next slot, waiting only for
+  // the upload made kSlots uploads earlier from it, so the host can queue several frames
+  // ahead of the device.
+  static constexpr int kSlots = 8;
   DevCtrl* h_ctrl = nullptr;
-  DevPersist* h_persist = nullptr;
-  int* h_lines = nullptr;
-  cudaEvent_t upload_done = nullptr;
-  bool upload_pending = false;
+  DevPersist* h_persist_slots = nullptr;   // [kSlots]
+  int* h_lines_slots = nullptr;            // [kSlots][plane]
+  cudaEvent_t slot_done[kSlots] = {};
+  bool slot_pending[kSlots] = {};
+  int slot_next = 0;
   // host state
   int nlines = 0, m_cap = 0;
   bool have_mask = false, have_coils = false, have_data = false, state_ready = false;
@@ -251,9 +256,10 @@ int free_plan(lps_plan* P) {
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
-  if (P->h_persist) cudaFreeHost(P->h_persist);
-  if (P->h_lines) cudaFreeHost(P->h_lines);
-  if (P->upload_done) cudaEventDestroy(P->upload_done);
+  if (P->h_persist_slots) cudaFreeHost(P->h_persist_slots);
+  if (P->h_lines_slots) cudaFreeHost(P->h_lines_slots);
+  for (int k = 0; k < lps_plan::kSlots; ++k)
+    if (P->slot_done[k]) cudaEventDestroy(P->slot_done[k]);
   if (P->cap) cudaStreamDestroy(P->cap);
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
   delete P;
@@ -262,23 +268,35 @@ int free_plan(lps_plan* P) {
 
 size_t support_words(const Geom& g) { return (size_t)(g.N / 32); }
 
-// Wait until the pinned upload sources may be rewritten (the previous upload has landed).
-int wait_upload(lps_plan* P) {
-  if (P->upload_pending) {
-    CK(cudaEventSynchronize(P->upload_done));
-    P->upload_pending = false;
+// Next pinned staging slot, once the upload last made from it has landed.
+int acquire_slot(lps_plan* P, int* slot) {
+  const int k = P->slot_next;
+  if (P->slot_pending[k]) {
+    CK(cudaEventSynchronize(P->slot_done[k]));
+    P->slot_pending[k] = false;
   }
+  *slot = k;
+  return LPS_OK;
+}
+
+// Marks the uploads enqueued from `slot` and moves to the next slot.
+int release_slot(lps_plan* P, int slot) {
+  CK(cudaEventRecord(P->slot_done[slot], P->st));
+  P->slot_pending[slot] = true;
+  P->slot_next = (slot + 1) % lps_plan::kSlots;
   return LPS_OK;
 }
 
 // Host-owned fields: nlines, has_sup, has_sigma; v_valid is written by the eigen kernel and
-// uploaded only when the host resets or restores it.
-int upload_persist(lps_plan* P, bool with_v = false) {
+// uploaded only when the host resets or restores it. `slot` >= 0: already acquired.
+int upload_persist(lps_plan* P, bool with_v = false, int slot = -1) {
+  int rc;
+  if (slot < 0 && (rc = acquire_slot(P, &slot))) return rc;
+  DevPersist* src = P->h_persist_slots + slot;
+  *src = P->hp;
   const size_t n = with_v ? sizeof(DevPersist) : offsetof(DevPersist, v_valid);
-  CK(cudaMemcpyAsync(P->persist, P->h_persist, n, cudaMemcpyHostToDevice, P->st));
-  CK(cudaEventRecord(P->upload_done, P->st));
-  P->upload_pending = true;
-  return LPS_OK;
+  CK(cudaMemcpyAsync(P->persist, src, n, cudaMemcpyHostToDevice, P->st));
+  return release_slot(P, slot);
 }
 
 // Grow the line-dependent buffers to hold m lines.
@@ -381,7 +399,7 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
   EigArgs e{};
   e.g = P->g;
   e.gram_part = P->gram_part;
-  e.nparts = P->g.nx;
+  e.nparts = dc_gram_parts(P->g);
   e.dc_part = P->dc_part;
   e.lrs_part = P->lrs_part;
   e.lrs_parts = lrs_blocks(P->g);
@@ -641,17 +659,21 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
   if ((rc = aalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
   if (cudaMallocHost((void**)&P->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
-      cudaMallocHost((void**)&P->h_persist, sizeof(DevPersist)) != cudaSuccess ||
-      cudaMallocHost((void**)&P->h_lines, (size_t)g.plane * sizeof(int)) != cudaSuccess) {
+      cudaMallocHost((void**)&P->h_persist_slots, lps_plan::kSlots * sizeof(DevPersist)) != cudaSuccess ||
+      cudaMallocHost((void**)&P->h_lines_slots, (size_t)lps_plan::kSlots * g.plane * sizeof(int)) != cudaSuccess) {
     set_err("pinned host allocation failed");
     return fail(LPS_ERR_OOM);
   }
-  std::memset(P->h_persist, 0, sizeof(DevPersist));
-  if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&P->upload_done, cudaEventDisableTiming) != cudaSuccess) {
+  std::memset(&P->hp, 0, sizeof(DevPersist));
+  if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
     set_err("stream creation failed");
     return fail(LPS_ERR_CUDA);
   }
+  for (int k = 0; k < lps_plan::kSlots; ++k)
+    if (cudaEventCreateWithFlags(&P->slot_done[k], cudaEventDisableTiming) != cudaSuccess) {
+      set_err("event creation failed");
+      return fail(LPS_ERR_CUDA);
+    }
   auto up = [&](float2* d, int n) -> int {
     std::vector<float2> t = twiddles(n);
     CK(cudaMemcpy(d, t.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
@@ -713,15 +735,17 @@ int lps_set_mask(lps_plan* P, const uint8_t* mask, int* nlines) {
   ARG(m > 0, "mask has no sampled entry");
   int rc = ensure_lines(P, m);
   if (rc) return rc;
-  if ((rc = wait_upload(P))) return rc;
+  int slot;
+  if ((rc = acquire_slot(P, &slot))) return rc;
+  int* hl = P->h_lines_slots + (size_t)slot * P->g.plane;
   int k = 0;
   for (int a = 0; a < nz; ++a)
     for (int ky = 0; ky < ny; ++ky)
-      if (h[(size_t)a * ny + ky]) P->h_lines[k++] = a * P->g.nyp + ky;
-  CK(cudaMemcpyAsync(P->lines, P->h_lines, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, P->st));
+      if (h[(size_t)a * ny + ky]) hl[k++] = a * P->g.nyp + ky;
+  CK(cudaMemcpyAsync(P->lines, hl, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, P->st));
   P->nlines = m;
-  P->h_persist->nlines = m;
-  if ((rc = upload_persist(P))) return rc;
+  P->hp.nlines = m;
+  if ((rc = upload_persist(P, false, slot))) return rc;
   P->have_mask = true;
   P->have_data = false;
   P->state_ready = false;
@@ -762,20 +786,16 @@ int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev
                        P->st));
   if (sigma_prev)
     CK(cudaMemcpyAsync(P->sigma_prev, sigma_prev, P->g.nc * sizeof(double), cudaMemcpyDefault, P->st));
-  int rc = wait_upload(P);
-  if (rc) return rc;
-  P->h_persist->has_sup = support ? 1 : 0;
-  P->h_persist->has_sigma = sigma_prev ? 1 : 0;
+  P->hp.has_sup = support ? 1 : 0;
+  P->hp.has_sigma = sigma_prev ? 1 : 0;
   return upload_persist(P);
 }
 
 int lps_clear_prior(lps_plan* P) {
   ARG(P != nullptr, "plan is NULL");
-  int rc = wait_upload(P);
-  if (rc) return rc;
-  P->h_persist->v_valid = 0;
-  P->h_persist->has_sup = 0;
-  P->h_persist->has_sigma = 0;
+  P->hp.v_valid = 0;
+  P->hp.has_sup = 0;
+  P->hp.has_sigma = 0;
   return upload_persist(P, true);
 }
 
@@ -807,9 +827,8 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
   P->state_ready = true;
   P->iters_done = P->p.max_iters;
   if (P->p.recursive) {
-    if ((rc = wait_upload(P))) return rc;
-    P->h_persist->has_sup = 1;
-    P->h_persist->has_sigma = 1;
+    P->hp.has_sup = 1;
+    P->hp.has_sigma = 1;
   }
   const size_t img = (size_t)P->g.N * sizeof(float2);
   bool host = false;
@@ -928,7 +947,7 @@ int lps_set_state(lps_plan* P, const void* X, const void* S, const void* L_prev,
   c.sigma_max = 0.0;
   *P->h_ctrl = c;
   CK(cudaMemcpyAsync(P->ctrl, P->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, P->st));
-  LK(launch_gram_plane(P->X, P->S, P->g, P->gram_part, P->st));
+  LK(launch_gram_plane(P->X, P->S, P->g, P->gram_part, dc_gram_parts(P->g), P->st));
   CK(cudaStreamSynchronize(P->st));
   P->state_ready = true;
   P->iters_done = iters_done;
@@ -1097,11 +1116,9 @@ int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
   CK(cudaMemcpy(P->X, i, img, cudaMemcpyHostToDevice));
   i += img;
   CK(cudaMemcpy(P->V, i, vb, cudaMemcpyHostToDevice));
-  int rc = wait_upload(P);
-  if (rc) return rc;
-  P->h_persist->has_sup = h.has_sup;
-  P->h_persist->has_sigma = h.has_sigma;
-  P->h_persist->v_valid = h.v_valid;
+  P->hp.has_sup = h.has_sup;
+  P->hp.has_sigma = h.has_sigma;
+  P->hp.v_valid = h.v_valid;
   return upload_persist(P, true);
 }
 

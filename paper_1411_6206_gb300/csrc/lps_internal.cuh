@@ -147,6 +147,7 @@ size_t dc_smem_bytes(const Geom& g);
 size_t xfft_smem_bytes(const Geom& g);
 int dc_ept(const Geom& g);
 int lrs_blocks(const Geom& g);
+int dc_gram_parts(const Geom& g);
 
 // Launch with programmatic stream serialization: the kernel may start while its predecessor
 // in the stream finishes; it must call pdl_wait() before reading the predecessor's outputs.

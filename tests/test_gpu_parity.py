@@ -67,6 +67,8 @@ SHAPES = [
     (13, 24, 48, 2, 1),      # prime nz = 13
     (12, 16, 16, 2, 0),      # per-slice 2D encode
     (32, 16, 64, 2, 1),      # largest column count
+    (8, 40, 32, 3, 1),       # compile-time plane 32 x 8, ten 4-plane Gram clusters
+    (8, 24, 32, 2, 1),       # same plane, six clusters
     (16, 128, 128, 8, 1),    # cardiac workload plane (compile-time specialised kernel)
     (32, 192, 192, 12, 1),   # precision workload plane (compile-time specialised kernel)
 ]
@@ -94,7 +96,7 @@ def test_forward_adjoint_match_oracle(L, nz, nx, ny, nc, fz):
     pl.close()
 
 
-@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES[:4] + SHAPES[-2:])
+@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES[:4] + SHAPES[-4:])
 def test_data_consistency_step(L, nz, nx, ny, nc, fz):
     case = make_case(nz, nx, ny, nc, seed=3, fft_z=fz)
     pl = plan_for(L, case, nz, nx, ny, nc, fft_z=fz)
@@ -140,7 +142,8 @@ def one_iteration_case(L, nz, nx, ny, nc, with_prior, lam_p=0.5, seed=11, J=3, e
 
 
 @pytest.mark.parametrize("with_prior", [False, True])
-@pytest.mark.parametrize("nz,nx,ny,nc", [(8, 32, 32, 2), (5, 16, 24, 3), (32, 16, 32, 2)])
+@pytest.mark.parametrize("nz,nx,ny,nc", [(8, 32, 32, 2), (5, 16, 24, 3), (32, 16, 32, 2), (8, 40, 32, 3),
+                                         (16, 128, 128, 8)])
 def test_one_iteration_from_state(L, nz, nx, ny, nc, with_prior):
     pl, ref, Xg, Lg, Sg = one_iteration_case(L, nz, nx, ny, nc, with_prior)
     tol = svt_tol(ref.sigma_in, ref.lambda_L, np.linalg.norm(ref.L))
