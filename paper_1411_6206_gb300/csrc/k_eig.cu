@@ -117,124 +117,129 @@ __device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T
   return r;
 }
 
-struct JacobiTables {
-  unsigned char pq[kMaxNc][kMaxNc];    // [step][2k], [step][2k+1]: indices p, q of pair k
-  unsigned char pos[kMaxNc][kMaxNc];   // [step][i]: (pair k << 1) | (i is the q of pair k)
-};
-
-// Round-robin (circle) schedule over np indices: step s pairs (np-1, s) and
-// ((s + k) mod (np-1), (s - k) mod (np-1)) for k = 1..np/2-1; over np-1 steps every pair
-// of indices meets once.
-__device__ void build_tables(JacobiTables* T, int np) {
-  const int m = np - 1, nh = np >> 1;
-  for (int t = threadIdx.x; t < m * nh; t += blockDim.x) {
-    const int s = t / nh, k = t - (t / nh) * nh;
-    int p, q;
-    if (k == 0) {
-      p = m;
-      q = s;
-    } else {
-      p = (s + k) % m;
-      q = (s - k + m) % m;
-    }
-    T->pq[s][2 * k] = (unsigned char)p;
-    T->pq[s][2 * k + 1] = (unsigned char)q;
-    T->pos[s][p] = (unsigned char)(k << 1);
-    T->pos[s][q] = (unsigned char)((k << 1) | 1);
-  }
+// Position of an index after one step of the circle schedule. The matrix is kept in
+// "position" order: step s rotates the pairs of positions (2k, 2k+1), then every element
+// moves to its next position, so that the next step again pairs (2k, 2k+1). Position 0 is
+// fixed; the others move along the ring 1 -> 2 -> 4 -> ... -> np-2 -> np-1 -> np-3 -> ... -> 3
+// -> 1 of length np-1 (odd). Two ring elements share a pair when they sit symmetrically
+// about position 1 of the ring, and each unordered pair has one such step per np-1 steps,
+// so np-1 steps (one sweep) meet every pair once and bring every index back to its own
+// position.
+__device__ __forceinline__ int next_pos(int p, int np) {
+  if (np == 2 || p == 0) return p;
+  if (p == 1) return 2;
+  if ((p & 1) == 0) return p == np - 2 ? np - 1 : p + 2;
+  return p - 2;
 }
 
-// Cyclic Jacobi on the Hermitian n x n matrix in A0 (zero-padded to even np); the
-// eigenvectors are accumulated into V. Returns the sweeps done; *result points at the
-// diagonalised matrix. `relw` (>= np/2 + 1 entries) and flags[0] are shared scratch.
+// Cyclic Jacobi on the Hermitian n x n matrix in A (zero-padded to even np); the
+// eigenvectors are accumulated into V (V <- V J per rotation). An and Vn are the second
+// buffers of the position permutation; on return A and V point at the results (index
+// order). Each thread keeps one task over all steps, since the tasks address positions:
+// either a block (k1 <= k2) of the 2 x 2 blocks of A, which it rotates on both sides with
+// the rotations of pairs k1 and k2 and writes (with its mirror) at the moved positions, or
+// two rows of V at pair k2. Every thread computes the rotations it needs itself from the
+// diagonal blocks, so one barrier per step suffices. Returns the sweeps done.
 template <typename R>
-__device__ int jacobi(typename Cx<R>::T* A0, typename Cx<R>::T* A1, typename Cx<R>::T* V, int n, R eps, R floor_,
-                      int max_sweeps, const JacobiTables* T, typename Cx<R>::T4* rot, R* relw, int* flags,
-                      typename Cx<R>::T** result) {
+__device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx<R>::T*& V,
+                      typename Cx<R>::T*& Vn, int n, R eps, R floor_, int max_sweeps, int* flags) {
   using C = typename Cx<R>::T;
   using C4 = typename Cx<R>::T4;
   const int np = n + (n & 1);
   const int nh = np >> 1;
-  const int nsq = np * np;
-  const int ntask = nsq + np * nh;
-  C* Ac = A0;
-  C* An = A1;
+  const int nblk = nh * (nh + 1) / 2;
+  const int vbase = ((nblk + 31) >> 5) << 5;   // V tasks start on a warp boundary
+  const int tid = threadIdx.x;
+  int role = 0, k1 = 0, k2 = 0, r0 = 0;
+  if (tid < nblk) {
+    role = 1;
+    int t = tid;
+    while (t >= nh - k1) {
+      t -= nh - k1;
+      ++k1;
+    }
+    k2 = k1 + t;
+  } else if (tid >= vbase && tid < vbase + nh * nh) {
+    role = 2;
+    const int t = tid - vbase;
+    k2 = t % nh;
+    r0 = 2 * (t / nh);
+  }
+  const int p1 = 2 * k1, q1 = p1 + 1, p2 = 2 * k2, q2 = p2 + 1;
+  const int np1 = next_pos(p1, np), nq1 = next_pos(q1, np);
+  const int np2 = next_pos(p2, np), nq2 = next_pos(q2, np);
   int sweep = 0;
   for (;;) {
     // converged when no off-diagonal entry exceeds its rotation threshold
-    if (threadIdx.x == 0) flags[sweep & 1] = 0;
+    if (tid == 0) flags[sweep & 1] = 0;
     __syncthreads();
-    for (int t = threadIdx.x; t < n * n; t += blockDim.x) {
+    for (int t = tid; t < n * n; t += blockDim.x) {
       const int p = t / n, q = t - (t / n) * n;
       R rm;
-      if (p < q && rot_params<R>(Ac, p, q, eps, floor_, &rm).w != R(0)) flags[sweep & 1] = 1;
+      if (p < q && rot_params<R>(A, p, q, eps, floor_, &rm).w != R(0)) flags[sweep & 1] = 1;
     }
     __syncthreads();
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
-      if (threadIdx.x < nh) {
-        R rm;
-        rot[threadIdx.x] =
-            rot_params<R>(Ac, T->pq[st][2 * threadIdx.x], T->pq[st][2 * threadIdx.x + 1], eps, floor_, &rm);
-      }
-      __syncthreads();
-      for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
-        if (t < nsq) {
-          // element (i, j) of J^H A J from the 2x2 block of rows {ip, iq}, columns {jp, jq}
-          const int i = t / np, j = t - (t / np) * np;
-          const int pi = T->pos[st][i], pj = T->pos[st][j];
-          const C4 r1 = rot[pi >> 1];
-          C v;
-          if ((pi >> 1) == (pj >> 1)) {
-            // diagonal block: a_pp - t|a_pq|, a_qq + t|a_pq|, exact zeros off the diagonal
-            if (r1.w == R(0)) {
-              v = Ac[i * kLd + j];
-            } else if (i == j) {
-              v = mkc(Ac[i * kLd + i].x + ((pi & 1) ? r1.w : -r1.w), R(0));
-            } else {
-              v = mkc(R(0), R(0));
-            }
-          } else {
-            const C4 r2 = rot[pj >> 1];
-            const int ip = T->pq[st][pi & ~1], iq = T->pq[st][pi | 1];
-            const int jp = T->pq[st][pj & ~1], jq = T->pq[st][pj | 1];
-            const C se1 = mkc(r1.y, r1.z), se2 = mkc(r2.y, r2.z);
-            const C bp0 = Ac[ip * kLd + jp], bp1 = Ac[ip * kLd + jq];
-            const C bq0 = Ac[iq * kLd + jp], bq1 = Ac[iq * kLd + jq];
-            C r0, r1v;   // row i of J1^H B at columns jp, jq
-            if (pi & 1) {
-              r0 = add_(mulc_(se1, bp0), scl_<C, R>(bq0, r1.x));
-              r1v = add_(mulc_(se1, bp1), scl_<C, R>(bq1, r1.x));
-            } else {
-              r0 = sub_(scl_<C, R>(bp0, r1.x), mul_(se1, bq0));
-              r1v = sub_(scl_<C, R>(bp1, r1.x), mul_(se1, bq1));
-            }
-            v = (pj & 1) ? add_(mul_(r0, se2), scl_<C, R>(r1v, r2.x))
-                         : sub_(scl_<C, R>(r0, r2.x), mul_(r1v, conj_(se2)));
+      R rm;
+      if (role == 1) {
+        const C b00 = A[p1 * kLd + p2], b01 = A[p1 * kLd + q2];
+        const C b10 = A[q1 * kLd + p2], b11 = A[q1 * kLd + q2];
+        const C4 ra = rot_params<R>(A, p1, q1, eps, floor_, &rm);
+        if (k1 == k2) {
+          C o00 = b00, o01 = b01, o10 = b10, o11 = b11;
+          if (ra.w != R(0)) {
+            // a_pp - t|a_pq|, a_qq + t|a_pq|, exact zeros off the diagonal
+            o00 = mkc(b00.x - ra.w, R(0));
+            o11 = mkc(b11.x + ra.w, R(0));
+            o01 = mkc(R(0), R(0));
+            o10 = o01;
           }
-          An[i * kLd + j] = v;
+          An[np1 * kLd + np1] = o00;
+          An[np1 * kLd + nq1] = o01;
+          An[nq1 * kLd + np1] = o10;
+          An[nq1 * kLd + nq1] = o11;
         } else {
-          // V J on the column pair of rotation k, row i (both entries read before written)
-          const int vt = t - nsq;
-          const int i = vt / nh, k = vt - (vt / nh) * nh;
-          const C4 r = rot[k];
-          if (r.w != R(0)) {
-            const int p = T->pq[st][2 * k], q = T->pq[st][2 * k + 1];
-            const C se = mkc(r.y, r.z);
-            const C vp = V[i * kLd + p], vq = V[i * kLd + q];
-            V[i * kLd + p] = sub_(scl_<C, R>(vp, r.x), mul_(vq, conj_(se)));
-            V[i * kLd + q] = add_(mul_(vp, se), scl_<C, R>(vq, r.x));
-          }
+          const C4 rb = rot_params<R>(A, p2, q2, eps, floor_, &rm);
+          const C s1 = mkc(ra.y, ra.z), s2 = mkc(rb.y, rb.z);
+          // rows of J1^H B, then (J1^H B) J2; J = [[c, se], [-conj(se), c]]
+          const C tp0 = sub_(scl_<C, R>(b00, ra.x), mul_(s1, b10));
+          const C tp1 = sub_(scl_<C, R>(b01, ra.x), mul_(s1, b11));
+          const C tq0 = add_(mulc_(s1, b00), scl_<C, R>(b10, ra.x));
+          const C tq1 = add_(mulc_(s1, b01), scl_<C, R>(b11, ra.x));
+          const C o00 = sub_(scl_<C, R>(tp0, rb.x), mul_(tp1, conj_(s2)));
+          const C o01 = add_(mul_(tp0, s2), scl_<C, R>(tp1, rb.x));
+          const C o10 = sub_(scl_<C, R>(tq0, rb.x), mul_(tq1, conj_(s2)));
+          const C o11 = add_(mul_(tq0, s2), scl_<C, R>(tq1, rb.x));
+          An[np1 * kLd + np2] = o00;
+          An[np1 * kLd + nq2] = o01;
+          An[nq1 * kLd + np2] = o10;
+          An[nq1 * kLd + nq2] = o11;
+          An[np2 * kLd + np1] = conj_(o00);
+          An[nq2 * kLd + np1] = conj_(o01);
+          An[np2 * kLd + nq1] = conj_(o10);
+          An[nq2 * kLd + nq1] = conj_(o11);
         }
+      } else if (role == 2) {
+        const C vp0 = V[r0 * kLd + p2], vq0 = V[r0 * kLd + q2];
+        const C vp1 = V[(r0 + 1) * kLd + p2], vq1 = V[(r0 + 1) * kLd + q2];
+        const C4 r = rot_params<R>(A, p2, q2, eps, floor_, &rm);
+        const C se = mkc(r.y, r.z);
+        Vn[r0 * kLd + np2] = sub_(scl_<C, R>(vp0, r.x), mul_(vq0, conj_(se)));
+        Vn[r0 * kLd + nq2] = add_(mul_(vp0, se), scl_<C, R>(vq0, r.x));
+        Vn[(r0 + 1) * kLd + np2] = sub_(scl_<C, R>(vp1, r.x), mul_(vq1, conj_(se)));
+        Vn[(r0 + 1) * kLd + nq2] = add_(mul_(vp1, se), scl_<C, R>(vq1, r.x));
       }
       __syncthreads();
-      C* tmp = Ac;
-      Ac = An;
-      An = tmp;
+      C* t = A;
+      A = An;
+      An = t;
+      t = V;
+      V = Vn;
+      Vn = t;
     }
     ++sweep;
   }
-  *result = Ac;
   return sweep;
 }
 
@@ -243,9 +248,7 @@ struct alignas(16) EigShared {
   float2 A1[kMaxNc * kLd];
   float2 V[kMaxNc * kLd];
   float2 G[kMaxNc * kLd];
-  JacobiTables tab;
-  float4 rot[kMaxNc / 2];
-  float relw[kMaxNc];
+  float2 V1[kMaxNc * kLd];   // second eigenvector buffer of the Jacobi permutation
   float sig[kMaxNc];       // sigma by rank
   float f[kMaxNc];         // sigma''_i / sigma_i
   double lam[kMaxNc];      // eigenvalues
@@ -268,9 +271,7 @@ struct alignas(16) EigShared64 {
   double2 A0[kMaxNc * kLd];
   double2 A1[kMaxNc * kLd];
   double2 V[kMaxNc * kLd];
-  double2 T[kMaxNc * kLd];
-  double4_16a rot[kMaxNc / 2];
-  double relw[kMaxNc];
+  double2 T[kMaxNc * kLd];   // G V, then the second eigenvector buffer of the Jacobi
 };
 
 // Sum four per-thread floats over the block in a fixed order; valid in every thread.
@@ -379,7 +380,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     gacc0 = gram_chunk(a.gram_part, tid, nn, ksub, a.nparts);
     if (tid + kEigThreads < ksub * nn) gacc1 = gram_chunk(a.gram_part, tid + kEigThreads, nn, ksub, a.nparts);
   }
-  build_tables(&sh.tab, np);
   if (tid < n) {
     int e = tid * n - tid * (tid - 1) / 2;
     for (int j = tid; j < n; ++j, ++e) {
@@ -484,9 +484,17 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   EIG_STAMP(3);
   float trace = 0.f;
   for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
-  float2* Af = nullptr;
-  const int sweeps = jacobi<float>(sh.A0, sh.A1, sh.V, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, &sh.tab, sh.rot,
-                                   sh.relw, sh.flags, &Af);
+  float2* Af = sh.A0;
+  float2* Afn = sh.A1;
+  float2* Vf = sh.V;
+  float2* Vfn = sh.V1;
+  const int sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
+  if (Vf != sh.V) {
+    for (int e = tid; e < np * np; e += kEigThreads) {
+      const int i = e / np, j = e - (e / np) * np;
+      sh.V[i * kLd + j] = Vf[i * kLd + j];
+    }
+  }
   __syncthreads();
 
   if (a.eig_fp64) {
@@ -523,13 +531,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     __syncthreads();
     double tr = 0.0;
     for (int i = 0; i < n; ++i) tr += fabs(d.A0[i * kLd + i].x);
-    double2* Ad = nullptr;
-    jacobi<double>(d.A0, d.A1, d.V, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 8, &sh.tab, d.rot, d.relw, sh.flags, &Ad);
+    double2* Ad = d.A0;
+    double2* Adn = d.A1;
+    double2* Vd = d.V;
+    double2* Vdn = d.T;
+    jacobi<double>(Ad, Adn, Vd, Vdn, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 8, sh.flags);
     __syncthreads();
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = Ad[i * kLd + i].x;
     for (int e = tid; e < np * np; e += kEigThreads) {
       const int i = e / np, j = e - (e / np) * np;
-      const double2 v = d.V[i * kLd + j];
+      const double2 v = Vd[i * kLd + j];
       sh.V[i * kLd + j] = make_float2((float)v.x, (float)v.y);
     }
   } else {
