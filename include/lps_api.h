@@ -71,6 +71,13 @@ extern "C" {
 #define LPS_LAYOUT_SLICES      0  /* Casorati columns = the nz slices of a volume (Sec. 2) */
 
 #define LPS_FP32               0  /* every stage in float32 (Gram and reprojection on FMA) */
+/* Precision modes: the two dense contractions (Casorati Gram and low-rank reprojection) run
+ * on the tensor cores with float32 accumulation; each float32 operand x is split into
+ * hi = round(x) and lo = round(x - hi) in the operand type and the products keep
+ * hi hi + hi lo + lo hi (one refinement step). FFTs, thresholds and the data-consistency
+ * step stay in float32; the eigendecomposition follows eig_precision. */
+#define LPS_TF32_REFINE        1  /* tf32 operands (11-bit significand)                      */
+#define LPS_BF16_REFINE        2  /* bf16 operands (8-bit significand)                       */
 
 #define LPS_EIG_FP32           0  /* Gram eigendecomposition by float32 Jacobi             */
 #define LPS_EIG_FP64           1  /* float32 Jacobi polished by float64 Jacobi sweeps      */
@@ -93,7 +100,7 @@ typedef struct lps_params {
   double lambda_p;         /* prior pull of step (2), in [0, 1]                             */
   double rank_tau;         /* drop directions with sigma_i <= rank_tau * sigma_1            */
   double tol;              /* stop when ||Z_k - Z_{k-1}|| / ||Z_{k-1}|| < tol (0 = never)   */
-  int precision;           /* LPS_FP32                                                      */
+  int precision;           /* LPS_FP32 | LPS_TF32_REFINE | LPS_BF16_REFINE                  */
   int eig_precision;       /* LPS_EIG_FP32 | LPS_EIG_FP64                                   */
   int support_rule;        /* LPS_SUPPORT_THRESHOLD | LPS_SUPPORT_NONZERO                   */
   int recursive;           /* 1: each lps_reconstruct_frame installs its support and sigma
@@ -187,14 +194,32 @@ int lps_adjoint(lps_plan* plan, const void* kdata, void* image);
  * (nullable). */
 int lps_data_consistency(lps_plan* plan, const void* Z, void* X, double* resid_norm2);
 
+/* Casorati Gram G = M^H M, M = X - S: the matrix whose eigendecomposition gives the
+ * singular values and right singular vectors for the singular-value thresholding of step (1)
+ * (Sec. 3; M is N_r x nz with N_r = nx ny, one column per slice). Computed with the plan's
+ * precision: float32 FMA for LPS_FP32, tensor cores with split operands otherwise.
+ * X, S: device [nz][nx][ny] complex64 (S may be NULL: S = 0). G: device nz x nz complex64,
+ * row-major, G[i][j] = sum_r conj(M[r][i]) M[r][j] (exactly Hermitian). Enqueued on the
+ * plan's stream; uses the plan's Gram scratch (do not overlap with other work of the plan). */
+int lps_casorati_gram(lps_plan* plan, const void* X, const void* S, void* G);
+/* Low-rank reprojection L = (X - S) W of steps (1)-(2) (Sec. 3): with W = V diag(sigma''/
+ * sigma) V^H from the eigendecomposition of the Gram, L = U diag(sigma'') V^H. Computed with
+ * the plan's precision. X, S as above (S may be NULL); W: device nz x nz complex64 row-major;
+ * L: device [nz][nx][ny] complex64, L[j][r] = sum_i M[i][r] W[i][j]. Enqueued on the plan's
+ * stream. */
+int lps_lowrank_reproject(lps_plan* plan, const void* X, const void* S, const void* W, void* L);
+
 /* Kernel timing of the per-frame graph. With profiling on, the graph records CUDA events
  * around every kernel it launches; lps_get_kernel_times synchronises the stream and returns,
  * for the last lps_reconstruct_frame, the launch count and summed device time of each class:
  * [0] data consistency (step 4), [1] low-rank/sparse update (steps 1-3 on the Casorati
- * matrix), [2] Gram eigendecomposition and singular-value steps, [3] step (0) kernels. */
+ * matrix), [2] Gram eigendecomposition and singular-value steps, [3] step (0) kernels,
+ * [4] Casorati Gram on the tensor cores and [5] reprojection on the tensor cores (precision
+ * modes only). */
+#define LPS_KERNEL_CLASSES 6
 typedef struct lps_kernel_times {
-  int launches[4];
-  double ms[4];
+  int launches[LPS_KERNEL_CLASSES];
+  double ms[LPS_KERNEL_CLASSES];
 } lps_kernel_times;
 int lps_set_profiling(lps_plan* plan, int on);
 int lps_get_kernel_times(lps_plan* plan, lps_kernel_times* out);

@@ -185,6 +185,21 @@ def uncasorati(m: np.ndarray, shape) -> np.ndarray:
     return m.T.reshape(shape)
 
 
+def casorati_gram(X: np.ndarray, S: Optional[np.ndarray] = None) -> np.ndarray:
+    """G = M^H M of the Casorati matrix M = casorati(X - S): the small Hermitian matrix
+    whose eigenpairs are the squared singular values and right singular vectors that the
+    singular-value thresholding of step (1) (Sec. 3) acts on. Plain definition, FP64."""
+    M = casorati(X if S is None else X - S).astype(np.complex128)
+    return M.conj().T @ M
+
+
+def reproject(X: np.ndarray, S: Optional[np.ndarray], W: np.ndarray) -> np.ndarray:
+    """L = uncasorati((X - S) W): with W = V diag(sigma''/sigma) V^H this is the low-rank
+    term U diag(sigma'') V^H of steps (1)-(2) (Sec. 3). Plain definition, FP64."""
+    M = casorati(X if S is None else X - S).astype(np.complex128)
+    return uncasorati(M @ np.asarray(W, np.complex128), X.shape)
+
+
 def svt(mat: np.ndarray, lam_L: float, lam_p: float = 0.0,
         sigma_prev: Optional[np.ndarray] = None, tau: float = 0.0):
     """Steps (1)-(2) of Algorithm 1 on a Casorati matrix.

@@ -216,7 +216,16 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   float2 Ln[8];
 #pragma unroll
   for (int v = 0; v < 8; ++v) Ln[v] = make_float2(0.f, 0.f);
-  if (act) {
+  if (act && a.Lnew) {
+    // precomputed on the tensor cores (precision modes)
+    const float4* ls = reinterpret_cast<const float4*>(a.Lnew + rowoff);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float4 q = ls[i];
+      Ln[2 * i] = make_float2(q.x, q.y);
+      Ln[2 * i + 1] = make_float2(q.z, q.w);
+    }
+  } else if (act) {
     const float2* mrow = Msh + tl * 64 * ldm + u * ldm;
     for (int i = 0; i < nc; ++i) {
       const float2 w = Wsh[i * nc + z];
@@ -273,7 +282,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_plane(const float2* X, const 
     for (int e = threadIdx.x; e < g.plane; e += kThreads) {
       const int z = e / ny, y = e - (e / ny) * ny;
       const long long gi = z * nxy + (long long)x * ny + y;
-      M[z * nyp + y] = csub(X[gi], S[gi]);
+      M[z * nyp + y] = S ? csub(X[gi], S[gi]) : X[gi];
     }
     __syncthreads();
     const bool first = x == (int)blockIdx.x * q;
@@ -292,6 +301,7 @@ __global__ void __launch_bounds__(kThreads) k_gram_plane(const float2* X, const 
         sr += o.x;
         si += o.y;
       }
+      if (i == j) si = 0.f;   // exactly real diagonal
       gp[i * nc + j] = make_float2(sr, si);
       if (i != j) gp[j * nc + i] = make_float2(sr, -si);
     }
@@ -336,6 +346,55 @@ cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
     case 2: return launch_lrs_j<2>(a, st);
     default: return launch_lrs_j<3>(a, st);
   }
+}
+
+// G = sum of the nparts partials, in partial order (one thread per entry).
+__global__ void k_gram_sum(const float2* __restrict__ part, int nparts, int nn, float2* __restrict__ G) {
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= nn) return;
+  float2 s = make_float2(0.f, 0.f);
+  for (int p = 0; p < nparts; ++p) s = cadd(s, part[(long long)p * nn + e]);
+  G[e] = s;
+}
+
+cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st) {
+  const int nn = nc * nc;
+  k_gram_sum<<<(nn + 255) / 256, 256, 0, st>>>(part, nparts, nn, G);
+  return cudaGetLastError();
+}
+
+// L[j][r] = sum_i (X - S)[i][r] W[i][j] in float32, one thread per pixel r (the stand-alone
+// form of the reprojection that k_lrs fuses with the sparse step).
+__global__ void k_reproj_f32(const float2* __restrict__ X, const float2* __restrict__ S,
+                             const float2* __restrict__ W, float2* __restrict__ L, Geom g) {
+  const long long nr = (long long)g.nx * g.ny;
+  const int nc = g.nc;
+  for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
+    float2 m[kMaxNc];
+#pragma unroll
+    for (int i = 0; i < kMaxNc; ++i)
+      m[i] = i < nc ? (S ? csub(X[i * nr + r], S[i * nr + r]) : X[i * nr + r]) : make_float2(0.f, 0.f);
+    for (int j = 0; j < nc; ++j) {
+      float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < kMaxNc; ++i) {
+        if (i < nc) {
+          const float2 w = W[i * nc + j];
+          acc.x = fmaf(m[i].x, w.x, fmaf(-m[i].y, w.y, acc.x));
+          acc.y = fmaf(m[i].x, w.y, fmaf(m[i].y, w.x, acc.y));
+        }
+      }
+      L[j * nr + r] = acc;
+    }
+  }
+}
+
+cudaError_t launch_reproj_f32(const float2* X, const float2* S, const float2* W, float2* L, const Geom& g,
+                              cudaStream_t st) {
+  const long long nr = (long long)g.nx * g.ny;
+  const int blocks = (int)std::min<long long>((nr + 127) / 128, 152LL * 8);
+  k_reproj_f32<<<blocks, 128, 0, st>>>(X, S, W, L, g);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, float2* gram_part, int nparts,

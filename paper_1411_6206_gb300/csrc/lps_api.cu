@@ -121,6 +121,7 @@ struct lps_plan {
   float2 *X = nullptr, *L = nullptr, *S = nullptr, *R = nullptr, *coils = nullptr;
   float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
   float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
+  float2* Lnew = nullptr;   // reprojection output of the precision modes
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   int* lines = nullptr;
   float *dc_part = nullptr, *lrs_part = nullptr;
@@ -183,10 +184,17 @@ int aalloc(lps_plan* P, T** ptr, size_t count) {
   return LPS_OK;
 }
 
+// Gram partials the eigen kernel sums: from the data-consistency epilogue in float32, from
+// the tensor-core Gram kernel in the precision modes.
+int gram_parts(const Geom& g, int precision) {
+  return precision == LPS_FP32 ? dc_gram_parts(g) : gram_tc_parts(g);
+}
+int gram_part_capacity(const Geom& g) { return std::max(g.nx, gram_tc_parts(g)); }
+
 size_t arena_size(const Geom& g, int max_iters) {
   auto r = [](size_t b) { return ((b + 255) / 256) * 256; };
   size_t s = 0;
-  s += r((size_t)g.nx * g.nc * g.nc * sizeof(float2));   // gram partials
+  s += r((size_t)gram_part_capacity(g) * g.nc * g.nc * sizeof(float2));   // gram partials
   s += 2 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V
   s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
   s += r((size_t)g.plane * sizeof(int));                  // line table
@@ -213,7 +221,8 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->lambda_p >= 0 && p->lambda_p <= 1, "lambda_p must be in [0, 1]");
   ARG(p->rank_tau >= 0 && p->rank_tau < 1, "rank_tau must be in [0, 1)");
   ARG(p->tol >= 0 && std::isfinite(p->tol), "tol must be finite, >= 0");
-  ARG(p->precision == LPS_FP32, "precision must be LPS_FP32");
+  ARG(p->precision == LPS_FP32 || p->precision == LPS_TF32_REFINE || p->precision == LPS_BF16_REFINE,
+      "precision must be LPS_FP32, LPS_TF32_REFINE or LPS_BF16_REFINE");
   ARG(p->eig_precision == LPS_EIG_FP32 || p->eig_precision == LPS_EIG_FP64, "bad eig_precision");
   ARG(p->support_rule == 0 || p->support_rule == 1, "bad support_rule");
   ARG(p->recursive == 0 || p->recursive == 1, "recursive must be 0 or 1");
@@ -252,7 +261,7 @@ int validate(const lps_params* p, Geom* gout) {
 int free_plan(lps_plan* P) {
   if (!P) return LPS_OK;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
-  void* bufs[] = {P->X, P->L, P->S, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena};
+  void* bufs[] = {P->X, P->L, P->S, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena, P->Lnew};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
@@ -368,19 +377,31 @@ int prof_end(lps_plan* P, cudaStream_t st) {
     if ((prc_ = prof_end(P, st))) return prc_;           \
   } while (0)
 
+GramTcArgs gram_tc_args(lps_plan* P, const float2* S, bool with_ctrl = true) {
+  GramTcArgs a{};
+  a.g = P->g;
+  a.X = P->X;
+  a.S = S;
+  a.gram_part = P->gram_part;
+  a.ctrl = with_ctrl ? P->ctrl : nullptr;
+  return a;
+}
+
 // Step (0): X_0 = E^H d, L_0 := X_0, S_0 = 0, Gram of X_0, max |T(X_0)|.
 int enqueue_init(lps_plan* P, cudaStream_t st) {
   CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), st));
   // Each frame starts its eigendecomposition from scratch unless the plan reconstructs a
   // sequence, where the previous frame's eigenvectors are the warm start.
   if (!P->p.recursive) CK(cudaMemsetAsync(&P->persist->v_valid, 0, sizeof(int), st));
+  const bool tc = P->p.precision != LPS_FP32;
   DcArgs a = dc_args(P);
   a.X = P->X;
   a.L_out = P->L;
   a.S_out = P->S;
-  a.gram_part = P->gram_part;
+  a.gram_part = tc ? nullptr : P->gram_part;
   a.ctrl = P->ctrl;
   PROF(3, LK(launch_dc(a, kDcAdjoint, st)));
+  if (tc) PROF(4, LK(launch_gram_tc(gram_tc_args(P, nullptr), P->p.precision, st)));
   LrsArgs l{};
   l.g = P->g;
   l.X = P->X;
@@ -399,7 +420,7 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
   EigArgs e{};
   e.g = P->g;
   e.gram_part = P->gram_part;
-  e.nparts = dc_gram_parts(P->g);
+  e.nparts = gram_parts(P->g, P->p.precision);
   e.dc_part = P->dc_part;
   e.lrs_part = P->lrs_part;
   e.lrs_parts = lrs_blocks(P->g);
@@ -423,7 +444,18 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
 
 // Iteration k: steps (1)-(2) (eig kernel), (3) (low-rank/sparse kernel), (4) (DC kernel).
 int enqueue_iter(lps_plan* P, int k, cudaStream_t st) {
+  const bool tc = P->p.precision != LPS_FP32;
   PROF(2, LK(launch_eig(eig_args(P, k, 0), st)));
+  if (tc) {
+    ReprojTcArgs r{};
+    r.g = P->g;
+    r.X = P->X;
+    r.S = P->S;
+    r.W = P->W;
+    r.Lnew = P->Lnew;
+    r.ctrl = P->ctrl;
+    PROF(5, LK(launch_reproj_tc(r, P->p.precision, st)));
+  }
   LrsArgs l{};
   l.g = P->g;
   l.X = P->X;
@@ -436,15 +468,17 @@ int enqueue_iter(lps_plan* P, int k, cudaStream_t st) {
   l.persist = P->persist;
   l.ctrl = P->ctrl;
   l.support_rule = P->p.support_rule;
+  l.Lnew = tc ? P->Lnew : nullptr;
   PROF(1, LK(launch_lrs(l, st)));
   DcArgs a = dc_args(P);
   a.L = P->L;
   a.S = P->S;
   a.X = P->X;
-  a.gram_part = P->gram_part;
+  a.gram_part = tc ? nullptr : P->gram_part;
   a.dc_part = P->dc_part;
   a.ctrl = P->ctrl;
   PROF(0, LK(launch_dc(a, kDcUpdate, st)));
+  if (tc) PROF(4, LK(launch_gram_tc(gram_tc_args(P, P->S), P->p.precision, st)));
   return LPS_OK;
 }
 
@@ -610,9 +644,10 @@ int lps_estimate_device_bytes(const lps_params* p, size_t* bytes) {
   const size_t m = (size_t)((g.plane / 2 + 1) & ~1);   // first frame at 50% of the lines
   size_t b = 0;
   b += 4 * N * 8;                              // X, L, S, recon
+  if (p->precision != LPS_FP32) b += N * 8;    // reprojection output
   b += (size_t)g.ncoil * N * 8;                // coils
   b += 3 * ((size_t)g.nx * g.ncoil * m + 4) * 8;   // hybrid data, k-space staging, scratch
-  b += (size_t)g.nx * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
+  b += (size_t)gram_part_capacity(g) * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
   b += (size_t)g.nx * 4 + (size_t)g.ntiles * 16 + 2 * N / 8;
   b += (size_t)(p->max_iters + 2) * sizeof(IterRec) + 4096;
   *bytes = b;
@@ -640,6 +675,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = dalloc(P, &P->R, N))) return fail(rc);
   if ((rc = dalloc(P, &P->istage, N))) return fail(rc);
   if ((rc = dalloc(P, &P->coils, N * g.ncoil))) return fail(rc);
+  if (p->precision != LPS_FP32 && (rc = dalloc(P, &P->Lnew, N))) return fail(rc);
   P->arena_bytes = arena_size(g, p->max_iters);
   if ((rc = dalloc(P, &P->arena, P->arena_bytes))) return fail(rc);
   if ((rc = aalloc(P, &P->ctrl, 1))) return fail(rc);
@@ -655,7 +691,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
   if ((rc = aalloc(P, &P->lines, (size_t)g.plane))) return fail(rc);
   if ((rc = aalloc(P, &P->hist, (size_t)p->max_iters + 2))) return fail(rc);
-  if ((rc = aalloc(P, &P->gram_part, (size_t)g.nx * g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->gram_part, (size_t)gram_part_capacity(g) * g.nc * g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
   if ((rc = aalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
   if (cudaMallocHost((void**)&P->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
@@ -947,10 +983,51 @@ int lps_set_state(lps_plan* P, const void* X, const void* S, const void* L_prev,
   c.sigma_max = 0.0;
   *P->h_ctrl = c;
   CK(cudaMemcpyAsync(P->ctrl, P->h_ctrl, sizeof(DevCtrl), cudaMemcpyHostToDevice, P->st));
-  LK(launch_gram_plane(P->X, P->S, P->g, P->gram_part, dc_gram_parts(P->g), P->st));
+  if (P->p.precision != LPS_FP32)
+    LK(launch_gram_tc(gram_tc_args(P, P->S, false), P->p.precision, P->st));
+  else
+    LK(launch_gram_plane(P->X, P->S, P->g, P->gram_part, dc_gram_parts(P->g), P->st));
   CK(cudaStreamSynchronize(P->st));
   P->state_ready = true;
   P->iters_done = iters_done;
+  return LPS_OK;
+}
+
+int lps_casorati_gram(lps_plan* P, const void* X, const void* S, void* G) {
+  ARG(P != nullptr && X != nullptr && G != nullptr, "NULL argument");
+  ARG(is_device_ptr(X) && is_device_ptr(G) && (S == nullptr || is_device_ptr(S)), "X, S, G must be device pointers");
+  int nparts;
+  if (P->p.precision != LPS_FP32) {
+    GramTcArgs a{};
+    a.g = P->g;
+    a.X = (const float2*)X;
+    a.S = (const float2*)S;
+    a.gram_part = P->gram_part;
+    LK(launch_gram_tc(a, P->p.precision, P->st));
+    nparts = gram_tc_parts(P->g);
+  } else {
+    nparts = P->g.nx;
+    LK(launch_gram_plane((const float2*)X, (const float2*)S, P->g, P->gram_part, nparts, P->st));
+  }
+  LK(launch_gram_sum(P->gram_part, nparts, P->g.nc, (float2*)G, P->st));
+  return LPS_OK;
+}
+
+int lps_lowrank_reproject(lps_plan* P, const void* X, const void* S, const void* W, void* L) {
+  ARG(P != nullptr && X != nullptr && W != nullptr && L != nullptr, "NULL argument");
+  ARG(is_device_ptr(X) && is_device_ptr(W) && is_device_ptr(L) && (S == nullptr || is_device_ptr(S)),
+      "X, S, W, L must be device pointers");
+  if (P->p.precision != LPS_FP32) {
+    ReprojTcArgs a{};
+    a.g = P->g;
+    a.X = (const float2*)X;
+    a.S = (const float2*)S;
+    a.W = (const float2*)W;
+    a.Lnew = (float2*)L;
+    LK(launch_reproj_tc(a, P->p.precision, P->st));
+  } else {
+    LK(launch_reproj_f32((const float2*)X, (const float2*)S, (const float2*)W, (float2*)L, P->g, P->st));
+  }
   return LPS_OK;
 }
 

@@ -115,6 +115,7 @@ struct LrsArgs {
   DevCtrl* ctrl;
   int support_rule;
   int haar_max_only;        // 1: only max |T(X)| into ctrl->haar_max_bits
+  const float2* Lnew;       // non-null: L_new precomputed (precision modes), not (X - S) W here
 };
 
 // ---- Gram reduction + eigendecomposition + SVT + prior pull (one CTA) --------------
@@ -138,6 +139,25 @@ struct EigArgs {
   int eig_fp64;
 };
 
+// ---- tensor-core contractions of the precision modes (tcgen05) ----------------------
+constexpr int kPrecTf32 = 1;   // = LPS_TF32_REFINE
+constexpr int kPrecBf16 = 2;   // = LPS_BF16_REFINE
+struct GramTcArgs {
+  Geom g;
+  const float2* X;
+  const float2* S;          // nullptr: S = 0
+  float2* gram_part;        // [gram_tc_parts][nc][nc]
+  DevCtrl* ctrl;
+};
+struct ReprojTcArgs {
+  Geom g;
+  const float2* X;
+  const float2* S;
+  const float2* W;          // [nc][nc]
+  float2* Lnew;             // (X - S) W
+  DevCtrl* ctrl;
+};
+
 // Host-side launchers (return cudaGetLastError()).
 cudaError_t launch_dc(const DcArgs& a, int mode, cudaStream_t st);
 cudaError_t launch_xfft(const XfftArgs& a, cudaStream_t st);
@@ -148,6 +168,12 @@ size_t xfft_smem_bytes(const Geom& g);
 int dc_ept(const Geom& g);
 int lrs_blocks(const Geom& g);
 int dc_gram_parts(const Geom& g);
+int gram_tc_parts(const Geom& g);
+cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st);
+cudaError_t launch_reproj_f32(const float2* X, const float2* S, const float2* W, float2* L, const Geom& g,
+                              cudaStream_t st);
+cudaError_t launch_gram_tc(const GramTcArgs& a, int precision, cudaStream_t st);
+cudaError_t launch_reproj_tc(const ReprojTcArgs& a, int precision, cudaStream_t st);
 
 // Launch with programmatic stream serialization: the kernel may start while its predecessor
 // in the stream finishes; it must call pdl_wait() before reading the predecessor's outputs.

@@ -28,6 +28,8 @@ ERR_STATE = -7
 ERR_UNSUPPORTED = -8
 
 EIG_FP32, EIG_FP64 = 0, 1
+FP32, TF32_REFINE, BF16_REFINE = 0, 1, 2
+KERNEL_CLASSES = 6
 SUPPORT_THRESHOLD, SUPPORT_NONZERO = 0, 1
 MAX_NC = 32
 NOALLOC_SCRATCH_BYTES = 16 << 20
@@ -61,9 +63,9 @@ class IterRecord(C.Structure):
 
 
 class KernelTimes(C.Structure):
-    _fields_ = [("launches", C.c_int * 4), ("ms", C.c_double * 4)]
+    _fields_ = [("launches", C.c_int * KERNEL_CLASSES), ("ms", C.c_double * KERNEL_CLASSES)]
 
-    CLASSES = ("data_consistency", "lowrank_sparse", "eig_svt", "init")
+    CLASSES = ("data_consistency", "lowrank_sparse", "eig_svt", "init", "gram_tc", "reproj_tc")
 
     def as_dict(self):
         return {n: {"launches": self.launches[i], "ms": self.ms[i]} for i, n in enumerate(self.CLASSES)}
@@ -101,6 +103,8 @@ _SIGS = {
     "lps_set_state": ([_VP, _VP, _VP, _VP, C.c_double, C.c_double, C.c_int], C.c_int),
     "lps_forward": ([_VP, _VP, _VP], C.c_int),
     "lps_adjoint": ([_VP, _VP, _VP], C.c_int),
+    "lps_casorati_gram": ([_VP, _VP, _VP, _VP], C.c_int),
+    "lps_lowrank_reproject": ([_VP, _VP, _VP, _VP, _VP], C.c_int),
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
@@ -278,6 +282,16 @@ def forward(plan: int, image, kdata):
 
 def adjoint(plan: int, kdata, image):
     _check(load().lps_adjoint(plan, ptr(kdata), ptr(image)), "adjoint")
+
+
+def casorati_gram(plan: int, X, S, G):
+    """G = (X - S)^H (X - S) over the Casorati columns (S may be None), plan precision."""
+    _check(load().lps_casorati_gram(plan, ptr(X), ptr(S), ptr(G)), "casorati_gram")
+
+
+def lowrank_reproject(plan: int, X, S, W, L):
+    """L = (X - S) W over the Casorati columns (S may be None), plan precision."""
+    _check(load().lps_lowrank_reproject(plan, ptr(X), ptr(S), ptr(W), ptr(L)), "lowrank_reproject")
 
 
 def data_consistency(plan: int, Z, X) -> float:

@@ -210,6 +210,48 @@ def test_svt_closed_form():
     assert np.abs(L0 - M).max() < 1e-12
 
 
+def test_casorati_gram_closed_form_and_svd():
+    rng = np.random.default_rng(7)
+    nz, nx, ny = 5, 4, 6
+    # slices with disjoint supports: orthogonal Casorati columns, diagonal Gram of squared norms
+    X = np.zeros((nz, nx, ny), complex)
+    for z in range(nz):
+        X[z].flat[z * 4:(z + 1) * 4] = crandn(4, rng=rng)
+    G = O.casorati_gram(X)
+    norms2 = np.array([np.sum(np.abs(X[z]) ** 2) for z in range(nz)])
+    assert np.abs(G - np.diag(norms2)).max() < 1e-12
+    # general case: eigenvalues = squared singular values of the Casorati (LAPACK SVD), and
+    # S enters as M = X - S
+    X = crandn(nz, nx, ny, rng=rng)
+    S = crandn(nz, nx, ny, rng=rng)
+    G = O.casorati_gram(X, S)
+    assert np.abs(G - G.conj().T).max() < 1e-12
+    M = np.stack([(X - S)[z].ravel() for z in range(nz)], axis=1)
+    sv = np.linalg.svd(M, compute_uv=False)
+    ev = np.sort(np.linalg.eigvalsh(G))[::-1]
+    assert np.allclose(ev, sv ** 2, rtol=1e-12, atol=1e-12 * sv[0] ** 2)
+
+
+def test_reproject_gram_route_equals_svt():
+    rng = np.random.default_rng(8)
+    N, n = 30, 5
+    U = rand_unitary_cols(N, n, rng)
+    V = rand_unitary_cols(n, n, rng)
+    s = np.array([4.0, 2.5, 1.5, 0.7, 0.2])
+    M = (U * s) @ V.conj().T
+    X = M.T.reshape(n, 5, 6)
+    lam = 0.6
+    f = np.maximum(s - lam, 0) / s
+    W = (V * f) @ V.conj().T
+    Lr = O.reproject(X, None, W)
+    ref = (U * np.maximum(s - lam, 0)) @ V.conj().T
+    assert np.abs(Lr - ref.T.reshape(n, 5, 6)).max() < 1e-12
+    # W = I gives X - S; W = 0 gives 0
+    S = crandn(n, 5, 6, rng=rng)
+    assert np.abs(O.reproject(X, S, np.eye(n)) - (X - S)).max() < 1e-12
+    assert np.abs(O.reproject(X, S, np.zeros((n, n)))).max() == 0
+
+
 def test_svt_rectangular_diagonal_with_phases():
     n = 4
     ph = np.exp(1j * np.array([0.3, -1.2, 2.0, 0.7]))
