@@ -209,6 +209,86 @@ int lps_casorati_gram(lps_plan* plan, const void* X, const void* S, void* G);
  * stream. */
 int lps_lowrank_reproject(lps_plan* plan, const void* X, const void* S, const void* W, void* L);
 
+/* recon = L + S of the last reconstructed frame (Algorithm 1's output, Sec. 3) into a device
+ * or host buffer [nz][nx][ny] complex64 (a host buffer makes the call synchronous). */
+int lps_get_recon(lps_plan* plan, void* out);
+
+/* ---- autotuner ---------------------------------------------------------------------
+ * Not in the paper (it fixes no launch shapes): times, on the plan's resident coils, mask and
+ * data, the candidate shapes of the two per-iteration kernels whose shape is a free choice,
+ * and installs the fastest in the plan (its frame graph is captured again):
+ *  - data consistency: the compile-time plane kernel where one exists, else/and the
+ *    runtime-sized kernel with each candidate ordering of the FFT radix passes along y and z;
+ *  - low-rank/sparse update: 8x8 in-plane tiles per CTA.
+ * Results are cached per geometry (nx, ny, nz, ncoil, fft_z, precision) for the process.
+ * Requires lps_set_coils, lps_set_mask and lps_set_data; synchronises the plan's stream; the
+ * plan's state (X, L, S, prior) is not modified. out may be NULL. */
+typedef struct lps_tune_result {
+  int dc_variant;          /* 0: compile-time plane kernel, 1: runtime-sized kernel         */
+  int radix_y[8];          /* FFT passes along y of the runtime-sized kernel (0-terminated) */
+  int radix_z[8];          /* FFT passes along z                                            */
+  int lrs_tiles;           /* 8x8 tiles per CTA of the low-rank/sparse kernel               */
+  int candidates;          /* configurations timed                                          */
+  int cached;              /* 1: taken from the cache, nothing timed                        */
+  double dc_us, lrs_us;    /* best measured time per launch (microseconds)                  */
+} lps_tune_result;
+int lps_autotune(lps_plan* plan, lps_tune_result* out);
+int lps_autotune_clear_cache(void);
+
+/* ---- batches of independent problems -------------------------------------------------
+ * Not in the paper: many independent problems (sizes, slices and coils may differ) whose
+ * frames are reconstructed together. Each member is an ordinary plan (set its coils, mask,
+ * data and prior through lps_batch_plan); lps_batch_reconstruct runs one frame of every
+ * active member with ONE graph launch on the batch stream: the members' per-frame graphs are
+ * parallel branches of one CUDA graph. Inactive members stay in the graph and return at once
+ * (their control block starts converged), so members may finish their sequences at
+ * different times without a rebuild. Results: lps_get_recon / lps_get_state per member. */
+typedef struct lps_batch lps_batch;
+int lps_batch_create(const lps_params* params /* [n] */, int n, void* cuda_stream, lps_batch** out);
+int lps_batch_destroy(lps_batch* batch);
+int lps_batch_size(lps_batch* batch);
+int lps_batch_plan(lps_batch* batch, int i, lps_plan** out);   /* owned by the batch */
+int lps_batch_set_active(lps_batch* batch, int i, int active);  /* default: active */
+int lps_batch_autotune(lps_batch* batch);                       /* lps_autotune per active member */
+int lps_batch_reconstruct(lps_batch* batch);
+
+/* ---- serving loop -------------------------------------------------------------------
+ * Not in the paper (it reconstructs one sequence): real-time recursive reconstruction of many
+ * concurrent sessions. A session is a recursive plan on its own CUDA stream whose coil maps,
+ * L, S, prior support and singular values stay on the device between frames. Sessions are
+ * admitted while the sum of their lps_estimate_device_bytes fits hbm_budget_bytes (else
+ * LPS_ERR_ADMISSION; retry after lps_server_close). Frames are submitted as they arrive; a
+ * frame goes to the device as soon as fewer than max_inflight frames are there (0 = no limit;
+ * 1 = one frame at a time, the plain frame-by-frame path), after the earlier frames of its
+ * session and concurrently with other sessions' frames. Latency = time at which the frame's
+ * L + S is in the session's output buffer minus the arrival time given at submission, both
+ * on the server clock (seconds since lps_server_create, lps_server_now). Single-threaded:
+ * calls on one server must not overlap. */
+typedef struct lps_server lps_server;
+typedef struct lps_server_config {
+  size_t hbm_budget_bytes;   /* admission budget over all open sessions                    */
+  int max_inflight;          /* frames on the device at once (0 = no limit)                */
+  int reserved[7];           /* must be zero                                               */
+} lps_server_config;
+int lps_server_create(const lps_server_config* cfg, lps_server** out);
+int lps_server_destroy(lps_server* server);
+double lps_server_now(lps_server* server);
+/* params->recursive must be 1; coils: device or host [ncoil][nz][nx][ny] complex64. */
+int lps_server_open(lps_server* server, const lps_params* params, const void* coils, int* session);
+int lps_server_close(lps_server* server, int session);   /* no frames in flight */
+int lps_server_plan(lps_server* server, int session, lps_plan** out);
+size_t lps_server_bytes_in_use(lps_server* server);
+/* mask: host ny*nz bytes (copied); kdata: device or pinned-host samples as for lps_set_data,
+ * caller-owned until the frame is done. */
+int lps_server_submit(lps_server* server, int session, const uint8_t* mask, const void* kdata,
+                      double arrival_s, long long* ticket);
+/* 1: done (latency and completion time in seconds, nullable), 0: not yet, < 0: error. */
+int lps_server_poll(lps_server* server, long long ticket, double* latency_s, double* completion_s);
+int lps_server_wait(lps_server* server, long long ticket, double* latency_s, double* completion_s);
+int lps_server_release(lps_server* server, long long ticket);   /* forget a finished frame */
+/* L + S of the session's last completed frame into a device or host buffer (synchronous). */
+int lps_server_result(lps_server* server, int session, void* out);
+
 /* Kernel timing of the per-frame graph. With profiling on, the graph records CUDA events
  * around every kernel it launches; lps_get_kernel_times synchronises the stream and returns,
  * for the last lps_reconstruct_frame, the launch count and summed device time of each class:

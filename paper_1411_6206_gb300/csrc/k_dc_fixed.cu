@@ -403,12 +403,14 @@ static cudaError_t launch_fixed_mode(const DcArgs& a, int mode, cudaStream_t st)
 }
 
 static bool has_fixed(const Geom& g) {
-  if (g.nx % kGramCluster != 0) return false;   // the grid is made of whole clusters (nx % 8 == 0 anyway)
+  if (g.dc_generic || g.nx % kGramCluster != 0) return false;   // the grid is made of whole clusters (nx % 8 == 0 anyway)
   return (g.ny == 128 && g.nz == 16) || (g.ny == 192 && g.nz == 32) || (g.ny == 32 && g.nz == 8);
 }
 
 // Number of Gram partials the data-consistency step leaves for the eigen kernel.
 int dc_gram_parts(const Geom& g) { return has_fixed(g) ? g.nx / kGramCluster : g.nx; }
+
+bool dc_has_fixed(const Geom& g) { return has_fixed(g); }
 
 // Returns cudaErrorNotSupported when no specialisation matches (the caller falls back to the
 // runtime-sized kernel).

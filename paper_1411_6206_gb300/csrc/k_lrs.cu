@@ -21,7 +21,7 @@ namespace lps {
 
 // Thread layout: 8 consecutive lanes own one (tile, slice z); lane u holds row u of the
 // slice's 8 x 8 tile as 8 complex registers v = 0..7. CTAs of 256 threads take
-// TPC = floor(32 / nc) tiles.
+// TPC = floor(32 / nc) tiles by default (Geom::lrs_tpc overrides it).
 __device__ __forceinline__ float2 shfl2(float2 v, int src) {
   return make_float2(__shfl_sync(0xffffffffu, v.x, src), __shfl_sync(0xffffffffu, v.y, src));
 }
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem[];
   const int nc = g.nc, ldm = nc + 1;
-  const int tpc = 32 / nc;                           // tiles per CTA
+  const int tpc = g.lrs_tpc > 0 ? g.lrs_tpc : 32 / nc;   // tiles per CTA
   float2* Msh = reinterpret_cast<float2*>(smem);      // [tpc][8 v][8 u * ldm]: M = X - S
   float2* Wsh = Msh + tpc * 64 * ldm;                 // [nc][nc]
   float* red = reinterpret_cast<float*>(Wsh + nc * nc);
@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
     }
   }
   if (!maxonly)
-    for (int i = tid; i < nc * nc; i += kThreads) Wsh[i] = a.W[i];
+    for (int i = tid; i < nc * nc; i += blockDim.x) Wsh[i] = a.W[i];
   if (conv) return;
 
   if (maxonly) {
@@ -321,7 +321,11 @@ cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long l
   return cudaGetLastError();
 }
 
-static int lrs_tpc(const Geom& g) { return 32 / g.nc; }
+int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : 32 / g.nc; }
+
+// Threads of one low-rank/sparse CTA: 8 per (tile, slice), rounded up to whole warps (the
+// Haar shuffles need full warps; lanes beyond the tiles are inactive).
+int lrs_threads(const Geom& g) { return (8 * g.nc * lrs_tpc(g) + 31) / 32 * 32; }
 
 static size_t lrs_smem(const Geom& g) {
   return (size_t)(lrs_tpc(g) * 64 * (g.nc + 1) + g.nc * g.nc) * sizeof(float2) + 32 * sizeof(float);
@@ -336,7 +340,7 @@ static cudaError_t launch_lrs_j(const LrsArgs& a, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k_lrs<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = launch_pdl(k_lrs<J>, dim3(lrs_blocks(a.g)), dim3(kThreads), smem, st, a);
+  cudaError_t e = launch_pdl(k_lrs<J>, dim3(lrs_blocks(a.g)), dim3(lrs_threads(a.g)), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

@@ -1,7 +1,6 @@
 // Host side of the C ABI declared in include/lps_api.h: plan lifetime, validation, device
 // buffers, the per-frame launch sequence of Algorithm 1 (Sec. 3) and its CUDA graph.
-#include "lps_api.h"
-#include "lps_internal.cuh"
+#include "plan_internal.h"
 
 #include <cmath>
 #include <cstddef>
@@ -18,7 +17,7 @@ cudaError_t launch_gram_plane(const float2* X, const float2* S, const Geom& g, f
 cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long long n, cudaStream_t st);
 }  // namespace lps
 
-namespace {
+namespace lps {
 
 thread_local char g_err[512] = "";
 
@@ -29,22 +28,9 @@ void set_err(const char* fmt, ...) {
   va_end(ap);
 }
 
-#define CK(call)                                                                        \
-  do {                                                                                  \
-    cudaError_t e_ = (call);                                                            \
-    if (e_ != cudaSuccess) {                                                            \
-      set_err("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
-      return (e_ == cudaErrorMemoryAllocation) ? LPS_ERR_OOM : LPS_ERR_CUDA;              \
-    }                                                                                   \
-  } while (0)
+}  // namespace lps
 
-#define ARG(cond, ...)          \
-  do {                          \
-    if (!(cond)) {              \
-      set_err(__VA_ARGS__);     \
-      return LPS_ERR_INVALID_ARG; \
-    }                           \
-  } while (0)
+namespace {
 
 bool make_fft_plan(int n, FftPlan& p) {
   p.n = n;
@@ -112,54 +98,6 @@ bool is_device_ptr(const void* p) {
 
 }  // namespace
 
-struct lps_plan {
-  lps_params p;
-  Geom g;
-  cudaStream_t st = nullptr;
-  cudaStream_t cap = nullptr;
-  // device state
-  float2 *X = nullptr, *L = nullptr, *S = nullptr, *R = nullptr, *coils = nullptr;
-  float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
-  float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
-  float2* Lnew = nullptr;   // reprojection output of the precision modes
-  float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
-  int* lines = nullptr;
-  float *dc_part = nullptr, *lrs_part = nullptr;
-  double *sigma_out = nullptr, *sigma_prev = nullptr;
-  uint32_t *sup_out = nullptr, *sup_prior = nullptr;
-  DevPersist* persist = nullptr;
-  DevCtrl* ctrl = nullptr;
-  IterRec* hist = nullptr;
-  // The small per-plan buffers (control block, statistics, Gram partials, W, V, sigma,
-  // bitmaps, line table, twiddles) live in one contiguous allocation so that a kernel
-  // starting on any SM touches few address-translation pages.
-  unsigned char* arena = nullptr;
-  size_t arena_bytes = 0, arena_used = 0;
-  // Host-owned persistent fields; the device copy is refreshed by stream-ordered uploads.
-  DevPersist hp{};
-  // Pinned upload sources, a ring of kSlots: an upload takes the next slot, waiting only for
-  // the upload made kSlots uploads earlier from it, so the host can queue several frames
-  // ahead of the device.
-  static constexpr int kSlots = 8;
-  DevCtrl* h_ctrl = nullptr;
-  DevPersist* h_persist_slots = nullptr;   // [kSlots]
-  int* h_lines_slots = nullptr;            // [kSlots][plane]
-  cudaEvent_t slot_done[kSlots] = {};
-  bool slot_pending[kSlots] = {};
-  int slot_next = 0;
-  // host state
-  int nlines = 0, m_cap = 0;
-  bool have_mask = false, have_coils = false, have_data = false, state_ready = false;
-  int iters_done = 0;
-  size_t dev_bytes = 0;
-  cudaGraphExec_t gexec = nullptr;
-  bool graph_valid = false;
-  // profiling: event pairs around every kernel of the frame graph, by kernel class
-  bool profiling = false;
-  std::vector<cudaEvent_t> ev;      // 2 per recorded launch
-  std::vector<int> ev_class;        // class of each pair
-  int ev_used = 0;
-};
 
 namespace {
 
@@ -261,6 +199,7 @@ int validate(const lps_params* p, Geom* gout) {
 int free_plan(lps_plan* P) {
   if (!P) return LPS_OK;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
+  if (P->graph) cudaGraphDestroy(P->graph);
   void* bufs[] = {P->X, P->L, P->S, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena, P->Lnew};
   for (void* b : bufs)
     if (b) cudaFree(b);
@@ -390,6 +329,8 @@ GramTcArgs gram_tc_args(lps_plan* P, const float2* S, bool with_ctrl = true) {
 // Step (0): X_0 = E^H d, L_0 := X_0, S_0 = 0, Gram of X_0, max |T(X_0)|.
 int enqueue_init(lps_plan* P, cudaStream_t st) {
   CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), st));
+  // an inactive batch member starts "converged": every kernel of the frame returns at once
+  CK(cudaMemcpyAsync(&P->ctrl->converged, &P->persist->skip, sizeof(int), cudaMemcpyDeviceToDevice, st));
   // Each frame starts its eigendecomposition from scratch unless the plan reconstructs a
   // sequence, where the previous frame's eigenvectors are the warm start.
   if (!P->p.recursive) CK(cudaMemsetAsync(&P->persist->v_valid, 0, sizeof(int), st));
@@ -520,9 +461,11 @@ int build_graph(lps_plan* P) {
   }
   CK(e);
   e = cudaGraphInstantiate(&P->gexec, graph, 0);
-  cudaGraphDestroy(graph);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->graph = graph;
   CK(e);
   P->graph_valid = true;
+  ++P->graph_gen;
   return LPS_OK;
 }
 
@@ -571,6 +514,17 @@ int copy_out(lps_plan* P, void* dst, const void* src, size_t bytes, bool* host_d
   return LPS_OK;
 }
 
+// Host bookkeeping once a frame graph has been enqueued: the state is the frame's result and,
+// in recursive mode, the graph has installed the frame's support and sigma as the prior.
+void frame_done(lps_plan* P) {
+  P->state_ready = true;
+  P->iters_done = P->p.max_iters;
+  if (P->p.recursive) {
+    P->hp.has_sup = 1;
+    P->hp.has_sigma = 1;
+  }
+}
+
 int need_ready(lps_plan* P) {
   if (!P) {
     set_err("plan is NULL");
@@ -588,6 +542,14 @@ int need_ready(lps_plan* P) {
 namespace lps {
 // Validated geometry of a parameter set (used by entry points that run without a plan).
 int make_geom(const lps_params* p, Geom* g) { return validate(p, g); }
+int plan_build_graph(lps_plan* P) { return build_graph(P); }
+int plan_need_ready(lps_plan* P) { return need_ready(P); }
+int plan_upload_persist(lps_plan* P, bool with_v) { return upload_persist(P, with_v); }
+int plan_frame_done(lps_plan* P) {
+  frame_done(P);
+  return LPS_OK;
+}
+DcArgs plan_dc_args(lps_plan* P) { return dc_args(P); }
 }  // namespace lps
 
 extern "C" {
@@ -860,12 +822,7 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
   if (rc) return rc;
   if ((rc = build_graph(P))) return rc;
   CK(cudaGraphLaunch(P->gexec, P->st));
-  P->state_ready = true;
-  P->iters_done = P->p.max_iters;
-  if (P->p.recursive) {
-    P->hp.has_sup = 1;
-    P->hp.has_sigma = 1;
-  }
+  frame_done(P);
   const size_t img = (size_t)P->g.N * sizeof(float2);
   bool host = false;
   if (out_recon) {

@@ -30,6 +30,7 @@ struct DevPersist {
   int nlines;               // sampled lines of the current mask
   int has_sup;              // prior support present (nonzero)
   int has_sigma;            // prior singular values present (nonzero)
+  int skip;                 // nonzero: the next frame is skipped (inactive member of a batch)
   int v_valid;              // eigenvectors from an earlier eigendecomposition are available
 };
 
@@ -66,6 +67,8 @@ struct Geom {
   float scale_yz;           // 1/sqrt(ny*nz) (fft_z) or 1/sqrt(ny)
   float scale_x;            // 1/sqrt(nx)
   FftPlan py, pz, px;
+  int dc_generic;           // 1: always the runtime-sized data-consistency kernel (autotuner)
+  int lrs_tpc;              // 8x8 tiles per CTA of the low-rank/sparse kernel (0: 32 / nc)
 };
 
 // ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
@@ -167,6 +170,9 @@ size_t dc_smem_bytes(const Geom& g);
 size_t xfft_smem_bytes(const Geom& g);
 int dc_ept(const Geom& g);
 int lrs_blocks(const Geom& g);
+int lrs_tpc(const Geom& g);
+int lrs_threads(const Geom& g);
+bool dc_has_fixed(const Geom& g);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);
 cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st);

@@ -71,6 +71,22 @@ class KernelTimes(C.Structure):
         return {n: {"launches": self.launches[i], "ms": self.ms[i]} for i, n in enumerate(self.CLASSES)}
 
 
+class TuneResult(C.Structure):
+    _fields_ = [("dc_variant", C.c_int), ("radix_y", C.c_int * 8), ("radix_z", C.c_int * 8),
+                ("lrs_tiles", C.c_int), ("candidates", C.c_int), ("cached", C.c_int),
+                ("dc_us", C.c_double), ("lrs_us", C.c_double)]
+
+    def as_dict(self):
+        return {"dc_variant": self.dc_variant, "radix_y": [r for r in self.radix_y if r],
+                "radix_z": [r for r in self.radix_z if r], "lrs_tiles": self.lrs_tiles,
+                "candidates": self.candidates, "cached": self.cached,
+                "dc_us": self.dc_us, "lrs_us": self.lrs_us}
+
+
+class ServerConfig(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("reserved", C.c_int * 7)]
+
+
 class LpsError(RuntimeError):
     def __init__(self, code: int, where: str, msg: str):
         super().__init__(f"{where}: {status_string(code)} ({code}): {msg}")
@@ -110,6 +126,28 @@ _SIGS = {
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
     "lps_adjoint_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_int, _VP, _VP],
                             C.c_int),
+    "lps_get_recon": ([_VP, _VP], C.c_int),
+    "lps_autotune": ([_VP, _VP], C.c_int),
+    "lps_autotune_clear_cache": ([], C.c_int),
+    "lps_batch_create": ([C.POINTER(Params), C.c_int, _VP, C.POINTER(_VP)], C.c_int),
+    "lps_batch_destroy": ([_VP], C.c_int),
+    "lps_batch_size": ([_VP], C.c_int),
+    "lps_batch_plan": ([_VP, C.c_int, C.POINTER(_VP)], C.c_int),
+    "lps_batch_set_active": ([_VP, C.c_int, C.c_int], C.c_int),
+    "lps_batch_autotune": ([_VP], C.c_int),
+    "lps_batch_reconstruct": ([_VP], C.c_int),
+    "lps_server_create": ([C.POINTER(ServerConfig), C.POINTER(_VP)], C.c_int),
+    "lps_server_destroy": ([_VP], C.c_int),
+    "lps_server_now": ([_VP], C.c_double),
+    "lps_server_open": ([_VP, C.POINTER(Params), _VP, C.POINTER(C.c_int)], C.c_int),
+    "lps_server_close": ([_VP, C.c_int], C.c_int),
+    "lps_server_plan": ([_VP, C.c_int, C.POINTER(_VP)], C.c_int),
+    "lps_server_bytes_in_use": ([_VP], C.c_size_t),
+    "lps_server_submit": ([_VP, C.c_int, _VP, _VP, C.c_double, C.POINTER(C.c_longlong)], C.c_int),
+    "lps_server_poll": ([_VP, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "lps_server_wait": ([_VP, C.c_longlong, C.POINTER(C.c_double), C.POINTER(C.c_double)], C.c_int),
+    "lps_server_release": ([_VP, C.c_longlong], C.c_int),
+    "lps_server_result": ([_VP, C.c_int, _VP], C.c_int),
     "lps_session_export": ([_VP, _VP, C.POINTER(C.c_size_t)], C.c_int),
     "lps_session_import": ([_VP, _VP, C.c_size_t], C.c_int),
 }
@@ -318,6 +356,20 @@ def adjoint_noalloc(nx: int, ny: int, nz: int, ncoil: int, mask, coils, kdata, n
                                       ptr(image), _stream(stream)), "adjoint_noalloc")
 
 
+def get_recon(plan: int, out):
+    _check(load().lps_get_recon(plan, ptr(out)), "get_recon")
+
+
+def autotune(plan: int) -> TuneResult:
+    r = TuneResult()
+    _check(load().lps_autotune(plan, C.byref(r)), "autotune")
+    return r
+
+
+def autotune_clear_cache():
+    _check(load().lps_autotune_clear_cache(), "autotune_clear_cache")
+
+
 def session_export(plan: int) -> bytes:
     n = C.c_size_t()
     _check(load().lps_session_export(plan, None, C.byref(n)), "session_export")
@@ -387,3 +439,134 @@ class Plan:
 
     def support_words(self):
         return support_words(self.params)
+
+    def autotune(self):
+        return autotune(self.handle)
+
+    def recon(self, out):
+        get_recon(self.handle, out)
+        return out
+
+
+class _MemberPlan(Plan):
+    """A plan owned by a batch: the same calls as Plan, never destroyed by Python."""
+
+    def __init__(self, handle, params):
+        self.params = params
+        self.handle = handle
+        self.nlines = 0
+
+    def close(self):
+        self.handle = None
+
+
+class Batch:
+    """Owning handle over lps_batch: independent problems reconstructed by one graph launch
+    per frame step."""
+
+    def __init__(self, params_list, stream=None):
+        n = len(params_list)
+        arr = (Params * n)(*params_list)
+        h = _VP()
+        _check(load().lps_batch_create(arr, n, _stream(stream), C.byref(h)), "batch_create")
+        self.handle = h.value
+        self.members = []
+        for i, p in enumerate(params_list):
+            ph = _VP()
+            _check(load().lps_batch_plan(self.handle, i, C.byref(ph)), "batch_plan")
+            self.members.append(_MemberPlan(ph.value, p))
+
+    def __len__(self):
+        return len(self.members)
+
+    def __getitem__(self, i):
+        return self.members[i]
+
+    def set_active(self, i, active: bool):
+        _check(load().lps_batch_set_active(self.handle, i, int(bool(active))), "batch_set_active")
+
+    def autotune(self):
+        _check(load().lps_batch_autotune(self.handle), "batch_autotune")
+
+    def reconstruct(self):
+        _check(load().lps_batch_reconstruct(self.handle), "batch_reconstruct")
+
+    def close(self):
+        if self.handle:
+            for m in self.members:
+                m.close()
+            load().lps_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Server:
+    """Owning handle over lps_server: admission by device-memory budget, per-session streams,
+    frames issued as slots free up (max_inflight = 0: no limit, 1: the plain path)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 0):
+        cfg = ServerConfig(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight))
+        h = _VP()
+        _check(load().lps_server_create(C.byref(cfg), C.byref(h)), "server_create")
+        self.handle = h.value
+        self._keep = {}
+
+    def now(self) -> float:
+        return load().lps_server_now(self.handle)
+
+    def bytes_in_use(self) -> int:
+        return load().lps_server_bytes_in_use(self.handle)
+
+    def open(self, params: Params, coils) -> int:
+        sid = C.c_int()
+        _check(load().lps_server_open(self.handle, C.byref(params), ptr(coils), C.byref(sid)), "server_open")
+        return sid.value
+
+    def close_session(self, sid: int):
+        _check(load().lps_server_close(self.handle, sid), "server_close")
+
+    def submit(self, sid: int, mask, kdata, arrival: float) -> int:
+        import numpy as np
+        m = np.ascontiguousarray(mask, dtype=np.uint8)
+        t = C.c_longlong()
+        _check(load().lps_server_submit(self.handle, sid, m.ctypes.data, ptr(kdata), float(arrival), C.byref(t)),
+               "server_submit")
+        self._keep[t.value] = (m, kdata)       # alive until the frame is released
+        return t.value
+
+    def poll(self, ticket: int):
+        lat, comp = C.c_double(), C.c_double()
+        rc = load().lps_server_poll(self.handle, ticket, C.byref(lat), C.byref(comp))
+        if rc < 0:
+            _check(rc, "server_poll")
+        return (lat.value, comp.value) if rc == 1 else None
+
+    def wait(self, ticket: int):
+        lat, comp = C.c_double(), C.c_double()
+        _check(load().lps_server_wait(self.handle, ticket, C.byref(lat), C.byref(comp)), "server_wait")
+        return lat.value, comp.value
+
+    def release(self, ticket: int):
+        _check(load().lps_server_release(self.handle, ticket), "server_release")
+        self._keep.pop(ticket, None)
+
+    def result(self, sid: int, out):
+        _check(load().lps_server_result(self.handle, sid, ptr(out)), "server_result")
+        return out
+
+    def close(self):
+        if self.handle:
+            load().lps_server_destroy(self.handle)
+            self.handle = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

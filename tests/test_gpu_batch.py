@@ -1,0 +1,136 @@
+"""Batches (one graph launch per frame step over independent problems of uneven size) and the
+autotuner: a member's frames are the same in the batch as alone, inactive members are left
+untouched, tuned launch shapes keep oracle parity."""
+import numpy as np
+import pytest
+
+from oracle import lps_oracle as O
+from tests.gpu_cases import c64, make_case, oracle_params, up
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+E2E_TOL = 1e-3
+# (nz, nx, ny, ncoil, frames): uneven sizes, slices, coils and sequence lengths
+MEMBERS = [(8, 32, 32, 2, 3), (16, 48, 64, 3, 2), (12, 40, 40, 4, 3), (5, 64, 48, 1, 1)]
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_1411_6206_gb300 import lps
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required for -m gpu tests")
+    lps.load()
+    return lps
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def cases():
+    out = []
+    for k, (nz, nx, ny, nc, T) in enumerate(MEMBERS):
+        frames = [make_case(nz, nx, ny, nc, seed=40 + 7 * k + t, frac=0.35) for t in range(T)]
+        for f in frames[1:]:
+            f["coils"] = frames[0]["coils"]          # one coil set per session
+        out.append(frames)
+    return out
+
+
+def feed(plan, f):
+    plan.set_mask(f["mask"])
+    plan.set_data(dev(f["d"]))
+
+
+def alone(L, frames, nz, nx, ny, nc, iters, **kw):
+    pl = L.Plan(nx, ny, nz, nc, max_iters=iters, recursive=1, **kw)
+    pl.set_coils(dev(frames[0]["coils"]))
+    res = []
+    for f in frames:
+        feed(pl, f)
+        out = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+        pl.reconstruct_frame(recon=out)
+        res.append(out.cpu().numpy())
+    pl.close()
+    return res
+
+
+def test_batch_equals_each_problem_alone(L):
+    iters = 12
+    cs = cases()
+    params = [L.params_init(nx=nx, ny=ny, nz=nz, ncoil=nc, max_iters=iters, recursive=1)
+              for (nz, nx, ny, nc, T) in MEMBERS]
+    B = L.Batch(params)
+    for m, frames in zip(B.members, cs):
+        m.set_coils(dev(frames[0]["coils"]))
+    T = max(x[4] for x in MEMBERS)
+    got = [[] for _ in MEMBERS]
+    for t in range(T):
+        for i, ((nz, nx, ny, nc, Ti), frames) in enumerate(zip(MEMBERS, cs)):
+            B.set_active(i, t < Ti)
+            if t < Ti:
+                feed(B[i], frames[t])
+        B.reconstruct()
+        for i, (nz, nx, ny, nc, Ti) in enumerate(MEMBERS):
+            if t < Ti:
+                out = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+                B[i].recon(out)
+                got[i].append(out.cpu().numpy())
+    for i, ((nz, nx, ny, nc, Ti), frames) in enumerate(zip(MEMBERS, cs)):
+        ref = alone(L, frames, nz, nx, ny, nc, iters)
+        for t in range(Ti):
+            assert np.array_equal(got[i][t], ref[t]), (i, t)   # bitwise: same kernels, fixed orders
+    B.close()
+
+
+def test_inactive_member_state_untouched(L):
+    iters = 8
+    (nz, nx, ny, nc, _), (nz2, nx2, ny2, nc2, _) = MEMBERS[0], MEMBERS[1]
+    params = [L.params_init(nx=nx, ny=ny, nz=nz, ncoil=nc, max_iters=iters, recursive=1),
+              L.params_init(nx=nx2, ny=ny2, nz=nz2, ncoil=nc2, max_iters=iters, recursive=1)]
+    B = L.Batch(params)
+    f0 = make_case(nz, nx, ny, nc, seed=90)
+    f1 = make_case(nz2, nx2, ny2, nc2, seed=91)
+    B[0].set_coils(dev(f0["coils"]))
+    B[1].set_coils(dev(f1["coils"]))
+    feed(B[0], f0)
+    feed(B[1], f1)
+    B.reconstruct()
+    X = torch.empty((nz2, nx2, ny2), dtype=torch.complex64, device="cuda")
+    Lb, Sb = torch.empty_like(X), torch.empty_like(X)
+    L.get_state(B[1].handle, X, Lb, Sb)
+    before = (Lb.cpu().numpy().copy(), Sb.cpu().numpy().copy())
+    B.set_active(1, False)
+    feed(B[0], make_case(nz, nx, ny, nc, seed=92))
+    B.reconstruct()
+    L.get_state(B[1].handle, X, Lb, Sb)
+    assert np.array_equal(Lb.cpu().numpy(), before[0]) and np.array_equal(Sb.cpu().numpy(), before[1])
+    B.close()
+
+
+@pytest.mark.parametrize("nz,nx,ny,nc", [(16, 128, 128, 8), (12, 48, 80, 3), (7, 32, 96, 2)])
+def test_autotuned_frame_matches_oracle(L, nz, nx, ny, nc):
+    L.autotune_clear_cache()
+    case = make_case(nz, nx, ny, nc, seed=13, frac=0.3)
+    pl = L.Plan(nx, ny, nz, nc, max_iters=20)
+    pl.set_coils(dev(case["coils"]))
+    pl.set_mask(case["mask"])
+    pl.set_data(dev(case["d"]))
+    r = pl.autotune()
+    assert r.candidates >= 2 and not r.cached
+    assert 1 <= r.lrs_tiles <= 32 // nz
+    if r.dc_variant:
+        assert np.prod([x for x in r.radix_y if x]) == ny and np.prod([x for x in r.radix_z if x]) == nz
+    recon = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    pl.reconstruct_frame(recon=recon)
+    ref = O.priori_ls(up(case["d"]), up(case["coils"]), case["mask"], oracle_params(pl.params))
+    assert O.nrmse(recon.cpu().numpy(), ref.recon) <= E2E_TOL
+    # a second plan of the same geometry takes the cached result
+    pl2 = L.Plan(nx, ny, nz, nc, max_iters=20)
+    pl2.set_coils(dev(case["coils"]))
+    pl2.set_mask(case["mask"])
+    pl2.set_data(dev(case["d"]))
+    assert pl2.autotune().cached == 1
+    pl.close()
+    pl2.close()
