@@ -46,6 +46,11 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=2, help="oracle frames in the CPU baseline")
     ap.add_argument("--profile", type=int, default=1, help="record kernel events in the frame graph")
+    ap.add_argument("--no-served", action="store_true", help="skip the serving study")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched study")
+    ap.add_argument("--serve-seconds", type=float, default=6.5, help="arrival window of the serving study")
+    ap.add_argument("--serve-sessions", type=int, default=16)
+    ap.add_argument("--batch-problems", type=int, default=64)
     return ap.parse_args()
 
 
@@ -461,6 +466,150 @@ def run_reference(args):
     }
 
 
+def gpu_problem(w, frames, lps, PG, P, dev, cycle=None):
+    """Device-generated inputs of `frames` frames of workload w: coil maps, host masks and
+    k-space made by the library's forward operator plus CN noise. With `cycle`, only that many
+    distinct frames are made (the heart beats with a period of 8 frames)."""
+    import torch
+    coils = PG.coil_maps(w.nx, w.ny, w.nz, w.ncoil, w.seed, dev)
+    masks = P.masks_for(w)
+    hf = PG.HeartFrames(w, dev)
+    fwd = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, max_iters=1)
+    fwd.set_coils(coils)
+    n = frames if cycle is None else min(cycle, frames)
+    out = []
+    for t in range(n):
+        m = masks[t % len(masks)]
+        nl = fwd.set_mask(m)
+        kd = torch.empty((w.ncoil, nl, w.nx), dtype=torch.complex64, device=dev)
+        lps.forward(fwd.handle, hf.frame(t), kd)
+        kd += PG.noise(w.ncoil, nl, w.nx, w.noise_sigma, w.seed * 1000 + t, dev)
+        out.append((np.ascontiguousarray(m), kd))
+    torch.cuda.synchronize()
+    fwd.close()
+    return coils, out
+
+
+def run_served(args):
+    """Serving study: sessions drawn from the uneven size mix, frames arriving as independent
+    Poisson processes of 20 frames/s per session, reconstructed recursively with every
+    session's state resident; served (per-session streams, no slot limit) against the plain
+    path (every frame in arrival order on one stream) on the same arrival trace."""
+    import torch
+    from paper_1411_6206_gb300 import lps, phantom as P, phantom_gpu as PG
+    dev = torch.device("cuda", 0)
+    ws_ = P.batched_mix(args.serve_sessions, seed0=500)
+    inputs = [gpu_problem(w, w.frames, lps, PG, P, dev, cycle=8) for w in ws_]
+    rate = 20.0
+    rng = np.random.default_rng(5)
+    trace = []
+    for k in range(len(ws_)):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > args.serve_seconds:
+                break
+            trace.append((t, k))
+    trace.sort()
+    res = {}
+    for mode in ("served", "plain"):
+        srv = lps.Server(150 * 10 ** 9, max_inflight=0, single_stream=(mode == "plain"))
+        sids = [srv.open(lps.params_init(nx=w.nx, ny=w.ny, nz=w.nz, ncoil=w.ncoil, max_iters=w.iters,
+                                         recursive=1), c) for w, (c, _) in zip(ws_, inputs)]
+        nframe = [0] * len(sids)
+        # warm-up: one frame per session (captures the frame graphs)
+        tk = [srv.submit(sid, *inputs[k][1][0], srv.now()) for k, sid in enumerate(sids)]
+        for t in tk:
+            srv.wait(t)
+            srv.release(t)
+        t0 = srv.now() + 0.05
+        tickets = []
+        for a, k in trace:
+            while srv.now() < t0 + a:
+                time.sleep(0.0001)
+            fr = inputs[k][1][(1 + nframe[k]) % len(inputs[k][1])]
+            nframe[k] += 1
+            tickets.append(srv.submit(sids[k], fr[0], fr[1], t0 + a))
+        lat, comp = [], []
+        for t in tickets:
+            l_, c_ = srv.wait(t)
+            lat.append(l_)
+            comp.append(c_)
+            srv.release(t)
+        span = max(comp) - (t0 + trace[0][0])
+        res[mode] = {"frames_per_s": round(len(tickets) / span, 2),
+                     "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+                     "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+                     "frames": len(tickets)}
+        srv.close()
+    out = dict(res["served"])
+    out["plain"] = res["plain"]
+    out.update({"sessions": len(ws_), "arrival_rate_per_session": rate, "offered_frames_per_s": rate * len(ws_),
+                "window_s": args.serve_seconds, "hbm_budget_bytes": 150 * 10 ** 9,
+                "sizes": [f"{w.nx}x{w.ny}x{w.nz}x{w.ncoil}c" for w in ws_],
+                "how": "Poisson arrivals (seeded), latency = result ready (device event) - arrival, "
+                       "server clock; plain = same trace, one stream in arrival order"})
+    return out
+
+
+def run_batched(args):
+    """Batched study: independent problems of uneven size (in-plane 64-160, 8-32 slices,
+    10-30 frames, 4-16 coils, R 4-12), one graph launch per frame step after the autotuner
+    picked each problem's launch shapes; against the same problems one frame graph at a time."""
+    import torch
+    from paper_1411_6206_gb300 import lps, phantom as P, phantom_gpu as PG
+    dev = torch.device("cuda", 0)
+    ws_ = P.batched_mix(args.batch_problems, seed0=400)
+    inputs = [gpu_problem(w, w.frames, lps, PG, P, dev) for w in ws_]
+    st = torch.cuda.Stream(device=dev)
+    B = lps.Batch([lps.params_init(nx=w.nx, ny=w.ny, nz=w.nz, ncoil=w.ncoil, max_iters=w.iters, recursive=1)
+                   for w in ws_], stream=st)
+    for m, (c, fr) in zip(B.members, inputs):
+        m.set_coils(c)
+        m.set_mask(fr[0][0])
+        m.set_data(fr[0][1])
+    t_tune = time.perf_counter()
+    B.autotune()
+    t_tune = time.perf_counter() - t_tune
+    T = max(w.frames for w in ws_)
+    total = sum(w.frames for w in ws_)
+
+    def sequence(batched):
+        for m in B.members:
+            m.clear_prior()
+        for t in range(T):
+            for i, w in enumerate(ws_):
+                act = t < w.frames
+                if batched:
+                    B.set_active(i, act)
+                if act:
+                    B[i].set_mask(inputs[i][1][t][0])
+                    B[i].set_data(inputs[i][1][t][1])
+                    if not batched:
+                        B[i].reconstruct_frame(stats=False)
+            if batched:
+                B.reconstruct()
+
+    out = {}
+    for mode in ("batched", "plain"):
+        sequence(mode == "batched")      # warm-up (graph captures)
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        sequence(mode == "batched")
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        out[mode] = {"frames_per_s": round(total / (ms / 1e3), 2), "ms": round(ms, 2)}
+    res = dict(out["batched"])
+    res["plain"] = out["plain"]
+    res.update({"problems": len(ws_), "frames": total, "frame_steps": T, "autotune_s": round(t_tune, 3),
+                "how": "one graph launch per frame step over all problems (inactive members return at "
+                       "once); plain = each problem's frame graph launched alone, in order"})
+    B.close()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -471,6 +620,10 @@ def main():
     out, (w, T) = run_ours(args)
     ws, rank, _ = dist()
     if rank == 0:
+        if ws == 1 and not args.no_served:
+            out["served"] = run_served(args)
+        if ws == 1 and not args.no_batched:
+            out["batched"] = run_batched(args)
         if ws == 1 and not args.no_cpu_baseline:
             cb, nr = cpu_baseline(args, w)
             out["cpu_baseline"] = cb

@@ -258,9 +258,9 @@ int lps_batch_reconstruct(lps_batch* batch);
  * L, S, prior support and singular values stay on the device between frames. Sessions are
  * admitted while the sum of their lps_estimate_device_bytes fits hbm_budget_bytes (else
  * LPS_ERR_ADMISSION; retry after lps_server_close). Frames are submitted as they arrive; a
- * frame goes to the device as soon as fewer than max_inflight frames are there (0 = no limit;
- * 1 = one frame at a time, the plain frame-by-frame path), after the earlier frames of its
- * session and concurrently with other sessions' frames. Latency = time at which the frame's
+ * frame goes to the device as soon as fewer than max_inflight frames are there (0 = no limit),
+ * after the earlier frames of its session and concurrently with other sessions' frames
+ * (single_stream = 1 runs every frame in arrival order on one stream instead). Latency = time at which the frame's
  * L + S is in the session's output buffer minus the arrival time given at submission, both
  * on the server clock (seconds since lps_server_create, lps_server_now). Single-threaded:
  * calls on one server must not overlap. */
@@ -268,7 +268,9 @@ typedef struct lps_server lps_server;
 typedef struct lps_server_config {
   size_t hbm_budget_bytes;   /* admission budget over all open sessions                    */
   int max_inflight;          /* frames on the device at once (0 = no limit)                */
-  int reserved[7];           /* must be zero                                               */
+  int single_stream;         /* 1: every session on one stream, frames run one after another
+                                in arrival order (the plain frame-by-frame path)           */
+  int reserved[6];           /* must be zero                                               */
 } lps_server_config;
 int lps_server_create(const lps_server_config* cfg, lps_server** out);
 int lps_server_destroy(lps_server* server);

@@ -821,6 +821,10 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
   int rc = need_ready(P);
   if (rc) return rc;
   if ((rc = build_graph(P))) return rc;
+  if (P->hp.skip) {   // left over from a batch in which this plan sat out a step
+    P->hp.skip = 0;
+    if ((rc = upload_persist(P))) return rc;
+  }
   CK(cudaGraphLaunch(P->gexec, P->st));
   frame_done(P);
   const size_t img = (size_t)P->g.N * sizeof(float2);

@@ -33,6 +33,7 @@ struct Session {
   float2* out = nullptr;      // L + S of the last completed frame
   size_t bytes = 0;           // admitted device bytes
   int queued = 0;             // frames submitted and not yet completed
+  bool shared = false;        // the server's single stream
 };
 
 struct Frame {
@@ -58,6 +59,7 @@ struct lps_server {
   std::map<long long, std::unique_ptr<Frame>> frames;
   int inflight = 0;
   cudaStream_t ref_st = nullptr;
+  cudaStream_t shared_st = nullptr;   // single_stream: the one stream of every session
   cudaEvent_t ref = nullptr;
   std::chrono::steady_clock::time_point t0;
 };
@@ -120,7 +122,7 @@ int close_session(lps_server* S, int id) {
   if (s.st) cudaStreamSynchronize(s.st);
   lps_plan_destroy(s.plan);
   if (s.out) cudaFree(s.out);
-  if (s.st) cudaStreamDestroy(s.st);
+  if (s.st && !s.shared) cudaStreamDestroy(s.st);
   S->used -= s.bytes;
   S->sessions.erase(it);
   return LPS_OK;
@@ -134,12 +136,20 @@ int lps_server_create(const lps_server_config* cfg, lps_server** out) {
   ARG(cfg != nullptr && out != nullptr, "NULL argument");
   ARG(cfg->hbm_budget_bytes > 0 && cfg->max_inflight >= 0, "bad server config");
   for (int r : cfg->reserved) ARG(r == 0, "reserved fields must be zero");
+  ARG(cfg->single_stream == 0 || cfg->single_stream == 1, "single_stream must be 0 or 1");
   lps_server* S = new lps_server();
   S->cfg = *cfg;
   if (cudaStreamCreateWithFlags(&S->ref_st, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreate(&S->ref) != cudaSuccess || cudaEventRecord(S->ref, S->ref_st) != cudaSuccess ||
       cudaEventSynchronize(S->ref) != cudaSuccess) {
     set_err("server clock setup failed");
+    delete S;
+    return LPS_ERR_CUDA;
+  }
+  if (cfg->single_stream && cudaStreamCreateWithFlags(&S->shared_st, cudaStreamNonBlocking) != cudaSuccess) {
+    set_err("stream creation failed");
+    cudaEventDestroy(S->ref);
+    cudaStreamDestroy(S->ref_st);
     delete S;
     return LPS_ERR_CUDA;
   }
@@ -157,6 +167,7 @@ int lps_server_destroy(lps_server* S) {
     if (kv.second->done) cudaEventDestroy(kv.second->done);
   if (S->ref) cudaEventDestroy(S->ref);
   if (S->ref_st) cudaStreamDestroy(S->ref_st);
+  if (S->shared_st) cudaStreamDestroy(S->shared_st);
   delete S;
   return LPS_OK;
 }
@@ -174,22 +185,30 @@ int lps_server_open(lps_server* S, const lps_params* p, const void* coils, int* 
     return LPS_ERR_ADMISSION;
   }
   Session s;
-  CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+  if (S->shared_st) {
+    s.st = S->shared_st;
+    s.shared = true;
+  } else {
+    CK(cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking));
+  }
+  auto drop_stream = [&] {
+    if (!s.shared) cudaStreamDestroy(s.st);
+  };
   if ((rc = lps_plan_create(p, s.st, &s.plan))) {
-    cudaStreamDestroy(s.st);
+    drop_stream();
     return rc;
   }
   const size_t img = (size_t)p->nx * p->ny * p->nz * sizeof(float2);
   if (cudaMalloc(&s.out, img) != cudaSuccess) {
     lps_plan_destroy(s.plan);
-    cudaStreamDestroy(s.st);
+    drop_stream();
     set_err("output buffer allocation failed");
     return LPS_ERR_OOM;
   }
   if ((rc = lps_set_coils(s.plan, coils))) {
     lps_plan_destroy(s.plan);
     cudaFree(s.out);
-    cudaStreamDestroy(s.st);
+    drop_stream();
     return rc;
   }
   s.bytes = need;

@@ -84,7 +84,8 @@ class TuneResult(C.Structure):
 
 
 class ServerConfig(C.Structure):
-    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("reserved", C.c_int * 7)]
+    _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("single_stream", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class LpsError(RuntimeError):
@@ -507,10 +508,12 @@ class Batch:
 
 class Server:
     """Owning handle over lps_server: admission by device-memory budget, per-session streams,
-    frames issued as slots free up (max_inflight = 0: no limit, 1: the plain path)."""
+    frames issued as slots free up (max_inflight = 0: no limit); single_stream runs every frame
+    in arrival order on one stream (the plain frame-by-frame path)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 0):
-        cfg = ServerConfig(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight))
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 0, single_stream: bool = False):
+        cfg = ServerConfig(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight),
+                           single_stream=int(bool(single_stream)))
         h = _VP()
         _check(load().lps_server_create(C.byref(cfg), C.byref(h)), "server_create")
         self.handle = h.value
