@@ -46,6 +46,12 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-frames", type=int, default=2, help="oracle frames in the CPU baseline")
     ap.add_argument("--profile", type=int, default=1, help="record kernel events in the frame graph")
+    ap.add_argument("--workload", default="cardiac", choices=["cardiac", "precision"],
+                    help="cardiac: 128x128x16 x 20 frames, 8 coils (default); precision: 192x192x32 x 25, 12 coils")
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
+                    help="Gram and reprojection arithmetic (tf32/bf16: tensor cores with one refinement step)")
+    ap.add_argument("--eig", default=None, choices=["fp32", "fp64"],
+                    help="eigendecomposition precision (default fp32 with --precision fp32, else fp64)")
     ap.add_argument("--no-served", action="store_true", help="skip the serving study")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched study")
     ap.add_argument("--serve-seconds", type=float, default=6.5, help="arrival window of the serving study")
@@ -149,9 +155,16 @@ def dist():
 # workload
 # ------------------------------------------------------------------------------------
 
-def workload(frames):
+def plan_kw(args):
+    from paper_1411_6206_gb300 import lps
+    prec = {"fp32": lps.FP32, "tf32": lps.TF32_REFINE, "bf16": lps.BF16_REFINE}[args.precision]
+    eig = args.eig or ("fp32" if args.precision == "fp32" else "fp64")
+    return {"precision": prec, "eig_precision": lps.EIG_FP64 if eig == "fp64" else lps.EIG_FP32}
+
+
+def workload(frames, name="cardiac"):
     from paper_1411_6206_gb300 import phantom as P
-    w = P.CARDIAC
+    w = P.CARDIAC if name == "cardiac" else P.PRECISION
     T = w.frames if frames is None else min(frames, w.frames)
     return w, T
 
@@ -181,7 +194,8 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as td
         td.init_process_group("nccl")
-    w, T = workload(args.frames)
+    w, T = workload(args.frames, args.workload)
+    kw = plan_kw(args)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(device=dev)
     lib = lps.load()
@@ -189,7 +203,7 @@ def run_ours(args):
     pr = P.problem(w, frames=T)
     coils = torch.from_numpy(np.ascontiguousarray(pr["coils"].astype(np.complex64))).to(dev)
     masks = [np.ascontiguousarray(m) for m in pr["masks"]]
-    plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1)
+    plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1, **kw)
     plan.set_coils(coils)
     # k-space of every frame by the library's forward operator, plus the generator's noise
     kdatas = []
@@ -261,7 +275,7 @@ def run_ours(args):
     # end to end through the C ABI with host buffers: pinned k-space in, pinned recon out
     pin_k = [kd.cpu().pin_memory() for kd in kdatas]
     pin_out = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64).pin_memory()
-    plan_h = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1)
+    plan_h = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=w.iters, recursive=1, **kw)
     plan_h.set_coils(coils)
 
     def seq_host():
@@ -297,7 +311,10 @@ def run_ours(args):
         hbm, sm_max, src = peaks()
         alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12   # TFLOP/s
         roof = None
-        launches_per_frame = 3 * w.iters + 5     # xfft, adjoint, haar-max, 3 per iteration, finalize, combine
+        # xfft, adjoint, haar-max, 3 per iteration, finalize, combine; the precision modes add the
+        # tensor-core Gram (init + every iteration) and reprojection (every iteration)
+        tc = args.precision != "fp32"
+        launches_per_frame = (5 if tc else 3) * w.iters + 5 + (1 if tc else 0)
         if ktimes:
             # dominant kernel class over the timed steps
             tot = {k: sum(d[k]["ms"] for d in ktimes) for k in ktimes[0]}
@@ -342,13 +359,15 @@ def run_ours(args):
         out = {
             "metric": METRIC, "value": round(value, 2), "unit": "frames/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp32": "f32", "tf32": "tf32x2-split/f32", "bf16": "bf16x2-split/f32"}[args.precision],
             "data": "synthetic: seeded beating-heart phantom, smooth SoS coil maps, VD ky-kz masks, "
                     "CN noise; k-space made by the library's forward operator",
-            "config": {"workload": f"cardiac-shaped recursive sequence {w.nx}x{w.ny}x{w.nz} x {T} frames, "
+            "config": {"workload": f"{args.workload}-shaped recursive sequence {w.nx}x{w.ny}x{w.nz} x {T} frames, "
                                    f"{w.ncoil} coils, R={w.accel:g} (frame 1 at 50%), {w.iters} iterations/frame",
                        "nx": w.nx, "ny": w.ny, "nz": w.nz, "ncoil": w.ncoil, "frames": T, "iters": w.iters,
                        "mode": "plain (frame by frame, CUDA-graph replay per frame)",
+                       "precision": args.precision, "eig": args.eig or ("fp32" if args.precision == "fp32" else "fp64"),
                        "l2": "256 MiB buffer written before every timed step (L2 flush)",
                        "parallelism": "independent sequence per GPU" if ws > 1 else "single GPU"},
             "frame_latency_ms": {"p50": round(float(np.percentile(fl, 50)), 4),
@@ -389,7 +408,7 @@ def cpu_baseline(args, w):
     coils64 = pr["coils"].astype(np.complex64)
     C128 = coils64.astype(np.complex128)
     datas = [(O.E(pr["x"][t], C128, pr["masks"][t]) + pr["noise"][t]).astype(np.complex64) for t in range(F)]
-    plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, max_iters=w.iters, recursive=1)
+    plan = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, max_iters=w.iters, recursive=1, **plan_kw(args))
     plan.set_coils(torch.from_numpy(coils64).cuda())
     gpu_out, priors = [], [None]
     out = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
@@ -427,7 +446,7 @@ def run_reference(args):
     ws, rank, _ = dist()
     if rank != 0:
         return None
-    w, T = workload(args.frames)
+    w, T = workload(args.frames, args.workload)
     nsteps = args.warmup + args.steps
     F = min(nsteps, w.frames)
     pr = P.problem(w, frames=F)
@@ -455,7 +474,7 @@ def run_reference(args):
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": round(sum(tt) / len(tt) * 1e3, 2), "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic (same generator and seeds as the GPU arm)",
-        "config": {"workload": f"cardiac-shaped recursive sequence {w.nx}x{w.ny}x{w.nz}, {w.ncoil} coils, "
+        "config": {"workload": f"{args.workload}-shaped recursive sequence {w.nx}x{w.ny}x{w.nz}, {w.ncoil} coils, "
                                f"R={w.accel:g}, {w.iters} iterations/frame; one frame per step",
                    "nx": w.nx, "ny": w.ny, "nz": w.nz, "ncoil": w.ncoil, "iters": w.iters},
         "frame_latency_ms": {"p50": round(float(np.percentile(fl, 50)), 2),

@@ -138,11 +138,14 @@ __device__ __forceinline__ int next_pos(int p, int np) {
 // order). Each thread keeps one task over all steps, since the tasks address positions:
 // either a block (k1 <= k2) of the 2 x 2 blocks of A, which it rotates on both sides with
 // the rotations of pairs k1 and k2 and writes (with its mirror) at the moved positions, or
-// two rows of V at pair k2. Every thread computes the rotations it needs itself from the
-// diagonal blocks, so one barrier per step suffices. Returns the sweeps done.
+// two rows of V at pair k2. In float32 every thread computes the rotations it needs itself
+// from the diagonal blocks, so one barrier per step suffices; in float64 (a small fraction of
+// the float32 issue rate, with square root and division in software) the nh rotations are
+// computed once per step into `rots` behind a second barrier. Returns the sweeps done.
 template <typename R>
 __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx<R>::T*& V,
-                      typename Cx<R>::T*& Vn, int n, R eps, R floor_, int max_sweeps, int* flags) {
+                      typename Cx<R>::T*& Vn, int n, R eps, R floor_, int max_sweeps, int* flags,
+                      typename Cx<R>::T4* rots) {
   using C = typename Cx<R>::T;
   using C4 = typename Cx<R>::T4;
   const int np = n + (n & 1);
@@ -182,10 +185,22 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
       R rm;
+      constexpr bool kShared = sizeof(R) == 8;
+      if constexpr (kShared) {
+        if (tid < nh) rots[tid] = rot_params<R>(A, 2 * tid, 2 * tid + 1, eps, floor_, &rm);
+        __syncthreads();
+      }
+      auto rot_of = [&](int k) -> C4 {
+        if constexpr (kShared) {
+          return rots[k];
+        } else {
+          return rot_params<R>(A, 2 * k, 2 * k + 1, eps, floor_, &rm);
+        }
+      };
       if (role == 1) {
         const C b00 = A[p1 * kLd + p2], b01 = A[p1 * kLd + q2];
         const C b10 = A[q1 * kLd + p2], b11 = A[q1 * kLd + q2];
-        const C4 ra = rot_params<R>(A, p1, q1, eps, floor_, &rm);
+        const C4 ra = rot_of(k1);
         if (k1 == k2) {
           C o00 = b00, o01 = b01, o10 = b10, o11 = b11;
           if (ra.w != R(0)) {
@@ -200,7 +215,7 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
           An[nq1 * kLd + np1] = o10;
           An[nq1 * kLd + nq1] = o11;
         } else {
-          const C4 rb = rot_params<R>(A, p2, q2, eps, floor_, &rm);
+          const C4 rb = rot_of(k2);
           const C s1 = mkc(ra.y, ra.z), s2 = mkc(rb.y, rb.z);
           // rows of J1^H B, then (J1^H B) J2; J = [[c, se], [-conj(se), c]]
           const C tp0 = sub_(scl_<C, R>(b00, ra.x), mul_(s1, b10));
@@ -223,7 +238,7 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
       } else if (role == 2) {
         const C vp0 = V[r0 * kLd + p2], vq0 = V[r0 * kLd + q2];
         const C vp1 = V[(r0 + 1) * kLd + p2], vq1 = V[(r0 + 1) * kLd + q2];
-        const C4 r = rot_params<R>(A, p2, q2, eps, floor_, &rm);
+        const C4 r = rot_of(k2);
         const C se = mkc(r.y, r.z);
         Vn[r0 * kLd + np2] = sub_(scl_<C, R>(vp0, r.x), mul_(vq0, conj_(se)));
         Vn[r0 * kLd + nq2] = add_(mul_(vp0, se), scl_<C, R>(vq0, r.x));
@@ -272,6 +287,7 @@ struct alignas(16) EigShared64 {
   double2 A1[kMaxNc * kLd];
   double2 V[kMaxNc * kLd];
   double2 T[kMaxNc * kLd];   // G V, then the second eigenvector buffer of the Jacobi
+  double4_16a rot[kMaxNc / 2];
 };
 
 // Sum four per-thread floats over the block in a fixed order; valid in every thread.
@@ -488,7 +504,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   float2* Afn = sh.A1;
   float2* Vf = sh.V;
   float2* Vfn = sh.V1;
-  const int sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
+  const int sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags, nullptr);
   if (Vf != sh.V) {
     for (int e = tid; e < np * np; e += kEigThreads) {
       const int i = e / np, j = e - (e / np) * np;
@@ -535,7 +551,9 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     double2* Adn = d.A1;
     double2* Vd = d.V;
     double2* Vdn = d.T;
-    jacobi<double>(Ad, Adn, Vd, Vdn, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 8, sh.flags);
+    // the float32 eigenvectors leave off-diagonals of about 1e-7 |A|: one float64 sweep takes
+    // them to about 1e-14, a second to rounding level
+    jacobi<double>(Ad, Adn, Vd, Vdn, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 3, sh.flags, d.rot);
     __syncthreads();
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = Ad[i * kLd + i].x;
     for (int e = tid; e < np * np; e += kEigThreads) {
