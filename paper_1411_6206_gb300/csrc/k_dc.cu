@@ -34,6 +34,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   float2* twz = twy + ny;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(twz + nz + ((ny + nz) & 1));
   float* red = reinterpret_cast<float*>(mbar + 2);
+  float2* wsh = reinterpret_cast<float2*>(red + 32);   // [nz][nz] W of the iteration form
 
   const int tid = threadIdx.x;
   const int x = blockIdx.x;
@@ -70,6 +71,18 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   float2 Zr[EPT];
   float2 acc[EPT];
   int pe[EPT];    // padded offset z*nyp + y
+  float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2
+  const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr);
+  if (iter_form && a.W) {
+    // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns.
+    for (int i = tid; i < nz * nz; i += kThreads) wsh[i] = a.W[i];
+    for (int e = tid; e < plane; e += kThreads) {
+      const int z = e / ny, y = e - (e / ny) * ny;
+      const long long gi = (long long)z * xy + (long long)x * ny + y;
+      bufA[z * nyp + y] = csub(a.X[gi], a.Sprev[gi]);
+    }
+    __syncthreads();
+  }
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
     const int e = tid + k * kThreads;
@@ -79,14 +92,33 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
     if (e < plane) {
       const int z = e / ny, y = e - (e / ny) * ny;
       pe[k] = z * nyp + y;
-      if (MODE != kDcAdjoint) {
-        const long long gi = (long long)z * xy + (long long)x * ny + y;
+      const long long gi = (long long)z * xy + (long long)x * ny + y;
+      if (iter_form) {
+        const float2 Sk = a.S[gi];
+        float2 Lk;
+        if (a.W) {
+          Lk = make_float2(0.f, 0.f);
+          for (int i = 0; i < nz; ++i) {
+            const float2 mv = bufA[i * nyp + y], w = wsh[i * nz + z];
+            Lk.x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Lk.x));
+            Lk.y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Lk.y));
+          }
+        } else {
+          Lk = a.Lpre[gi];
+        }
+        Zr[k] = cadd(Lk, Sk);
+        const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
+        a.Lbuf[gi] = Lk;
+        dz2 += cabs2(csub(Zr[k], Zo));
+        z2 += cabs2(Zo);
+      } else if (MODE != kDcAdjoint) {
         float2 v = a.L[gi];
         if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
         Zr[k] = v;
       }
     }
   }
+  if (iter_form && a.W) __syncthreads();   // bufA is the first FFT buffer of the coil loop
 
   const float sc = g.scale_yz;
   float resid = 0.f;
@@ -212,8 +244,10 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
     }
   }
   if (MODE == kDcUpdate && a.dc_part) {
-    const float tot = block_sum(resid, red);
-    if (tid == 0) a.dc_part[x] = tot;
+    const float r2 = block_sum(resid, red);
+    const float d2 = block_sum(dz2, red);
+    const float o2 = block_sum(z2, red);
+    if (tid == 0) reinterpret_cast<float4*>(a.dc_part)[x] = make_float4(r2, d2, o2, 0.f);
   }
 }
 
@@ -235,6 +269,7 @@ size_t dc_smem_bytes(const Geom& g) {
   b += (size_t)(g.ny + g.nz + ((g.ny + g.nz) & 1)) * sizeof(float2);
   b += 2 * sizeof(uint64_t);
   b += 32 * sizeof(float);
+  b += (size_t)g.nz * g.nz * sizeof(float2);   // W of the iteration form
   return b;
 }
 

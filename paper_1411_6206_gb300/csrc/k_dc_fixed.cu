@@ -99,7 +99,7 @@ struct DcFixedLayout {
   static constexpr int GROUP = 2 * PLANEP + 2 * PLANE;   // complex elements per coil group
   static constexpr size_t bytes() {
     return (size_t)(NCG * GROUP + NY + NZ + ((NY + NZ) & 1)) * sizeof(float2) + 2 * NCG * sizeof(uint64_t) +
-           64 * sizeof(float);
+           64 * sizeof(float) + (size_t)NZ * NZ * sizeof(float2);   // ..., reduction scratch, W
   }
 };
 
@@ -115,6 +115,7 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   float2* twz = twy + NY;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(twz + NZ + ((NY + NZ) & 1));
   float* red = reinterpret_cast<float*>(mbar + 2 * NCG);
+  float2* wsh = reinterpret_cast<float2*>(red + 64);   // [NZ][NZ] W of the iteration form
 
   const int tid = threadIdx.x;
   const int grp = tid / NT, gtid = tid - grp * NT;
@@ -160,17 +161,64 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   const int m = a.persist->nlines;
 
   float2 Zr[EPT], acc[EPT];
+  float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2 (group 0's elements)
+  const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr) && !conv;
+  if (iter_form) {
+    // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W, column by column of the
+    // Casorati matrix (the x-plane holds every slice of its pixels), or the precomputed L_k.
+    float2* Mp = base;   // group 0's first buffer: M_{k-1} as [z][NYP]
+    if (a.W) {
+      for (int i = tid; i < NZ * NZ; i += NTH) wsh[i] = a.W[i];
+      for (int e = tid; e < PLANE; e += NTH) {
+        const int z = e / NY, y = e % NY;
+        const long long gi = (long long)z * xy + (long long)x * NY + y;
+        Mp[z * NYP + y] = csub(a.X[gi], a.Sprev[gi]);
+      }
+    }
+    __syncthreads();
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int e = gtid + k * NT;
-    acc[k] = make_float2(0.f, 0.f);
-    Zr[k] = make_float2(0.f, 0.f);
-    if ((PLANE % NT == 0 || e < PLANE) && MODE != kDcAdjoint) {
-      const int z = e / NY, y = e % NY;
-      const long long gi = (long long)z * xy + (long long)x * NY + y;
-      float2 v = a.L[gi];
-      if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
-      Zr[k] = v;
+    for (int k = 0; k < EPT; ++k) {
+      const int e = gtid + k * NT;
+      acc[k] = make_float2(0.f, 0.f);
+      Zr[k] = make_float2(0.f, 0.f);
+      if (PLANE % NT == 0 || e < PLANE) {
+        const int z = e / NY, y = e % NY;
+        const long long gi = (long long)z * xy + (long long)x * NY + y;
+        const float2 Sk = a.S[gi];
+        float2 Lk;
+        if (a.W) {
+          Lk = make_float2(0.f, 0.f);
+#pragma unroll 8
+          for (int i = 0; i < NZ; ++i) {
+            const float2 mv = Mp[i * NYP + y], w = wsh[i * NZ + z];
+            Lk.x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Lk.x));
+            Lk.y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Lk.y));
+          }
+        } else {
+          Lk = a.Lpre[gi];
+        }
+        Zr[k] = cadd(Lk, Sk);
+        if (grp == 0) {
+          const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
+          a.Lbuf[gi] = Lk;
+          dz2 += cabs2(csub(Zr[k], Zo));
+          z2 += cabs2(Zo);
+        }
+      }
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = gtid + k * NT;
+      acc[k] = make_float2(0.f, 0.f);
+      Zr[k] = make_float2(0.f, 0.f);
+      if ((PLANE % NT == 0 || e < PLANE) && MODE != kDcAdjoint) {
+        const int z = e / NY, y = e % NY;
+        const long long gi = (long long)z * xy + (long long)x * NY + y;
+        float2 v = a.L[gi];
+        if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
+        Zr[k] = v;
+      }
     }
   }
   __syncthreads();
@@ -358,8 +406,10 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
     cl.sync();   // no CTA leaves while another still reads its shared memory
   }
   if (MODE == kDcUpdate && a.dc_part) {
-    const float tot = block_sum(resid, red);
-    if (tid == 0) a.dc_part[x] = tot;
+    const float r2 = block_sum(resid, red);
+    const float d2 = block_sum(dz2, red);
+    const float o2 = block_sum(z2, red);
+    if (tid == 0) reinterpret_cast<float4*>(a.dc_part)[x] = make_float4(r2, d2, o2, 0.f);
   }
 }
 

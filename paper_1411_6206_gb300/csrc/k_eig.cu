@@ -378,14 +378,16 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   const int sw = (kEigThreads >> 5) - 1;
   float4 st4 = make_float4(0.f, 0.f, 0.f, 0.f);
   if ((tid >> 5) == sw && a.iter > 1) {
+    // x: ||E Z - d||^2, z: ||Z_k - Z_{k-1}||^2, w: ||Z_{k-1}||^2 (data consistency);
+    // y: l1 off the prior support (sparse step)
     const int lane = tid & 31;
-    for (int i = lane; i < a.g.nx; i += 32) st4.x += a.dc_part[i];
-    for (int i = lane; i < a.lrs_parts; i += 32) {
-      const float4 q = reinterpret_cast<const float4*>(a.lrs_part)[i];
-      st4.y += q.x;
+    for (int i = lane; i < a.g.nx; i += 32) {
+      const float4 q = reinterpret_cast<const float4*>(a.dc_part)[i];
+      st4.x += q.x;
       st4.z += q.y;
       st4.w += q.z;
     }
+    for (int i = lane; i < a.lrs_parts; i += 32) st4.y += a.lrs_part[2 * i];
   }
   // Gram partials: all n x n entries, ksub interleaved chunks per entry
   const int ksub = nn <= kEigThreads / 2 ? 2 : 1;

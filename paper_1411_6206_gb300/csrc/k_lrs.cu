@@ -1,13 +1,12 @@
-// Steps (1)-(3) of Algorithm 1 (Sec. 3) that touch the Casorati matrix, one CTA per
-// 8 x 8 in-plane tile and all nc slice columns:
-//   step (1)+(2) reprojection   L_new = (X - S) W,  W = V diag(sigma''/sigma) V^H
-//                               (= U diag(sigma'') V^H of the thresholded SVD; W comes
-//                               from the eigendecomposition kernel)
-//   step (3) sparse update      c = T(X - L_prev) (orthonormal 2D Haar per slice, J levels),
-//                               c' = c on the prior support T^(t-1), soft(c, lambda_S) off it,
-//                               S_new = T^{-1}(c'); support bits [|c| > lambda_S].
-// Partial sums for the objective (l1 off the support) and for the relative-change stopping
-// rule are reduced per tile in a fixed order.
+// Step (3) of Algorithm 1 (Sec. 3), the support-aware sparse update, one CTA per group of
+// 8 x 8 in-plane tiles and all nc slices:
+//   c = T(X_{k-1} - L_{k-1}) (orthonormal 2D Haar per slice, J levels),
+//   c' = c on the prior support T^(t-1), soft(c, lambda_S) off it,
+//   S_k = T^{-1}(c'); support bits [|c| > lambda_S].
+// It needs neither the singular values nor W of the same iteration, so it runs concurrently
+// with the eigen kernel; the reprojection L_k = (X_{k-1} - S_{k-1}) W of steps (1)-(2) is
+// formed by the data-consistency kernel that consumes it. Partial sums for the objective
+// (l1 off the support) and the support count are reduced per CTA in a fixed order.
 //
 // Wavelet coefficient layout: within a tile the 8 x 8 coefficient array holds, for every
 // aligned 2^J x 2^J sub-block, that sub-block's own Mallat layout. Thread t owns tile row
@@ -109,11 +108,9 @@ template <int J>
 __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem[];
-  const int nc = g.nc, ldm = nc + 1;
+  float* red = reinterpret_cast<float*>(smem);
+  const int nc = g.nc;
   const int tpc = g.lrs_tpc > 0 ? g.lrs_tpc : 32 / nc;   // tiles per CTA
-  float2* Msh = reinterpret_cast<float2*>(smem);      // [tpc][8 v][8 u * ldm]: M = X - S
-  float2* Wsh = Msh + tpc * 64 * ldm;                 // [nc][nc]
-  float* red = reinterpret_cast<float*>(Wsh + nc * nc);
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int u = tid & 7, grp = tid >> 3;
@@ -129,15 +126,19 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const long long wbase = ((long long)(z * (g.nx >> 3) + tx) * nty + ty) * 2;
 
   pdl_trigger();
-  pdl_wait();   // X, L, S, W and the control block come from the preceding kernels
+  pdl_wait();   // X, L and the control block come from the preceding kernels
   // Every independent global load is issued up front: their latencies overlap.
   const int conv = a.ctrl->converged;
-  const float lamS = a.ctrl->lambda_S;
+  // lambda_S is fixed with lambda_L by the eigen kernel of the first iteration, which may run
+  // concurrently with this one; until then it is lambda_S_rel * max |T(X_0)| (the same value)
+  const int lset = a.ctrl->lambdas_set;
+  const float lamS_set = a.ctrl->lambda_S;
+  const float hmax = __uint_as_float(a.ctrl->haar_max_bits);
   const int has_sup = a.persist->has_sup;
   const unsigned prior_word = (act && !maxonly) ? a.sup_prior[wbase + (u >> 2)] : 0u;
-  float2 Xr[8], Lp[8], So[8];
+  float2 Xr[8], Lp[8];
 #pragma unroll
-  for (int v = 0; v < 8; ++v) Xr[v] = Lp[v] = So[v] = make_float2(0.f, 0.f);
+  for (int v = 0; v < 8; ++v) Xr[v] = Lp[v] = make_float2(0.f, 0.f);
   if (act) {
     const float4* xs = reinterpret_cast<const float4*>(a.X + rowoff);
 #pragma unroll
@@ -148,19 +149,14 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
     }
     if (!maxonly) {
       const float4* ls = reinterpret_cast<const float4*>(a.L + rowoff);
-      const float4* ss = reinterpret_cast<const float4*>(a.S + rowoff);
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
-        const float4 q = ls[i], w = ss[i];
+        const float4 q = ls[i];
         Lp[2 * i] = make_float2(q.x, q.y);
         Lp[2 * i + 1] = make_float2(q.z, q.w);
-        So[2 * i] = make_float2(w.x, w.y);
-        So[2 * i + 1] = make_float2(w.z, w.w);
       }
     }
   }
-  if (!maxonly)
-    for (int i = tid; i < nc * nc; i += blockDim.x) Wsh[i] = a.W[i];
   if (conv) return;
 
   if (maxonly) {
@@ -172,13 +168,7 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
     if (tid == 0) atomicMax(&a.ctrl->haar_max_bits, __float_as_uint(mx));
     return;
   }
-
-  // M = X - S rows to shared memory for the reprojection; W to shared memory.
-  if (act) {
-    float2* mrow = Msh + tl * 64 * ldm + u * ldm + z;
-#pragma unroll
-    for (int v = 0; v < 8; ++v) mrow[v * 8 * ldm] = csub(Xr[v], So[v]);
-  }
+  const float lamS = lset ? lamS_set : (float)(a.lambda_S_rel * (double)hmax);
 
   // Sparse step on D = X - L_prev: Haar analysis, support-aware shrink, synthesis.
   float2 D[8];
@@ -210,59 +200,17 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const float cnt = (act && (u & 3) == 0) ? (float)__popc(word) : 0.f;
   if (!act) l1 = 0.f;
   haar_inv<J>(D, u, lane);
-
-  __syncthreads();
-  // Reprojection L_new[(u, v)][z] = sum_i M[(u, v)][i] W[i][z].
-  float2 Ln[8];
-#pragma unroll
-  for (int v = 0; v < 8; ++v) Ln[v] = make_float2(0.f, 0.f);
-  if (act && a.Lnew) {
-    // precomputed on the tensor cores (precision modes)
-    const float4* ls = reinterpret_cast<const float4*>(a.Lnew + rowoff);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const float4 q = ls[i];
-      Ln[2 * i] = make_float2(q.x, q.y);
-      Ln[2 * i + 1] = make_float2(q.z, q.w);
-    }
-  } else if (act) {
-    const float2* mrow = Msh + tl * 64 * ldm + u * ldm;
-    for (int i = 0; i < nc; ++i) {
-      const float2 w = Wsh[i * nc + z];
-#pragma unroll
-      for (int v = 0; v < 8; ++v) {
-        const float2 mv = mrow[v * 8 * ldm + i];
-        Ln[v].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Ln[v].x));
-        Ln[v].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Ln[v].y));
-      }
-    }
-  }
-  float dz2 = 0.f, z2 = 0.f;
   if (act) {
-    float4* ld = reinterpret_cast<float4*>(a.L + rowoff);
     float4* sd = reinterpret_cast<float4*>(a.S + rowoff);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      ld[i] = make_float4(Ln[2 * i].x, Ln[2 * i].y, Ln[2 * i + 1].x, Ln[2 * i + 1].y);
-      sd[i] = make_float4(D[2 * i].x, D[2 * i].y, D[2 * i + 1].x, D[2 * i + 1].y);
-    }
-#pragma unroll
-    for (int v = 0; v < 8; ++v) {
-      const float2 Zo = cadd(Lp[v], So[v]);
-      dz2 += cabs2(csub(cadd(Ln[v], D[v]), Zo));
-      z2 += cabs2(Zo);
-    }
+    for (int i = 0; i < 4; ++i) sd[i] = make_float4(D[2 * i].x, D[2 * i].y, D[2 * i + 1].x, D[2 * i + 1].y);
   }
-  float* part = a.lrs_part + (long long)blockIdx.x * 4;
+  float* part = a.lrs_part + (long long)blockIdx.x * 2;
   float r;
   r = block_sum(l1, red);
   if (tid == 0) part[0] = r;
-  r = block_sum(dz2, red);
-  if (tid == 0) part[1] = r;
-  r = block_sum(z2, red);
-  if (tid == 0) part[2] = r;
   r = block_sum(cnt, red);
-  if (tid == 0) part[3] = r;
+  if (tid == 0) part[1] = r;
 }
 
 // Partials of the Casorati Gram (X - S)^H (X - S) straight from global memory; used when
@@ -327,9 +275,7 @@ int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : 32 / g.nc; }
 // Haar shuffles need full warps; lanes beyond the tiles are inactive).
 int lrs_threads(const Geom& g) { return (8 * g.nc * lrs_tpc(g) + 31) / 32 * 32; }
 
-static size_t lrs_smem(const Geom& g) {
-  return (size_t)(lrs_tpc(g) * 64 * (g.nc + 1) + g.nc * g.nc) * sizeof(float2) + 32 * sizeof(float);
-}
+static size_t lrs_smem(const Geom&) { return 32 * sizeof(float); }
 
 int lrs_blocks(const Geom& g) { return (g.ntiles + lrs_tpc(g) - 1) / lrs_tpc(g); }
 

@@ -136,7 +136,7 @@ size_t arena_size(const Geom& g, int max_iters) {
   s += 2 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V
   s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
   s += r((size_t)g.plane * sizeof(int));                  // line table
-  s += r((size_t)g.nx * sizeof(float)) + r((size_t)g.ntiles * 4 * sizeof(float));
+  s += r((size_t)g.nx * 4 * sizeof(float)) + r((size_t)g.ntiles * 4 * sizeof(float));   // statistic partials
   s += 2 * r((size_t)g.nc * sizeof(double));
   s += 2 * r((size_t)(g.N / 32) * sizeof(uint32_t));
   s += r(sizeof(DevPersist)) + r(sizeof(DevCtrl)) + r((size_t)(max_iters + 2) * sizeof(IterRec));
@@ -200,7 +200,8 @@ int free_plan(lps_plan* P) {
   if (!P) return LPS_OK;
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->graph) cudaGraphDestroy(P->graph);
-  void* bufs[] = {P->X, P->L, P->S, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena, P->Lnew};
+  void* bufs[] = {P->X, P->L, P->S, P->S2, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena,
+                  P->Lnew};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
@@ -209,6 +210,10 @@ int free_plan(lps_plan* P) {
   for (int k = 0; k < lps_plan::kSlots; ++k)
     if (P->slot_done[k]) cudaEventDestroy(P->slot_done[k]);
   if (P->cap) cudaStreamDestroy(P->cap);
+  if (P->side) cudaStreamDestroy(P->side);
+  if (P->cap_side) cudaStreamDestroy(P->cap_side);
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
   delete P;
   return LPS_OK;
@@ -290,7 +295,7 @@ DcArgs dc_args(lps_plan* P) {
 
 // Event pair around one launch when profiling (only while building the frame graph).
 int prof_begin(lps_plan* P, int cls, cudaStream_t st) {
-  if (!P->profiling || st != P->cap) return LPS_OK;
+  if (!P->profiling || (st != P->cap && st != P->cap_side)) return LPS_OK;
   const size_t need = 2 * (size_t)(P->ev_used + 1);
   while (P->ev.size() < need) {
     cudaEvent_t e;
@@ -303,7 +308,7 @@ int prof_begin(lps_plan* P, int cls, cudaStream_t st) {
   return LPS_OK;
 }
 int prof_end(lps_plan* P, cudaStream_t st) {
-  if (!P->profiling || st != P->cap) return LPS_OK;
+  if (!P->profiling || (st != P->cap && st != P->cap_side)) return LPS_OK;
   CK(cudaEventRecordWithFlags(P->ev[2 * P->ev_used + 1], st, cudaEventRecordExternal));
   ++P->ev_used;
   return LPS_OK;
@@ -347,8 +352,7 @@ int enqueue_init(lps_plan* P, cudaStream_t st) {
   l.g = P->g;
   l.X = P->X;
   l.L = P->L;
-  l.S = P->S;
-  l.W = P->W;
+  l.S = P->S2;
   l.lrs_part = P->lrs_part;
   l.persist = P->persist;
   l.ctrl = P->ctrl;
@@ -383,43 +387,69 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
   return e;
 }
 
-// Iteration k: steps (1)-(2) (eig kernel), (3) (low-rank/sparse kernel), (4) (DC kernel).
-int enqueue_iter(lps_plan* P, int k, cudaStream_t st) {
+// Iteration k of Algorithm 1. The sparse step (3) needs only X_{k-1} and L_{k-1}, so it runs
+// on a second stream beside the eigendecomposition of steps (1)-(2); the data-consistency
+// kernel of step (4) joins both, forms L_k = (X_{k-1} - S_{k-1}) W in its prologue (or takes
+// the tensor-core reprojection) and writes X_k, L_k and the next Gram:
+//   main:  eig_k [-> reproj_tc_k] ----------+-> DC_k [-> gram_tc_k]
+//   side:  (after DC_{k-1}) sparse_k -------+
+// S alternates between two buffers: the i-th iteration of a run reads S_{k-1} from one and
+// writes S_k to the other.
+int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) {
   const bool tc = P->p.precision != LPS_FP32;
-  PROF(2, LK(launch_eig(eig_args(P, k, 0), st)));
-  if (tc) {
-    ReprojTcArgs r{};
-    r.g = P->g;
-    r.X = P->X;
-    r.S = P->S;
-    r.W = P->W;
-    r.Lnew = P->Lnew;
-    r.ctrl = P->ctrl;
-    PROF(5, LK(launch_reproj_tc(r, P->p.precision, st)));
-  }
+  float2* Sprev = (i & 1) ? P->S2 : P->S;
+  float2* Snew = (i & 1) ? P->S : P->S2;
+  CK(cudaEventRecord(P->ev_fork, st));
+  CK(cudaStreamWaitEvent(side, P->ev_fork, 0));
   LrsArgs l{};
   l.g = P->g;
   l.X = P->X;
   l.L = P->L;
-  l.S = P->S;
-  l.W = P->W;
+  l.S = Snew;
   l.sup_prior = P->sup_prior;
   l.sup_out = P->sup_out;
   l.lrs_part = P->lrs_part;
   l.persist = P->persist;
   l.ctrl = P->ctrl;
+  l.lambda_S_rel = P->p.lambda_S_rel;
   l.support_rule = P->p.support_rule;
-  l.Lnew = tc ? P->Lnew : nullptr;
-  PROF(1, LK(launch_lrs(l, st)));
+  {
+    int prc;
+    if ((prc = prof_begin(P, 1, side))) return prc;
+    LK(launch_lrs(l, side));
+    if ((prc = prof_end(P, side))) return prc;
+  }
+  CK(cudaEventRecord(P->ev_join, side));
+  PROF(2, LK(launch_eig(eig_args(P, k, 0), st)));
+  if (tc) {
+    ReprojTcArgs r{};
+    r.g = P->g;
+    r.X = P->X;
+    r.S = Sprev;
+    r.W = P->W;
+    r.Lnew = P->Lnew;
+    r.ctrl = P->ctrl;
+    PROF(5, LK(launch_reproj_tc(r, P->p.precision, st)));
+  }
+  CK(cudaStreamWaitEvent(st, P->ev_join, 0));
   DcArgs a = dc_args(P);
-  a.L = P->L;
-  a.S = P->S;
+  a.S = Snew;
+  a.Sprev = Sprev;
+  a.W = tc ? nullptr : P->W;
+  a.Lpre = tc ? P->Lnew : nullptr;
+  a.Lbuf = P->L;
   a.X = P->X;
   a.gram_part = tc ? nullptr : P->gram_part;
   a.dc_part = P->dc_part;
   a.ctrl = P->ctrl;
   PROF(0, LK(launch_dc(a, kDcUpdate, st)));
-  if (tc) PROF(4, LK(launch_gram_tc(gram_tc_args(P, P->S), P->p.precision, st)));
+  if (tc) PROF(4, LK(launch_gram_tc(gram_tc_args(P, Snew), P->p.precision, st)));
+  return LPS_OK;
+}
+
+// After a run of n iterations the current S is in S2 when n is odd: move it to S.
+int enqueue_settle_s(lps_plan* P, int n, cudaStream_t st) {
+  if (n & 1) CK(cudaMemcpyAsync(P->S, P->S2, (size_t)P->g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
   return LPS_OK;
 }
 
@@ -431,8 +461,10 @@ int enqueue_finalize(lps_plan* P, int k_last, cudaStream_t st) {
 int enqueue_frame(lps_plan* P, cudaStream_t st) {
   int rc;
   if ((rc = enqueue_init(P, st))) return rc;
+  cudaStream_t side = (st == P->cap) ? P->cap_side : P->side;
   for (int k = 1; k <= P->p.max_iters; ++k)
-    if ((rc = enqueue_iter(P, k, st))) return rc;
+    if ((rc = enqueue_iter(P, k, k - 1, st, side))) return rc;
+  if ((rc = enqueue_settle_s(P, P->p.max_iters, st))) return rc;
   if ((rc = enqueue_finalize(P, P->p.max_iters, st))) return rc;
   if (P->p.recursive) {
     const size_t w = support_words(P->g);
@@ -499,10 +531,10 @@ int read_stats(lps_plan* P, lps_stats* s) {
   }
   // support count from the last low-rank/sparse partials
   const int nb = lrs_blocks(P->g);
-  std::vector<float> part((size_t)nb * 4);
+  std::vector<float> part((size_t)nb * 2);
   CK(cudaMemcpy(part.data(), P->lrs_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost));
   long long cnt = 0;
-  for (int t = 0; t < nb; ++t) cnt += (long long)part[(size_t)t * 4 + 3];
+  for (int t = 0; t < nb; ++t) cnt += (long long)part[(size_t)t * 2 + 1];
   s->support_count = cnt;
   return LPS_OK;
 }
@@ -634,6 +666,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = dalloc(P, &P->X, N))) return fail(rc);
   if ((rc = dalloc(P, &P->L, N))) return fail(rc);
   if ((rc = dalloc(P, &P->S, N))) return fail(rc);
+  if ((rc = dalloc(P, &P->S2, N))) return fail(rc);
   if ((rc = dalloc(P, &P->R, N))) return fail(rc);
   if ((rc = dalloc(P, &P->istage, N))) return fail(rc);
   if ((rc = dalloc(P, &P->coils, N * g.ncoil))) return fail(rc);
@@ -646,7 +679,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->V, (size_t)g.nc * g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
-  if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx))) return fail(rc);
+  if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx * 4))) return fail(rc);
   if ((rc = aalloc(P, &P->lrs_part, (size_t)g.ntiles * 4))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
@@ -663,7 +696,11 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
     return fail(LPS_ERR_OOM);
   }
   std::memset(&P->hp, 0, sizeof(DevPersist));
-  if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&P->cap_side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess) {
     set_err("stream creation failed");
     return fail(LPS_ERR_CUDA);
   }
@@ -680,7 +717,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = up(P->tw_x, g.nx)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.nz))) return fail(rc);
   if (cudaMemset(P->persist, 0, sizeof(DevPersist)) != cudaSuccess ||
       cudaMemset(P->ctrl, 0, sizeof(DevCtrl)) != cudaSuccess ||
-      cudaMemset(P->dc_part, 0, g.nx * sizeof(float)) != cudaSuccess ||
+      cudaMemset(P->dc_part, 0, g.nx * 4 * sizeof(float)) != cudaSuccess ||
       cudaMemset(P->lrs_part, 0, g.ntiles * 4 * sizeof(float)) != cudaSuccess ||
       cudaMemset(P->sup_prior, 0, support_words(g) * 4) != cudaSuccess ||
       cudaMemset(P->sup_out, 0, support_words(g) * 4) != cudaSuccess) {
@@ -810,8 +847,9 @@ int lps_iterate(lps_plan* P, int n_iters, lps_stats* stats) {
   }
   for (int i = 0; i < n_iters; ++i) {
     ++P->iters_done;
-    if ((rc = enqueue_iter(P, P->iters_done, P->st))) return rc;
+    if ((rc = enqueue_iter(P, P->iters_done, i, P->st, P->side))) return rc;
   }
+  if ((rc = enqueue_settle_s(P, n_iters, P->st))) return rc;
   if (P->iters_done > 0 && (rc = enqueue_finalize(P, P->iters_done, P->st))) return rc;
   return read_stats(P, stats);
 }
@@ -935,7 +973,7 @@ int lps_set_state(lps_plan* P, const void* X, const void* S, const void* L_prev,
   CK(cudaMemcpyAsync(P->S, S, img, cudaMemcpyDefault, P->st));
   CK(cudaMemcpyAsync(P->L, L_prev ? L_prev : X, img, cudaMemcpyDefault, P->st));
   CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), P->st));
-  CK(cudaMemsetAsync(P->dc_part, 0, P->g.nx * sizeof(float), P->st));
+  CK(cudaMemsetAsync(P->dc_part, 0, P->g.nx * 4 * sizeof(float), P->st));
   CK(cudaMemsetAsync(P->lrs_part, 0, P->g.ntiles * 4 * sizeof(float), P->st));
   DevCtrl c{};
   c.lambda_L = (float)lambda_L;
@@ -1077,11 +1115,11 @@ int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm
   LK(launch_dc(a, kDcUpdate, P->st));
   if (!dev) CK(cudaMemcpyAsync(X, P->R, img, cudaMemcpyDefault, P->st));
   if (resid_norm2) {
-    std::vector<float> part(P->g.nx);
+    std::vector<float> part((size_t)P->g.nx * 4);
     CK(cudaMemcpyAsync(part.data(), P->dc_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost, P->st));
     CK(cudaStreamSynchronize(P->st));
     double s = 0;
-    for (float v : part) s += v;
+    for (int i = 0; i < P->g.nx; ++i) s += part[(size_t)i * 4];
     *resid_norm2 = s;
   } else if (!dev) {
     CK(cudaStreamSynchronize(P->st));

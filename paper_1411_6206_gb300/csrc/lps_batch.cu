@@ -279,7 +279,6 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
       l.X = P->X;
       l.L = P->istage;
       l.S = P->R;
-      l.W = P->W;
       l.sup_prior = P->sup_prior;
       l.lrs_part = P->lrs_part;
       l.persist = P->persist;

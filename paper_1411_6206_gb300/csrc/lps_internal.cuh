@@ -76,8 +76,14 @@ enum DcMode { kDcUpdate = 0, kDcAdjoint = 1, kDcForward = 2 };
 
 struct DcArgs {
   Geom g;
-  const float2* L;          // update: Z = L + S;  forward: image
-  const float2* S;          // update: S (Gram of X - S)
+  const float2* L;          // update (operator form): Z = L + S;  forward: image
+  const float2* S;          // update: S (the iteration's new sparse part; Gram of X - S)
+  // Iteration form of the update (Algorithm 1): L_k is formed here, Z = L_k + S_k, and
+  // X_{k-1} is read from X before X_k is written there.
+  const float2* W;          // [nc][nc]: L_k = (X_{k-1} - S_{k-1}) W in the prologue
+  const float2* Lpre;       // or L_k precomputed (tensor-core reprojection)
+  const float2* Sprev;      // S_{k-1}
+  float2* Lbuf;             // in: L_{k-1} (change statistic), out: L_k
   float2* X;                // update/adjoint: output X
   float2* L_out;            // adjoint: also write X_0 here (L_0 := X_0)
   float2* S_out;            // adjoint: zero S
@@ -89,7 +95,7 @@ struct DcArgs {
   const float2* tw_y;
   const float2* tw_z;
   float2* gram_part;        // [nx][nc][nc]; nullptr = skip
-  float* dc_part;           // [nx] residual-norm partials; nullptr = skip
+  float* dc_part;           // [nx][4]: ||E Z - d||^2, ||Z_k - Z_{k-1}||^2, ||Z_{k-1}||^2, 0; nullptr = skip
   const DevPersist* persist;
   DevCtrl* ctrl;            // nullptr = no convergence gating
 };
@@ -104,21 +110,20 @@ struct XfftArgs {
   int inverse;              // 1: k-space [c][l][kx] -> hybrid [x][c][l]; 0: the reverse
 };
 
-// ---- low-rank reprojection + support-aware sparse step (one CTA per 8x8 tile) ------
+// ---- support-aware sparse step (step 3), one CTA per group of 8x8 tiles ------------
 struct LrsArgs {
   Geom g;
-  const float2* X;
-  float2* L;                // in: L_prev, out: L_new (in place)
-  float2* S;                // in: S_old, out: S_new (in place)
-  const float2* W;          // [nc][nc]
+  const float2* X;          // X_{k-1}
+  const float2* L;          // L_{k-1}
+  float2* S;                // out: S_k
   const uint32_t* sup_prior;
   uint32_t* sup_out;        // nullptr = do not write the support bitmap
-  float* lrs_part;          // [CTAs][4]: l1 off-support, ||dZ||^2, ||Z_old||^2, support count
+  float* lrs_part;          // [CTAs][2]: l1 off the prior support, support count
   const DevPersist* persist;
   DevCtrl* ctrl;
+  double lambda_S_rel;      // lambda_S = lambda_S_rel * max |T(X_0)| until the lambdas are set
   int support_rule;
   int haar_max_only;        // 1: only max |T(X)| into ctrl->haar_max_bits
-  const float2* Lnew;       // non-null: L_new precomputed (precision modes), not (X - S) W here
 };
 
 // ---- Gram reduction + eigendecomposition + SVT + prior pull (one CTA) --------------
@@ -126,8 +131,8 @@ struct EigArgs {
   Geom g;
   const float2* gram_part;  // [nparts][nc][nc]
   int nparts;
-  const float* dc_part;     // [nx]
-  const float* lrs_part;    // [lrs_parts][4]
+  const float* dc_part;     // [nx][4]
+  const float* lrs_part;    // [lrs_parts][2]
   int lrs_parts;            // CTAs of the low-rank/sparse kernel
   float2* W;                // [nc][nc]
   float2* V;                // [nc][nc] warm-start eigenvectors

@@ -42,9 +42,13 @@ struct lps_plan {
   lps_params p;
   Geom g;
   cudaStream_t st = nullptr;
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr;    // capture stream of the frame graph
+  cudaStream_t side = nullptr;   // second stream: the sparse step beside the eigen kernel
+  cudaStream_t cap_side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // device state
   float2 *X = nullptr, *L = nullptr, *S = nullptr, *R = nullptr, *coils = nullptr;
+  float2* S2 = nullptr;   // second sparse-part buffer: iteration k writes S_k while S_{k-1} is read
   float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
   float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
   float2* Lnew = nullptr;   // reprojection output of the precision modes
