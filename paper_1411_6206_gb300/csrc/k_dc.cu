@@ -74,12 +74,35 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2
   const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr);
   if (iter_form && a.W) {
-    // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns.
+    // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns,
+    // one pixel column and 4 output slices per task, into bufB.
     for (int i = tid; i < nz * nz; i += kThreads) wsh[i] = a.W[i];
     for (int e = tid; e < plane; e += kThreads) {
       const int z = e / ny, y = e - (e / ny) * ny;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
       bufA[z * nyp + y] = csub(a.X[gi], a.Sprev[gi]);
+    }
+    __syncthreads();
+    const int nzb = (nz + 3) / 4;
+    for (int task = tid; task < ny * nzb; task += kThreads) {
+      const int y = task % ny, zb = (task / ny) * 4;
+      float2 o[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) o[j] = make_float2(0.f, 0.f);
+      for (int i = 0; i < nz; ++i) {
+        const float2 mv = bufA[i * nyp + y];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (zb + j < nz) {
+            const float2 w = wsh[i * nz + zb + j];
+            o[j].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, o[j].x));
+            o[j].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, o[j].y));
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < 4; ++j)
+        if (zb + j < nz) bufB[(zb + j) * nyp + y] = o[j];
     }
     __syncthreads();
   }
@@ -94,19 +117,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
       pe[k] = z * nyp + y;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
       if (iter_form) {
-        const float2 Sk = a.S[gi];
-        float2 Lk;
-        if (a.W) {
-          Lk = make_float2(0.f, 0.f);
-          for (int i = 0; i < nz; ++i) {
-            const float2 mv = bufA[i * nyp + y], w = wsh[i * nz + z];
-            Lk.x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Lk.x));
-            Lk.y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Lk.y));
-          }
-        } else {
-          Lk = a.Lpre[gi];
-        }
-        Zr[k] = cadd(Lk, Sk);
+        const float2 Lk = a.W ? bufB[z * nyp + y] : a.Lpre[gi];
+        Zr[k] = cadd(Lk, a.S[gi]);
         const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
         a.Lbuf[gi] = Lk;
         dz2 += cabs2(csub(Zr[k], Zo));
@@ -118,7 +130,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
       }
     }
   }
-  if (iter_form && a.W) __syncthreads();   // bufA is the first FFT buffer of the coil loop
+  if (iter_form && a.W) __syncthreads();   // bufA and bufB are the FFT buffers of the coil loop
 
   const float sc = g.scale_yz;
   float resid = 0.f;

@@ -166,13 +166,35 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
   if (iter_form) {
     // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W, column by column of the
     // Casorati matrix (the x-plane holds every slice of its pixels), or the precomputed L_k.
-    float2* Mp = base;   // group 0's first buffer: M_{k-1} as [z][NYP]
+    float2* Mp = base;            // group 0's first buffer: M_{k-1} as [z][NYP]
+    float2* Lsh = base + PLANEP;  // group 0's second buffer: L_k as [z][NYP]
     if (a.W) {
       for (int i = tid; i < NZ * NZ; i += NTH) wsh[i] = a.W[i];
       for (int e = tid; e < PLANE; e += NTH) {
         const int z = e / NY, y = e % NY;
         const long long gi = (long long)z * xy + (long long)x * NY + y;
         Mp[z * NYP + y] = csub(a.X[gi], a.Sprev[gi]);
+      }
+      __syncthreads();
+      // one pixel column y and 8 output slices per task: M[i][y] read once per 8 products,
+      // W rows broadcast across the warp
+      for (int task = tid; task < NY * (NZ / 8); task += NTH) {
+        const int y = task % NY, zb = (task / NY) * 8;
+        float2 o[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) o[j] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int i = 0; i < NZ; ++i) {
+          const float2 mv = Mp[i * NYP + y];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const float2 w = wsh[i * NZ + zb + j];
+            o[j].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, o[j].x));
+            o[j].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, o[j].y));
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Lsh[(zb + j) * NYP + y] = o[j];
       }
     }
     __syncthreads();
@@ -184,20 +206,8 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
       if (PLANE % NT == 0 || e < PLANE) {
         const int z = e / NY, y = e % NY;
         const long long gi = (long long)z * xy + (long long)x * NY + y;
-        const float2 Sk = a.S[gi];
-        float2 Lk;
-        if (a.W) {
-          Lk = make_float2(0.f, 0.f);
-#pragma unroll 8
-          for (int i = 0; i < NZ; ++i) {
-            const float2 mv = Mp[i * NYP + y], w = wsh[i * NZ + z];
-            Lk.x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, Lk.x));
-            Lk.y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, Lk.y));
-          }
-        } else {
-          Lk = a.Lpre[gi];
-        }
-        Zr[k] = cadd(Lk, Sk);
+        const float2 Lk = a.W ? Lsh[z * NYP + y] : a.Lpre[gi];
+        Zr[k] = cadd(Lk, a.S[gi]);
         if (grp == 0) {
           const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
           a.Lbuf[gi] = Lk;
