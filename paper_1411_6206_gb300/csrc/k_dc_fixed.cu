@@ -162,8 +162,13 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
 
   float2 Zr[EPT], acc[EPT];
   float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2 (group 0's elements)
-  const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr) && !conv;
-  if (iter_form) {
+  // Iteration form (Algorithm 1) or operator form (Z = L + S given); nothing is read once the
+  // frame has converged (the iteration form leaves a.L null).
+  const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr);
+  if (conv) {
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) Zr[k] = acc[k] = make_float2(0.f, 0.f);
+  } else if (iter_form) {
     // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W, column by column of the
     // Casorati matrix (the x-plane holds every slice of its pixels), or the precomputed L_k.
     float2* Mp = base;            // group 0's first buffer: M_{k-1} as [z][NYP]

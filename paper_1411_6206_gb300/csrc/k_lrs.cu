@@ -298,6 +298,32 @@ cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
   }
 }
 
+// End of a run of iterations: the sparse step alternates its outputs (S, support words,
+// statistic partials) between two buffers by iteration, and the run may have stopped early
+// on the relative-change rule. Buffer 1 holds the last completed iteration's outputs when
+// the count of iterations completed in this run (iters_done - k0 + 1) is odd; copy them to
+// buffer 0 then.
+__global__ void k_settle(const DevCtrl* __restrict__ ctrl, int k0, float2* S0, const float2* __restrict__ S1,
+                         long long n, uint32_t* sup0, const uint32_t* __restrict__ sup1, long long nw, float* part0,
+                         const float* __restrict__ part1, int np) {
+  pdl_wait();
+  const int done = ctrl->iters_done - k0 + 1;   // iterations completed in this run
+  if (done <= 0 || (done & 1) == 0) return;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long t0 = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  for (long long i = t0; i < n; i += stride) S0[i] = S1[i];
+  for (long long i = t0; i < nw; i += stride) sup0[i] = sup1[i];
+  for (long long i = t0; i < np; i += stride) part0[i] = part1[i];
+}
+
+cudaError_t launch_settle(const DevCtrl* ctrl, int k0, float2* S0, const float2* S1, long long n, uint32_t* sup0,
+                          const uint32_t* sup1, long long nw, float* part0, const float* part1, int np,
+                          cudaStream_t st) {
+  const int blocks = (int)std::min<long long>((n + 255) / 256, 152LL * 4);
+  k_settle<<<blocks, 256, 0, st>>>(ctrl, k0, S0, S1, n, sup0, sup1, nw, part0, part1, np);
+  return cudaGetLastError();
+}
+
 // G = sum of the nparts partials, in partial order (one thread per entry).
 __global__ void k_gram_sum(const float2* __restrict__ part, int nparts, int nn, float2* __restrict__ G) {
   const int e = blockIdx.x * blockDim.x + threadIdx.x;

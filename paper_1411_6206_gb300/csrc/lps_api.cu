@@ -136,9 +136,9 @@ size_t arena_size(const Geom& g, int max_iters) {
   s += 2 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V
   s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
   s += r((size_t)g.plane * sizeof(int));                  // line table
-  s += r((size_t)g.nx * 4 * sizeof(float)) + r((size_t)g.ntiles * 4 * sizeof(float));   // statistic partials
+  s += r((size_t)g.nx * 4 * sizeof(float)) + 2 * r((size_t)g.ntiles * 2 * sizeof(float));   // statistic partials
   s += 2 * r((size_t)g.nc * sizeof(double));
-  s += 2 * r((size_t)(g.N / 32) * sizeof(uint32_t));
+  s += 3 * r((size_t)(g.N / 32) * sizeof(uint32_t));   // support: prior, output, second output
   s += r(sizeof(DevPersist)) + r(sizeof(DevCtrl)) + r((size_t)(max_iters + 2) * sizeof(IterRec));
   return s;
 }
@@ -361,13 +361,15 @@ int enqueue_init(lps_plan* P, cudaStream_t st) {
   return LPS_OK;
 }
 
-EigArgs eig_args(lps_plan* P, int iter, int finalize) {
+// `i`: index of the iteration within its run; the statistics of the previous iteration are in
+// the sparse-step partial buffer i & 1.
+EigArgs eig_args(lps_plan* P, int iter, int finalize, int i) {
   EigArgs e{};
   e.g = P->g;
   e.gram_part = P->gram_part;
   e.nparts = gram_parts(P->g, P->p.precision);
   e.dc_part = P->dc_part;
-  e.lrs_part = P->lrs_part;
+  e.lrs_part = (i & 1) ? P->lrs_part2 : P->lrs_part;
   e.lrs_parts = lrs_blocks(P->g);
   e.W = P->W;
   e.V = P->V;
@@ -393,8 +395,11 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize) {
 // the tensor-core reprojection) and writes X_k, L_k and the next Gram:
 //   main:  eig_k [-> reproj_tc_k] ----------+-> DC_k [-> gram_tc_k]
 //   side:  (after DC_{k-1}) sparse_k -------+
-// S alternates between two buffers: the i-th iteration of a run reads S_{k-1} from one and
-// writes S_k to the other.
+// The sparse step's outputs (S, support words, statistic partials) alternate between two
+// buffers: the i-th iteration of a run reads S_{k-1} from buffer i & 1 and writes iteration k
+// to buffer (i + 1) & 1, so the eigen kernel, which runs beside the next sparse step, still
+// reads the previous iteration's partials; enqueue_settle moves the last completed
+// iteration's buffers into place at the end of the run.
 int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) {
   const bool tc = P->p.precision != LPS_FP32;
   float2* Sprev = (i & 1) ? P->S2 : P->S;
@@ -407,8 +412,8 @@ int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) 
   l.L = P->L;
   l.S = Snew;
   l.sup_prior = P->sup_prior;
-  l.sup_out = P->sup_out;
-  l.lrs_part = P->lrs_part;
+  l.sup_out = (i & 1) ? P->sup_out : P->sup_out2;
+  l.lrs_part = (i & 1) ? P->lrs_part : P->lrs_part2;
   l.persist = P->persist;
   l.ctrl = P->ctrl;
   l.lambda_S_rel = P->p.lambda_S_rel;
@@ -420,7 +425,7 @@ int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) 
     if ((prc = prof_end(P, side))) return prc;
   }
   CK(cudaEventRecord(P->ev_join, side));
-  PROF(2, LK(launch_eig(eig_args(P, k, 0), st)));
+  PROF(2, LK(launch_eig(eig_args(P, k, 0, i), st)));
   if (tc) {
     ReprojTcArgs r{};
     r.g = P->g;
@@ -447,14 +452,17 @@ int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) 
   return LPS_OK;
 }
 
-// After a run of n iterations the current S is in S2 when n is odd: move it to S.
-int enqueue_settle_s(lps_plan* P, int n, cudaStream_t st) {
-  if (n & 1) CK(cudaMemcpyAsync(P->S, P->S2, (size_t)P->g.N * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+// End of a run whose first iteration was k0: the last completed iteration (the eigen kernel
+// may have stopped the run early) decides on the device which buffers hold the result.
+int enqueue_settle(lps_plan* P, int k0, cudaStream_t st) {
+  LK(launch_settle(P->ctrl, k0, P->S, P->S2, P->g.N, P->sup_out, P->sup_out2, (long long)support_words(P->g),
+                   P->lrs_part, P->lrs_part2, 2 * lrs_blocks(P->g), st));
   return LPS_OK;
 }
 
-int enqueue_finalize(lps_plan* P, int k_last, cudaStream_t st) {
-  PROF(2, LK(launch_eig(eig_args(P, k_last + 1, 1), st)));
+// Statistics of the last iteration of a run of n iterations (its partials are in buffer n & 1).
+int enqueue_finalize(lps_plan* P, int k_last, int n, cudaStream_t st) {
+  PROF(2, LK(launch_eig(eig_args(P, k_last + 1, 1, n), st)));
   return LPS_OK;
 }
 
@@ -464,8 +472,8 @@ int enqueue_frame(lps_plan* P, cudaStream_t st) {
   cudaStream_t side = (st == P->cap) ? P->cap_side : P->side;
   for (int k = 1; k <= P->p.max_iters; ++k)
     if ((rc = enqueue_iter(P, k, k - 1, st, side))) return rc;
-  if ((rc = enqueue_settle_s(P, P->p.max_iters, st))) return rc;
-  if ((rc = enqueue_finalize(P, P->p.max_iters, st))) return rc;
+  if ((rc = enqueue_finalize(P, P->p.max_iters, P->p.max_iters, st))) return rc;
+  if ((rc = enqueue_settle(P, 1, st))) return rc;
   if (P->p.recursive) {
     const size_t w = support_words(P->g);
     CK(cudaMemcpyAsync(P->sup_prior, P->sup_out, w * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
@@ -680,7 +688,8 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx * 4))) return fail(rc);
-  if ((rc = aalloc(P, &P->lrs_part, (size_t)g.ntiles * 4))) return fail(rc);
+  if ((rc = aalloc(P, &P->lrs_part, (size_t)g.ntiles * 2))) return fail(rc);
+  if ((rc = aalloc(P, &P->lrs_part2, (size_t)g.ntiles * 2))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
@@ -688,6 +697,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->hist, (size_t)p->max_iters + 2))) return fail(rc);
   if ((rc = aalloc(P, &P->gram_part, (size_t)gram_part_capacity(g) * g.nc * g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sup_out, support_words(g)))) return fail(rc);
+  if ((rc = aalloc(P, &P->sup_out2, support_words(g)))) return fail(rc);
   if ((rc = aalloc(P, &P->sup_prior, support_words(g)))) return fail(rc);
   if (cudaMallocHost((void**)&P->h_ctrl, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMallocHost((void**)&P->h_persist_slots, lps_plan::kSlots * sizeof(DevPersist)) != cudaSuccess ||
@@ -718,9 +728,11 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if (cudaMemset(P->persist, 0, sizeof(DevPersist)) != cudaSuccess ||
       cudaMemset(P->ctrl, 0, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMemset(P->dc_part, 0, g.nx * 4 * sizeof(float)) != cudaSuccess ||
-      cudaMemset(P->lrs_part, 0, g.ntiles * 4 * sizeof(float)) != cudaSuccess ||
+      cudaMemset(P->lrs_part, 0, g.ntiles * 2 * sizeof(float)) != cudaSuccess ||
+      cudaMemset(P->lrs_part2, 0, g.ntiles * 2 * sizeof(float)) != cudaSuccess ||
       cudaMemset(P->sup_prior, 0, support_words(g) * 4) != cudaSuccess ||
-      cudaMemset(P->sup_out, 0, support_words(g) * 4) != cudaSuccess) {
+      cudaMemset(P->sup_out, 0, support_words(g) * 4) != cudaSuccess ||
+      cudaMemset(P->sup_out2, 0, support_words(g) * 4) != cudaSuccess) {
     set_err("device memset failed");
     return fail(LPS_ERR_CUDA);
   }
@@ -845,12 +857,13 @@ int lps_iterate(lps_plan* P, int n_iters, lps_stats* stats) {
     P->iters_done = 0;
     P->state_ready = true;
   }
+  const int k0 = P->iters_done + 1;
   for (int i = 0; i < n_iters; ++i) {
     ++P->iters_done;
     if ((rc = enqueue_iter(P, P->iters_done, i, P->st, P->side))) return rc;
   }
-  if ((rc = enqueue_settle_s(P, n_iters, P->st))) return rc;
-  if (P->iters_done > 0 && (rc = enqueue_finalize(P, P->iters_done, P->st))) return rc;
+  if (P->iters_done > 0 && (rc = enqueue_finalize(P, P->iters_done, n_iters, P->st))) return rc;
+  if ((rc = enqueue_settle(P, k0, P->st))) return rc;
   return read_stats(P, stats);
 }
 
@@ -888,7 +901,7 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
 #ifdef LPS_EIG_PHASE_TIMING
 // probe-only: launch the eigen kernel `reps` times back to back (iteration ids 4000 + r)
 int lps_probe_eig_repeat(lps_plan* P, int reps) {
-  for (int r = 0; r < reps; ++r) LK(launch_eig(eig_args(P, 4000 + r, 0), P->st));
+  for (int r = 0; r < reps; ++r) LK(launch_eig(eig_args(P, 4000 + r, 0, 0), P->st));
   CK(cudaStreamSynchronize(P->st));
   return LPS_OK;
 }
@@ -974,7 +987,7 @@ int lps_set_state(lps_plan* P, const void* X, const void* S, const void* L_prev,
   CK(cudaMemcpyAsync(P->L, L_prev ? L_prev : X, img, cudaMemcpyDefault, P->st));
   CK(cudaMemsetAsync(P->ctrl, 0, sizeof(DevCtrl), P->st));
   CK(cudaMemsetAsync(P->dc_part, 0, P->g.nx * 4 * sizeof(float), P->st));
-  CK(cudaMemsetAsync(P->lrs_part, 0, P->g.ntiles * 4 * sizeof(float), P->st));
+  CK(cudaMemsetAsync(P->lrs_part, 0, P->g.ntiles * 2 * sizeof(float), P->st));
   DevCtrl c{};
   c.lambda_L = (float)lambda_L;
   c.lambda_S = (float)lambda_S;

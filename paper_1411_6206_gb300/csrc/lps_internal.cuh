@@ -181,6 +181,9 @@ bool dc_has_fixed(const Geom& g);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);
 cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st);
+cudaError_t launch_settle(const DevCtrl* ctrl, int k0, float2* S0, const float2* S1, long long n, uint32_t* sup0,
+                          const uint32_t* sup1, long long nw, float* part0, const float* part1, int np,
+                          cudaStream_t st);
 cudaError_t launch_reproj_f32(const float2* X, const float2* S, const float2* W, float2* L, const Geom& g,
                               cudaStream_t st);
 cudaError_t launch_gram_tc(const GramTcArgs& a, int precision, cudaStream_t st);

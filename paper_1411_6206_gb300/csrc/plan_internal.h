@@ -55,8 +55,10 @@ struct lps_plan {
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   int* lines = nullptr;
   float *dc_part = nullptr, *lrs_part = nullptr;
+  float* lrs_part2 = nullptr;     // second buffer of the sparse step's partials
   double *sigma_out = nullptr, *sigma_prev = nullptr;
   uint32_t *sup_out = nullptr, *sup_prior = nullptr;
+  uint32_t* sup_out2 = nullptr;   // second buffer of the sparse step's support words
   DevPersist* persist = nullptr;
   DevCtrl* ctrl = nullptr;
   IterRec* hist = nullptr;

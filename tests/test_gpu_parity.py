@@ -247,6 +247,36 @@ def test_objective_non_increasing_on_gpu(L):
     pl.close()
 
 
+def test_stopping_rule_and_history_match_oracle(L):
+    """The relative-change rule of Sec. 3 (stop once ||Z_k - Z_{k-1}|| / ||Z_{k-1}|| < tol) and
+    the per-iteration statistics (residual, nuclear norm, l1 off the support, objective,
+    relative change) against the oracle; the early stop also checks that the frame's outputs
+    are those of the last completed iteration."""
+    case = make_case(8, 32, 32, 2, seed=21, frac=0.35)
+    tol = 2e-3
+    pl = plan_for(L, case, 8, 32, 32, 2, max_iters=60, tol=tol)
+    recon = torch.empty((8, 32, 32), dtype=torch.complex64, device="cuda")
+    st = pl.reconstruct_frame(recon=recon)
+    h = pl.history()
+    ref = O.priori_ls(up(case["d"]), up(case["coils"]), case["mask"], oracle_params(pl.params))
+    assert ref.iters < 60, "the rule must stop this case early"
+    if st.iters != ref.iters:
+        # allowed only where the oracle's change sits within rounding of tol at the boundary
+        k = min(st.iters, ref.iters)
+        assert abs(st.iters - ref.iters) == 1
+        assert abs(ref.history[k - 1]["rel_change"] - tol) < 1e-3 * tol
+    assert len(h) == st.iters
+    for k in range(min(len(h), len(ref.history))):
+        g, r = h[k], ref.history[k]
+        for key, gk in (("resid2", "resid_norm2"), ("nuclear", "nuclear"), ("l1", "l1_off_support"),
+                        ("objective", "objective")):
+            assert abs(g[gk] - r[key]) <= 1e-3 * abs(r[key]) + 1e-9, (k, key, g[gk], r[key])
+        assert abs(g["rel_change"] - r["rel_change"]) <= 1e-3 * r["rel_change"] + 1e-6, (k, g, r)
+    if st.iters == ref.iters:
+        assert O.nrmse(recon.cpu().numpy(), ref.recon) <= E2E_TOL
+    pl.close()
+
+
 def test_exact_recovery_full_mask(L):
     case = make_case(8, 16, 16, 1, seed=2, full=True, noise=0.0)
     pl, st, recon, *_ = run_frame(L, case, 8, 16, 16, 1, 4, lambda_L_rel=0.0, lambda_S_rel=0.0,
