@@ -10,7 +10,7 @@
 //   3. diagonalises G by cyclic two-sided Jacobi rotations in round-robin order, starting
 //      from A = V_prev^H G V_prev with the previous eigenvectors; each step computes the
 //      nc/2 disjoint rotations, then updates every element of A (J^H A J) and every column
-//      pair of V (V J) in parallel; optionally polished by float64 Jacobi sweeps;
+//      pair of V (V J) in parallel (float64 mode: refined afterwards by k_ritz64_a/b);
 //   4. sigma = sqrt(lambda), step (1) sigma' = max(sigma - lambda_L, 0), step (2)
 //      sigma'' = sigma' - lambda_p (sigma' - sigma_prev) (matched by rank), rank guard
 //      sigma''_i = 0 where sigma_i <= tau sigma_1;
@@ -282,13 +282,6 @@ struct alignas(16) EigShared {
   int lambdas_set, rank_prev, sweeps_prev, has_sigma, v_valid;
 };
 
-struct alignas(16) EigShared64 {
-  double2 A0[kMaxNc * kLd];
-  double2 A1[kMaxNc * kLd];
-  double2 V[kMaxNc * kLd];
-  double2 T[kMaxNc * kLd];   // G V, then the second eigenvector buffer of the Jacobi
-  double4_16a rot[kMaxNc / 2];
-};
 
 // Sum four per-thread floats over the block in a fixed order; valid in every thread.
 __device__ __forceinline__ float4 block_sum4(float4 v, float4* red) {
@@ -372,12 +365,14 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     default: break;
   }
   if (tid >= 32 && tid < 32 + n) sh.sprev[tid - 32] = a.sigma_prev[tid - 32];
-  if (!a.finalize)
-    for (int e = tid; e < nn; e += kEigThreads) sh.V[(e / n) * kLd + e % n] = a.V[e];
+  if (!a.finalize) {
+    const float2* vsrc = a.Vin ? a.Vin : a.V;
+    for (int e = tid; e < nn; e += kEigThreads) sh.V[(e / n) * kLd + e % n] = vsrc[e];
+  }
   // statistics of iteration iter-1: the last warp
   const int sw = (kEigThreads >> 5) - 1;
   float4 st4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if ((tid >> 5) == sw && a.iter > 1) {
+  if ((tid >> 5) == sw && a.iter > 1 && a.part != 2) {
     // x: ||E Z - d||^2, z: ||Z_k - Z_{k-1}||^2, w: ||Z_{k-1}||^2 (data consistency);
     // y: l1 off the prior support (sparse step)
     const int lane = tid & 31;
@@ -394,7 +389,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   float2* sub = sh.A0;   // scratch [ksub][nn], spans A0 and A1 (free until the Jacobi)
   // at most two tasks per thread: ksub * nn <= 2 * kEigThreads (n <= 32)
   float2 gacc0 = make_float2(0.f, 0.f), gacc1 = make_float2(0.f, 0.f);
-  if (!a.finalize) {
+  if (!a.finalize && a.part != 2) {
     gacc0 = gram_chunk(a.gram_part, tid, nn, ksub, a.nparts);
     if (tid + kEigThreads < ksub * nn) gacc1 = gram_chunk(a.gram_part, tid + kEigThreads, nn, ksub, a.nparts);
   }
@@ -408,8 +403,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   __syncthreads();
   if (sh.flags[2]) return;
 
-  // 1. statistics record and the stopping rule
-  if (a.iter > 1 && (tid >> 5) == sw) {
+  // 1. statistics record and the stopping rule (the second part of the float64 mode has done it)
+  if (a.iter > 1 && a.part != 2 && (tid >> 5) == sw) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       st4.x += __shfl_xor_sync(0xffffffffu, st4.x, o);
@@ -438,133 +433,102 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
   }
   if (a.finalize) return;
-  if (tol_on && a.iter > 1) {
+  if (tol_on && a.iter > 1 && a.part != 2) {
     __syncthreads();
     if (sh.flags[3]) return;
   }
   EIG_STAMP(1);
 
-  // 2. Gram matrix: combine the chunk sums in a fixed order; exact Hermitian symmetry
-  if (tid < ksub * nn) sub[tid] = gacc0;
-  if (tid + kEigThreads < ksub * nn) sub[tid + kEigThreads] = gacc1;
-  const bool warm = sh.v_valid != 0;
-  if (!warm)
+  int sweeps = 0;
+  if (a.part != 2) {
+    // 2. Gram matrix: combine the chunk sums in a fixed order; exact Hermitian symmetry
+    if (tid < ksub * nn) sub[tid] = gacc0;
+    if (tid + kEigThreads < ksub * nn) sub[tid + kEigThreads] = gacc1;
+    const bool warm = sh.v_valid != 0;
+    if (!warm)
+      for (int e = tid; e < nn; e += kEigThreads) {
+        const int i = e / n, j = e - i * n;
+        sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+      }
+    for (int e = tid; e < np * np; e += kEigThreads) {
+      const int i = e / np, j = e - (e / np) * np;
+      if (i >= n || j >= n) sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
+    }
+    __syncthreads();
     for (int e = tid; e < nn; e += kEigThreads) {
       const int i = e / n, j = e - i * n;
-      sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-    }
-  for (int e = tid; e < np * np; e += kEigThreads) {
-    const int i = e / np, j = e - (e / np) * np;
-    if (i >= n || j >= n) sh.V[i * kLd + j] = (i == j) ? make_float2(1.f, 0.f) : make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  for (int e = tid; e < nn; e += kEigThreads) {
-    const int i = e / n, j = e - i * n;
-    float2 s = sub[e];
-    for (int q = 1; q < ksub; ++q) s = cadd(s, sub[q * nn + e]);
-    if (i == j) s.y = 0.f;
-    sh.G[i * kLd + j] = s;
-  }
-  __syncthreads();
-  EIG_STAMP(2);
-
-  // 3. Jacobi, warm-started from the previous eigenvectors
-  if (warm) {
-    // A1 = G V, then A0 = V^H A1 (upper triangle, mirrored: exactly Hermitian)
-    for (int e = tid; e < nn; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
-      float2 s = make_float2(0.f, 0.f);
-      for (int k = 0; k < n; ++k) s = cadd(s, cmul(sh.G[i * kLd + k], sh.V[k * kLd + j]));
-      sh.A1[i * kLd + j] = s;
-    }
-    __syncthreads();
-    for (int e = tid; e < nut; e += kEigThreads) {
-      const int i = sh.tri[0][e], j = sh.tri[1][e];
-      float2 s = make_float2(0.f, 0.f);
-      for (int k = 0; k < n; ++k) s = cadd(s, cmulc(sh.V[k * kLd + i], sh.A1[k * kLd + j]));
+      float2 s = sub[e];
+      for (int q = 1; q < ksub; ++q) s = cadd(s, sub[q * nn + e]);
       if (i == j) s.y = 0.f;
-      sh.A0[i * kLd + j] = s;
-      sh.A0[j * kLd + i] = cconj(s);
+      sh.G[i * kLd + j] = s;
     }
-  } else {
-    for (int e = tid; e < nut; e += kEigThreads) {
-      const int i = sh.tri[0][e], j = sh.tri[1][e];
-      const float2 g = sh.G[i * kLd + j];
-      sh.A0[i * kLd + j] = g;
-      sh.A0[j * kLd + i] = cconj(g);
-    }
-  }
-  for (int e = tid; e < np * np; e += kEigThreads) {
-    const int i = e / np, j = e - (e / np) * np;
-    if (i >= n || j >= n) sh.A0[i * kLd + j] = make_float2(0.f, 0.f);
-  }
-  __syncthreads();
-  EIG_STAMP(3);
-  float trace = 0.f;
-  for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
-  float2* Af = sh.A0;
-  float2* Afn = sh.A1;
-  float2* Vf = sh.V;
-  float2* Vfn = sh.V1;
-  const int sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags, nullptr);
-  if (Vf != sh.V) {
-    for (int e = tid; e < np * np; e += kEigThreads) {
-      const int i = e / np, j = e - (e / np) * np;
-      sh.V[i * kLd + j] = Vf[i * kLd + j];
-    }
-  }
-  __syncthreads();
+    __syncthreads();
+    EIG_STAMP(2);
 
-  if (a.eig_fp64) {
-    // Float64 polish: A = V^H G V in double, then double Jacobi sweeps; V <- V Q.
-    EigShared64& d = *reinterpret_cast<EigShared64*>(smem_raw + sizeof(EigShared));
-    for (int e = tid; e < np * np; e += kEigThreads) {
-      const int i = e / np, j = e - (e / np) * np;
-      const float2 v = sh.V[i * kLd + j];
-      d.V[i * kLd + j] = make_double2(v.x, v.y);
-    }
-    __syncthreads();
-    for (int e = tid; e < nn; e += kEigThreads) {
-      const int i = e / n, j = e - (e / n) * n;
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = 0; k < n; ++k) {
-        const float2 gk = sh.G[i * kLd + k];
-        s = add_(s, mul_(make_double2(gk.x, gk.y), d.V[k * kLd + j]));
+    // 3. Jacobi, warm-started from the previous eigenvectors
+    if (warm) {
+      // A1 = G V, then A0 = V^H A1 (upper triangle, mirrored: exactly Hermitian)
+      for (int e = tid; e < nn; e += kEigThreads) {
+        const int i = e / n, j = e - (e / n) * n;
+        float2 s = make_float2(0.f, 0.f);
+        for (int k = 0; k < n; ++k) s = cadd(s, cmul(sh.G[i * kLd + k], sh.V[k * kLd + j]));
+        sh.A1[i * kLd + j] = s;
       }
-      d.T[i * kLd + j] = s;
+      __syncthreads();
+      for (int e = tid; e < nut; e += kEigThreads) {
+        const int i = sh.tri[0][e], j = sh.tri[1][e];
+        float2 s = make_float2(0.f, 0.f);
+        for (int k = 0; k < n; ++k) s = cadd(s, cmulc(sh.V[k * kLd + i], sh.A1[k * kLd + j]));
+        if (i == j) s.y = 0.f;
+        sh.A0[i * kLd + j] = s;
+        sh.A0[j * kLd + i] = cconj(s);
+      }
+    } else {
+      for (int e = tid; e < nut; e += kEigThreads) {
+        const int i = sh.tri[0][e], j = sh.tri[1][e];
+        const float2 g = sh.G[i * kLd + j];
+        sh.A0[i * kLd + j] = g;
+        sh.A0[j * kLd + i] = cconj(g);
+      }
     }
-    __syncthreads();
     for (int e = tid; e < np * np; e += kEigThreads) {
       const int i = e / np, j = e - (e / np) * np;
-      if (i >= n || j >= n) d.A0[i * kLd + j] = make_double2(0.0, 0.0);
-    }
-    for (int e = tid; e < nut; e += kEigThreads) {
-      const int i = sh.tri[0][e], j = sh.tri[1][e];
-      double2 s = make_double2(0.0, 0.0);
-      for (int k = 0; k < n; ++k) s = add_(s, mulc_(d.V[k * kLd + i], d.T[k * kLd + j]));
-      if (i == j) s.y = 0.0;
-      d.A0[i * kLd + j] = s;
-      d.A0[j * kLd + i] = conj_(s);
+      if (i >= n || j >= n) sh.A0[i * kLd + j] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    double tr = 0.0;
-    for (int i = 0; i < n; ++i) tr += fabs(d.A0[i * kLd + i].x);
-    double2* Ad = d.A0;
-    double2* Adn = d.A1;
-    double2* Vd = d.V;
-    double2* Vdn = d.T;
-    // the float32 eigenvectors leave off-diagonals of about 1e-7 |A|: one float64 sweep takes
-    // them to about 1e-14, a second to rounding level
-    jacobi<double>(Ad, Adn, Vd, Vdn, n, 9.0e-16, 1.2e-16 * tr + 1e-300, 3, sh.flags, d.rot);
-    __syncthreads();
-    for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = Ad[i * kLd + i].x;
-    for (int e = tid; e < np * np; e += kEigThreads) {
-      const int i = e / np, j = e - (e / np) * np;
-      const double2 v = Vd[i * kLd + j];
-      sh.V[i * kLd + j] = make_float2((float)v.x, (float)v.y);
+    EIG_STAMP(3);
+    float trace = 0.f;
+    for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
+    float2* Af = sh.A0;
+    float2* Afn = sh.A1;
+    float2* Vf = sh.V;
+    float2* Vfn = sh.V1;
+    sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags, nullptr);
+    if (Vf != sh.V) {
+      for (int e = tid; e < np * np; e += kEigThreads) {
+        const int i = e / np, j = e - (e / np) * np;
+        sh.V[i * kLd + j] = Vf[i * kLd + j];
+      }
     }
-  } else {
+    __syncthreads();
+
+    if (a.part == 1) {
+      // float64 mode, first part: hand the Gram, the float32 eigenvectors and eigenvalues to the
+      // float64 Rayleigh-Ritz kernels (k_ritz64_a, k_ritz64_b)
+      for (int e = tid; e < nn; e += kEigThreads) {
+        const int i = e / n, j = e - (e / n) * n;
+        a.Gout[e] = sh.G[i * kLd + j];
+        a.V[e] = sh.V[i * kLd + j];
+      }
+      for (int i = tid; i < n; i += kEigThreads) a.lam64[i] = (double)Af[i * kLd + i].x;
+      if (tid == 32) ctrl->sweeps_cur = sweeps;
+      return;
+    }
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = (double)Af[i * kLd + i].x;
+  } else {
+    // float64 mode, second part: the Rayleigh-Ritz eigenvalues and refined eigenvectors
+    // (V was loaded with the warm start above)
+    for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = a.lam64[i];
   }
   __syncthreads();
   EIG_STAMP(4);
@@ -634,7 +598,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
     ctrl->nuclear_cur = nuc;
     ctrl->rank_cur = rk;
-    ctrl->sweeps_cur = sweeps;
+    if (a.part != 2) ctrl->sweeps_cur = sweeps;
   }
   EIG_STAMP(5);
   // 5. W = V diag(f) V^H and the eigenvectors for the next warm start
@@ -659,15 +623,99 @@ extern "C" int lps_probe_eig_phases(unsigned long long* out, int n) {
 #endif
 
 cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
-  const size_t smem = sizeof(EigShared) + (a.eig_fp64 ? sizeof(EigShared64) : 0);
-  static size_t set_for = 0;
-  if (smem > 48 * 1024 && set_for < smem) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)(sizeof(EigShared) + sizeof(EigShared64)));
+  const size_t smem = sizeof(EigShared);
+  static bool attr_set = false;
+  if (smem > 48 * 1024 && !attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    set_for = sizeof(EigShared) + sizeof(EigShared64);
+    attr_set = true;
   }
   cudaError_t e = launch_pdl(k_eig, dim3(1), dim3(kEigThreads), smem, st, a);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// float64 Rayleigh-Ritz refinement of the float32 eigendecomposition (LPS_EIG_FP64), one warp
+// per eigenvector j, in two kernels (the second needs every column of A):
+//   k_ritz64_a: A[:, j] = V^H (G v_j)
+//   k_ritz64_b: lambda_j = A_jj + sum_i |A_ij|^2 / (A_jj - A_ii) and
+//               v'_j = v_j + sum_i v_i A_ij / (A_jj - A_ii), normalised,
+// the first- and second-order corrections of the eigenpairs of A = D + F (F the off-diagonal
+// part left by the float32 Jacobi, ~1e-7 |A|), taken only for pairs whose coupling is below
+// 1e-3 of their gap, where the corrected vectors stay orthonormal to ~1e-6; inside a cluster of
+// close eigenvalues (the noise floor) any rotation of the vectors is an eigenbasis to the
+// cluster's width, so the float32 vectors, orthonormal to float32 rounding, are kept there.
+__global__ void __launch_bounds__(32) k_ritz64_a(const RitzArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  if (a.ctrl->converged) return;
+  __shared__ double2 t[kMaxNc];
+  const int n = a.n, j = blockIdx.x, i = threadIdx.x;
+  if (i < n) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const float2 g = a.G[i * n + k], v = a.V[k * n + j];
+      s = add_(s, mul_(make_double2(g.x, g.y), make_double2(v.x, v.y)));
+    }
+    t[i] = s;
+  }
+  __syncwarp();
+  if (i < n) {
+    double2 s = make_double2(0.0, 0.0);
+    for (int k = 0; k < n; ++k) {
+      const float2 v = a.V[k * n + i];
+      s = add_(s, mulc_(make_double2(v.x, v.y), t[k]));
+    }
+    a.A[i * n + j] = s;
+  }
+}
+
+__global__ void __launch_bounds__(32) k_ritz64_b(const RitzArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  if (a.ctrl->converged) return;
+  __shared__ double2 e[kMaxNc];
+  const int n = a.n, j = blockIdx.x, i = threadIdx.x;
+  const double ajj = a.A[j * n + j].x;
+  double dl = 0.0;
+  if (i < n) {
+    double2 c = make_double2(0.0, 0.0);
+    if (i != j) {
+      const double2 aij = a.A[i * n + j];
+      const double gap = ajj - a.A[i * n + i].x;
+      const double m2 = aij.x * aij.x + aij.y * aij.y;
+      if (m2 < 1e-6 * gap * gap) {   // |E_ij| < 1e-3: the dropped second-order terms stay below 1e-6
+        c = make_double2(aij.x / gap, aij.y / gap);
+        dl = m2 / gap;
+      }
+    }
+    e[i] = c;
+  }
+  __syncwarp();
+  // v'_j row i: v_ij + sum_k v_ik e_k
+  double2 v = make_double2(0.0, 0.0);
+  if (i < n) {
+    const float2 vij = a.V[i * n + j];
+    v = make_double2(vij.x, vij.y);
+    for (int k = 0; k < n; ++k) {
+      const float2 vik = a.V[i * n + k];
+      v = add_(v, mul_(make_double2(vik.x, vik.y), e[k]));
+    }
+  }
+  double nrm = v.x * v.x + v.y * v.y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    nrm += __shfl_xor_sync(0xffffffffu, nrm, o);
+    dl += __shfl_xor_sync(0xffffffffu, dl, o);
+  }
+  const double inv = nrm > 0.0 ? 1.0 / sqrt(nrm) : 1.0;
+  if (i < n) a.Vout[i * n + j] = make_float2((float)(v.x * inv), (float)(v.y * inv));
+  if (i == 0) a.lam64[j] = ajj + dl;
+}
+
+cudaError_t launch_ritz64(const RitzArgs& a, cudaStream_t st) {
+  cudaError_t e = launch_pdl(k_ritz64_a, dim3(a.n), dim3(32), 0, st, a);
+  if (e != cudaSuccess) return e;
+  e = launch_pdl(k_ritz64_b, dim3(a.n), dim3(32), 0, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 

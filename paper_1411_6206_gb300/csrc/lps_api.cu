@@ -133,7 +133,8 @@ size_t arena_size(const Geom& g, int max_iters) {
   auto r = [](size_t b) { return ((b + 255) / 256) * 256; };
   size_t s = 0;
   s += r((size_t)gram_part_capacity(g) * g.nc * g.nc * sizeof(float2));   // gram partials
-  s += 2 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V
+  s += 4 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V, float64 mode: Gram, refined V
+  s += r((size_t)g.nc * g.nc * sizeof(double2)) + r((size_t)g.nc * sizeof(double));   // A, eigenvalues
   s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
   s += r((size_t)g.plane * sizeof(int));                  // line table
   s += r((size_t)g.nx * 4 * sizeof(float)) + 2 * r((size_t)g.ntiles * 2 * sizeof(float));   // statistic partials
@@ -425,7 +426,30 @@ int enqueue_iter(lps_plan* P, int k, int i, cudaStream_t st, cudaStream_t side) 
     if ((prc = prof_end(P, side))) return prc;
   }
   CK(cudaEventRecord(P->ev_join, side));
-  PROF(2, LK(launch_eig(eig_args(P, k, 0, i), st)));
+  if (P->p.eig_precision == LPS_EIG_FP64) {
+    // float32 Jacobi, float64 Rayleigh-Ritz refinement over nc CTAs, then the SVT steps
+    EigArgs e1 = eig_args(P, k, 0, i);
+    e1.part = 1;
+    e1.Gout = P->G64in;
+    e1.lam64 = P->lam64;
+    PROF(2, LK(launch_eig(e1, st)));
+    RitzArgs ra{};
+    ra.n = P->g.nc;
+    ra.G = P->G64in;
+    ra.V = P->V;
+    ra.A = P->A64;
+    ra.Vout = P->Vref;
+    ra.lam64 = P->lam64;
+    ra.ctrl = P->ctrl;
+    PROF(2, LK(launch_ritz64(ra, st)));
+    EigArgs e2 = eig_args(P, k, 0, i);
+    e2.part = 2;
+    e2.lam64 = P->lam64;
+    e2.Vin = P->Vref;
+    PROF(2, LK(launch_eig(e2, st)));
+  } else {
+    PROF(2, LK(launch_eig(eig_args(P, k, 0, i), st)));
+  }
   if (tc) {
     ReprojTcArgs r{};
     r.g = P->g;
@@ -685,6 +709,10 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->persist, 1))) return fail(rc);
   if ((rc = aalloc(P, &P->W, (size_t)g.nc * g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->V, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->G64in, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->Vref, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->A64, (size_t)g.nc * g.nc))) return fail(rc);
+  if ((rc = aalloc(P, &P->lam64, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sigma_out, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->sigma_prev, (size_t)g.nc))) return fail(rc);
   if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx * 4))) return fail(rc);

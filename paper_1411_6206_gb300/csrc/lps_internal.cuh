@@ -145,7 +145,25 @@ struct EigArgs {
   int iter;                 // iteration k whose SVT this launch computes (1-based)
   int finalize;             // 1: only record the stats of iteration `iter`-1
   int eig_fp64;
+  // float64 mode: part 1 (statistics, Gram, float32 Jacobi) hands off to the float64
+  // Rayleigh-Ritz kernels, part 2 (singular-value steps and W) continues from their output
+  int part;                 // 0: whole kernel; 1 or 2
+  float2* Gout;             // part 1: the Gram [nc][nc]
+  double* lam64;            // part 1 out: float32 eigenvalues; part 2 in: float64 ones
+  const float2* Vin;        // part 2: refined eigenvectors (else the warm start is V)
 };
+
+// ---- float64 Rayleigh-Ritz refinement of the float32 eigendecomposition ------------
+struct RitzArgs {
+  int n;
+  const float2* G;          // [n][n]
+  const float2* V;          // [n][n] float32 eigenvectors (columns)
+  double2* A;               // [n][n] A = V^H G V (float64)
+  float2* Vout;             // [n][n] refined eigenvectors
+  double* lam64;            // [n] refined eigenvalues
+  const DevCtrl* ctrl;
+};
+cudaError_t launch_ritz64(const RitzArgs& a, cudaStream_t st);
 
 // ---- tensor-core contractions of the precision modes (tcgen05) ----------------------
 constexpr int kPrecTf32 = 1;   // = LPS_TF32_REFINE

@@ -51,6 +51,10 @@ struct lps_plan {
   float2* S2 = nullptr;   // second sparse-part buffer: iteration k writes S_k while S_{k-1} is read
   float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
   float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
+  // float64 eigen mode: Gram, refined eigenvectors, A = V^H G V, eigenvalues
+  float2 *G64in = nullptr, *Vref = nullptr;
+  double2* A64 = nullptr;
+  double* lam64 = nullptr;
   float2* Lnew = nullptr;   // reprojection output of the precision modes
   float2 *tw_x = nullptr, *tw_y = nullptr, *tw_z = nullptr;
   int* lines = nullptr;
