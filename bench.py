@@ -545,11 +545,11 @@ def run_served(args):
     trace.sort()
     res = {}
     for mode in ("served", "plain"):
-        srv = lps.Server(150 * 10 ** 9, max_inflight=0, single_stream=(mode == "plain"))
+        srv = lps.Server(150 * 10 ** 9, max_inflight=0, single_stream=(mode == "plain"), autotune=True)
         sids = [srv.open(lps.params_init(nx=w.nx, ny=w.ny, nz=w.nz, ncoil=w.ncoil, max_iters=w.iters,
                                          recursive=1), c) for w, (c, _) in zip(ws_, inputs)]
         nframe = [0] * len(sids)
-        # warm-up: one frame per session (captures the frame graphs)
+        # warm-up: one frame per session (autotunes and captures the frame graphs)
         tk = [srv.submit(sid, *inputs[k][1][0], srv.now()) for k, sid in enumerate(sids)]
         for t in tk:
             srv.wait(t)

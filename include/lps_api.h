@@ -218,13 +218,16 @@ int lps_get_recon(lps_plan* plan, void* out);
  * data, the candidate shapes of the two per-iteration kernels whose shape is a free choice,
  * and installs the fastest in the plan (its frame graph is captured again):
  *  - data consistency: the compile-time plane kernel where one exists, else/and the
- *    runtime-sized kernel with each candidate ordering of the FFT radix passes along y and z;
- *  - low-rank/sparse update: 8x8 in-plane tiles per CTA.
+ *    runtime-sized kernel with each candidate ordering of the FFT radix passes along y and z,
+ *    coil planes staged in shared memory or read from global memory;
+ *  - sparse update: 8x8 in-plane tiles per CTA.
  * Results are cached per geometry (nx, ny, nz, ncoil, fft_z, precision) for the process.
  * Requires lps_set_coils, lps_set_mask and lps_set_data; synchronises the plan's stream; the
  * plan's state (X, L, S, prior) is not modified. out may be NULL. */
 typedef struct lps_tune_result {
-  int dc_variant;          /* 0: compile-time plane kernel, 1: runtime-sized kernel         */
+  int dc_variant;          /* 0: compile-time plane kernel, 1: runtime-sized kernel with the
+                              coil planes staged in shared memory, 2: the same reading coil
+                              maps from global memory (half the shared memory)              */
   int radix_y[8];          /* FFT passes along y of the runtime-sized kernel (0-terminated) */
   int radix_z[8];          /* FFT passes along z                                            */
   int lrs_tiles;           /* 8x8 tiles per CTA of the low-rank/sparse kernel               */
@@ -234,6 +237,11 @@ typedef struct lps_tune_result {
 } lps_tune_result;
 int lps_autotune(lps_plan* plan, lps_tune_result* out);
 int lps_autotune_clear_cache(void);
+/* Install a launch shape (for instance one measured by lps_autotune in an earlier process):
+ * dc_variant, radix_y / radix_z (variants 1 and 2; their products must be ny and nz) and
+ * lrs_tiles are used, the other fields ignored. Synchronises the plan's stream; the frame
+ * graph is captured again at the next frame. */
+int lps_apply_tune(lps_plan* plan, const lps_tune_result* tune);
 
 /* ---- batches of independent problems -------------------------------------------------
  * Not in the paper: many independent problems (sizes, slices and coils may differ) whose
@@ -270,7 +278,9 @@ typedef struct lps_server_config {
   int max_inflight;          /* frames on the device at once (0 = no limit)                */
   int single_stream;         /* 1: every session on one stream, frames run one after another
                                 in arrival order (the plain frame-by-frame path)           */
-  int reserved[6];           /* must be zero                                               */
+  int autotune;              /* 1: lps_autotune each session on its first frame (cached per
+                                geometry; that frame's latency includes the tuning)        */
+  int reserved[5];           /* must be zero                                               */
 } lps_server_config;
 int lps_server_create(const lps_server_config* cfg, lps_server** out);
 int lps_server_destroy(lps_server* server);

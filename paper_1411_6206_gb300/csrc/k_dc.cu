@@ -17,8 +17,11 @@
 
 namespace lps {
 
-template <int EPT, int MODE>
-__global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
+// STAGE: coil planes staged in shared memory by TMA (1 CTA per SM for large planes); without,
+// the coil values are read from global memory (L2) where they are used, which halves the
+// shared memory so that two CTAs share an SM.
+template <int EPT, int MODE, bool STAGE>
+__global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) {
   const Geom& g = a.g;
   pdl_trigger();
   pdl_wait();
@@ -29,8 +32,8 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   float2* bufA = reinterpret_cast<float2*>(smem);
   float2* bufB = bufA + g.planeP;
   float2* coilS0 = bufB + g.planeP;
-  float2* coilS1 = coilS0 + plane;
-  float2* twy = coilS1 + plane;
+  float2* coilS1 = coilS0 + (STAGE ? plane : 0);
+  float2* twy = coilS1 + (STAGE ? plane : 0);
   float2* twz = twy + ny;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(twz + nz + ((ny + nz) & 1));
   float* red = reinterpret_cast<float*>(mbar + 2);
@@ -44,7 +47,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
 
   for (int i = tid; i < ny; i += kThreads) twy[i] = a.tw_y[i];
   for (int i = tid; i < nz; i += kThreads) twz[i] = a.tw_z[i];
-  if (tid == 0) {
+  if (STAGE && tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
     fence_mbar_init();
@@ -58,7 +61,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   };
   // Thread 0 tracks which slots have a copy in flight (bit s) and their wait parity.
   unsigned inflight = 0;
-  if (tid == 0) {
+  if (STAGE && tid == 0) {
     issue(0, coilS0, &mbar[0]);
     inflight |= 1u;
     if (g.ncoil > 1) {
@@ -71,6 +74,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   float2 Zr[EPT];
   float2 acc[EPT];
   int pe[EPT];    // padded offset z*nyp + y
+  int go[EPT];    // offset z*nx*ny + y of the element in a coil plane starting at x*ny
   float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2
   const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr);
   if (iter_form && a.W) {
@@ -112,9 +116,11 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
     acc[k] = make_float2(0.f, 0.f);
     Zr[k] = make_float2(0.f, 0.f);
     pe[k] = -1;
+    go[k] = 0;
     if (e < plane) {
       const int z = e / ny, y = e - (e / ny) * ny;
       pe[k] = z * nyp + y;
+      go[k] = (int)(z * xy) + y;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
       if (iter_form) {
         const float2 Lk = a.W ? bufB[z * nyp + y] : a.Lpre[gi];
@@ -137,13 +143,16 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
   for (int c = 0; c < g.ncoil; ++c) {
     const int s = c & 1;
     float2* coil = s ? coilS1 : coilS0;
-    const bool bad = !mbar_wait_bounded(&mbar[s], (c >> 1) & 1, errp);
-    if (__syncthreads_or(bad)) {
-      // Give up on this plane; first let the other slot's copy (if any) land.
-      if (tid == 0 && (inflight & (2u >> s))) mbar_wait_bounded(&mbar[s ^ 1], ((c + 1) >> 1) & 1, nullptr);
-      return;
+    const float2* gcoil = a.coils + (long long)c * g.N + (long long)x * ny;   // without staging
+    if (STAGE) {
+      const bool bad = !mbar_wait_bounded(&mbar[s], (c >> 1) & 1, errp);
+      if (__syncthreads_or(bad)) {
+        // Give up on this plane; first let the other slot's copy (if any) land.
+        if (tid == 0 && (inflight & (2u >> s))) mbar_wait_bounded(&mbar[s ^ 1], ((c + 1) >> 1) & 1, nullptr);
+        return;
+      }
+      if (tid == 0) inflight &= ~(1u << s);
     }
-    if (tid == 0) inflight &= ~(1u << s);
     float2* src = bufA;
     float2* dst = bufB;
     const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
@@ -152,7 +161,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = tid + k * kThreads;
-        if (e < plane) src[pe[k]] = cscale(cmul(coil[e], Zr[k]), sc);
+        if (e < plane) src[pe[k]] = cscale(cmul(STAGE ? coil[e] : __ldg(gcoil + go[k]), Zr[k]), sc);
       }
       __syncthreads();
       fft_run(&src, &dst, g.py, nz, 1, nyp, twy, false);
@@ -161,7 +170,7 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
         float2* ho = a.hyb_out + ((long long)x * g.ncoil + c) * g.mpad;
         for (int l = tid; l < m; l += kThreads) ho[l] = src[a.lines[l]];
         __syncthreads();
-        if (tid == 0 && c + 2 < g.ncoil) {
+        if (STAGE && tid == 0 && c + 2 < g.ncoil) {
           fence_proxy_async();
           issue(c + 2, coil, &mbar[s]);
           inflight |= 1u << s;
@@ -198,14 +207,14 @@ __global__ void __launch_bounds__(kThreads, 1) k_dc(const DcArgs a) {
       const int e = tid + k * kThreads;
       if (e < plane) {
         const float2 r = src[pe[k]];
-        const float2 cc = coil[e];
+        const float2 cc = STAGE ? coil[e] : __ldg(gcoil + go[k]);
         const float2 v = cmulc(cc, r);   // conj(C) * r
         acc[k].x = fmaf(v.x, sc, acc[k].x);
         acc[k].y = fmaf(v.y, sc, acc[k].y);
       }
     }
     __syncthreads();
-    if (tid == 0 && c + 2 < g.ncoil) {
+    if (STAGE && tid == 0 && c + 2 < g.ncoil) {
       fence_proxy_async();
       issue(c + 2, coil, &mbar[s]);
       inflight |= 1u << s;
@@ -277,7 +286,7 @@ int dc_ept(const Geom& g) {
 size_t dc_smem_bytes(const Geom& g) {
   size_t b = 0;
   b += 2 * (size_t)g.planeP * sizeof(float2);
-  b += 2 * (size_t)g.plane * sizeof(float2);
+  if (!g.dc_direct) b += 2 * (size_t)g.plane * sizeof(float2);   // staged coil planes
   b += (size_t)(g.ny + g.nz + ((g.ny + g.nz) & 1)) * sizeof(float2);
   b += 2 * sizeof(uint64_t);
   b += 32 * sizeof(float);
@@ -285,33 +294,36 @@ size_t dc_smem_bytes(const Geom& g) {
   return b;
 }
 
-template <int EPT, int MODE>
+template <int EPT, int MODE, bool STAGE>
 static cudaError_t launch_dc_t(const DcArgs& a, cudaStream_t st) {
   const size_t smem = dc_smem_bytes(a.g);
   static bool attr_set = false;
-  static size_t attr_bytes = 0;
-  if (!attr_set || smem > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_dc<EPT, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_dc<EPT, MODE, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
-    attr_bytes = 227 * 1024;
   }
-  cudaError_t e = launch_pdl(k_dc<EPT, MODE>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
+  cudaError_t e = launch_pdl(k_dc<EPT, MODE, STAGE>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int MODE>
+template <int MODE, bool STAGE>
 static cudaError_t launch_dc_m(const DcArgs& a, cudaStream_t st) {
   switch (dc_ept(a.g)) {
-    case 1: return launch_dc_t<1, MODE>(a, st);
-    case 2: return launch_dc_t<2, MODE>(a, st);
-    case 4: return launch_dc_t<4, MODE>(a, st);
-    case 8: return launch_dc_t<8, MODE>(a, st);
-    case 16: return launch_dc_t<16, MODE>(a, st);
-    case 24: return launch_dc_t<24, MODE>(a, st);
+    case 1: return launch_dc_t<1, MODE, STAGE>(a, st);
+    case 2: return launch_dc_t<2, MODE, STAGE>(a, st);
+    case 4: return launch_dc_t<4, MODE, STAGE>(a, st);
+    case 8: return launch_dc_t<8, MODE, STAGE>(a, st);
+    case 16: return launch_dc_t<16, MODE, STAGE>(a, st);
+    case 24: return launch_dc_t<24, MODE, STAGE>(a, st);
     default: return cudaErrorInvalidValue;
   }
+}
+
+template <int MODE>
+static cudaError_t launch_dc_s(const DcArgs& a, cudaStream_t st) {
+  return a.g.dc_direct ? launch_dc_m<MODE, false>(a, st) : launch_dc_m<MODE, true>(a, st);
 }
 
 cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st);
@@ -322,9 +334,9 @@ cudaError_t launch_dc(const DcArgs& a, int mode, cudaStream_t st) {
   if (ef != cudaErrorNotSupported) return ef;
   if (dc_smem_bytes(a.g) > 227 * 1024) return cudaErrorInvalidValue;
   switch (mode) {
-    case kDcUpdate: return launch_dc_m<kDcUpdate>(a, st);
-    case kDcAdjoint: return launch_dc_m<kDcAdjoint>(a, st);
-    case kDcForward: return launch_dc_m<kDcForward>(a, st);
+    case kDcUpdate: return launch_dc_s<kDcUpdate>(a, st);
+    case kDcAdjoint: return launch_dc_s<kDcAdjoint>(a, st);
+    case kDcForward: return launch_dc_s<kDcForward>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }

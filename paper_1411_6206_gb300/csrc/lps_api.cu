@@ -188,6 +188,13 @@ int validate(const lps_params* p, Geom* gout) {
     set_err("FFT lengths need prime factors <= 64 and at most %d passes", kMaxPasses);
     return LPS_ERR_UNSUPPORTED;
   }
+  // runtime-sized DC kernel: with more planes than SMs, read the coil maps from global memory
+  // (two CTAs per SM) when that fits; lps_autotune measures both
+  if (g.nx > 152) {
+    Geom gd = g;
+    gd.dc_direct = 1;
+    g.dc_direct = dc_smem_bytes(gd) <= 113 * 1024 ? 1 : 0;
+  }
   if (dc_ept(g) < 0 || dc_smem_bytes(g) > 227 * 1024) {
     set_err("x-plane of %d x %d does not fit one CTA", p->ny, p->nz);
     return LPS_ERR_UNSUPPORTED;

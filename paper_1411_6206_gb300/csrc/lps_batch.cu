@@ -11,8 +11,9 @@
 // The autotuner times, on a plan's own resident data, the candidate launch shapes of the two
 // per-iteration kernels whose shape is a free choice: the data-consistency kernel (the
 // compile-time plane kernel where one exists, else the runtime-sized kernel with every
-// candidate ordering of FFT radix passes along y and z) and the low-rank/sparse kernel (8x8
-// tiles per CTA). The fastest is installed in the plan; results are cached per geometry.
+// candidate ordering of FFT radix passes along y and z, with the coil planes staged in shared
+// memory or read from global memory) and the sparse-step kernel (8x8 tiles per CTA). The
+// fastest is installed in the plan; results are cached per geometry.
 #include "plan_internal.h"
 
 #include <algorithm>
@@ -111,7 +112,8 @@ std::mutex g_tune_mutex;
 std::map<TuneKey, TuneEntry> g_tune_cache;
 
 void install(lps_plan* P, const TuneEntry& t) {
-  P->g.dc_generic = t.res.dc_variant;
+  P->g.dc_generic = t.res.dc_variant != 0;
+  P->g.dc_direct = t.res.dc_variant == 2;
   if (t.res.dc_variant) {
     P->g.py = t.py;
     P->g.pz = t.pz;
@@ -248,22 +250,24 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
   {
     const std::vector<FftPlan> cy = fft_candidates(g0.ny, 6);
     const std::vector<FftPlan> cz = fft_candidates(g0.nz, 4);
-    for (const FftPlan& py : cy)
-      for (const FftPlan& pz : cz) {
-        Geom g = g0;
-        g.dc_generic = 1;
-        g.py = py;
-        g.pz = pz;
-        double us;
-        if ((rc = dc_time(g, &us))) goto done;
-        ++count;
-        if (us < best.res.dc_us) {
-          best.res.dc_us = us;
-          best.res.dc_variant = 1;
-          best.py = py;
-          best.pz = pz;
+    for (int direct = 0; direct < 2; ++direct)
+      for (const FftPlan& py : cy)
+        for (const FftPlan& pz : cz) {
+          Geom g = g0;
+          g.dc_generic = 1;
+          g.dc_direct = direct;
+          g.py = py;
+          g.pz = pz;
+          double us;
+          if ((rc = dc_time(g, &us))) goto done;
+          ++count;
+          if (us < best.res.dc_us) {
+            best.res.dc_us = us;
+            best.res.dc_variant = 1 + direct;
+            best.py = py;
+            best.pz = pz;
+          }
         }
-      }
   }
   // low-rank / sparse kernel: 8x8 tiles per CTA
   {
@@ -309,6 +313,40 @@ done:
   cudaStreamSynchronize(P->st);
   cudaFree(ctrl);
   return rc;
+}
+
+int lps_apply_tune(lps_plan* P, const lps_tune_result* t) {
+  ARG(P != nullptr && t != nullptr, "NULL argument");
+  ARG(t->dc_variant >= 0 && t->dc_variant <= 2, "dc_variant must be 0, 1 or 2");
+  ARG(t->lrs_tiles >= 1 && t->lrs_tiles <= 32 / P->g.nc, "lrs_tiles must be in 1..32/nz");
+  TuneEntry e{};
+  e.res = *t;
+  if (t->dc_variant == 0) {
+    Geom g = P->g;
+    g.dc_generic = 0;
+    ARG(dc_has_fixed(g), "no compile-time kernel for this plane size");
+  } else {
+    auto plan_of = [&](const int* r, int n, FftPlan& f) -> bool {
+      f = FftPlan{};
+      f.n = n;
+      long long prod = 1;
+      for (int i = 0; i < 8 && r[i]; ++i) {
+        if (r[i] < 2 || r[i] > 64) return false;
+        f.r[f.np++] = r[i];
+        prod *= r[i];
+      }
+      return f.np > 0 && prod == n;
+    };
+    ARG(plan_of(t->radix_y, P->g.ny, e.py), "radix_y does not factor ny");
+    ARG(plan_of(t->radix_z, P->g.nz, e.pz), "radix_z does not factor nz");
+  }
+  ARG(cudaStreamSynchronize(P->st) == cudaSuccess, "stream error");
+  install(P, e);
+  if (dc_smem_bytes(P->g) > 227 * 1024) {
+    set_err("the plane does not fit one CTA with this variant");
+    return LPS_ERR_UNSUPPORTED;
+  }
+  return LPS_OK;
 }
 
 int lps_autotune_clear_cache(void) {

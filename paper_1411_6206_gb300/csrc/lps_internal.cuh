@@ -68,6 +68,7 @@ struct Geom {
   float scale_x;            // 1/sqrt(nx)
   FftPlan py, pz, px;
   int dc_generic;           // 1: always the runtime-sized data-consistency kernel (autotuner)
+  int dc_direct;            // runtime-sized kernel reads coil maps from global memory (no staging)
   int lrs_tpc;              // 8x8 tiles per CTA of the low-rank/sparse kernel (0: 32 / nc)
 };
 
@@ -429,6 +430,21 @@ __device__ __forceinline__ void dft_reg(float2* v, bool inv, const float2* tw, i
   }
 }
 
+// Division by a divisor fixed for a whole pass: q = floor(t * m / 2^32) with m = ceil(2^32 / d)
+// is floor(t / d) or one more (for t < 2^32), corrected once.
+struct FastDiv {
+  unsigned d, m;
+};
+__device__ __forceinline__ FastDiv make_fdiv(unsigned d) {
+  return FastDiv{d, d > 1 ? (unsigned)(0xFFFFFFFFull / d + 1ull) : 0u};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned t, FastDiv f) {
+  if (f.d == 1) return t;
+  unsigned q = __umulhi(t, f.m);
+  if (q * f.d > t) --q;
+  return q;
+}
+
 // One Stockham pass over `nb` transforms of length n held in shared memory.
 // Element i of transform b is at base[b*bs + i*es]. Ns = product of the radices of the
 // previous passes. Twiddle table tw[q] = exp(-2 pi i q / n). Batch index runs fastest
@@ -440,10 +456,12 @@ __device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2
   const int nbf = n / R;
   const int total = nb * nbf;
   const int tws = n / (Ns * R);
+  const FastDiv fnb = make_fdiv((unsigned)nb), fns = make_fdiv((unsigned)Ns);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = t % nb;
-    const int j = t / nb;
-    const int k = j % Ns;
+    const int j = (int)fdiv((unsigned)t, fnb);
+    const int b = t - j * nb;
+    const int jq = (int)fdiv((unsigned)j, fns);
+    const int k = j - jq * Ns;
     const float2* src = in + b * bs;
     float2 v[R];
 #pragma unroll
@@ -457,7 +475,7 @@ __device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2
       }
     }
     dft_reg<R>(v, inv, tw, n);
-    const int idxD = (j / Ns) * Ns * R + k;
+    const int idxD = jq * Ns * R + k;
     float2* dst = out + b * bs;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];
@@ -472,12 +490,14 @@ __device__ __forceinline__ void fft_pass_any(const float2* __restrict__ in, floa
   const int total = nb * n;
   const int tws = n / (Ns * R);
   const int st = n / R;
+  const FastDiv fnb = make_fdiv((unsigned)nb), fnbf = make_fdiv((unsigned)nbf), fns = make_fdiv((unsigned)Ns);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
-    const int b = t % nb;
-    const int rest = t / nb;
-    const int j = rest % nbf;
-    const int s = rest / nbf;
-    const int k = j % Ns;
+    const int rest = (int)fdiv((unsigned)t, fnb);
+    const int b = t - rest * nb;
+    const int s = (int)fdiv((unsigned)rest, fnbf);
+    const int j = rest - s * nbf;
+    const int jq = (int)fdiv((unsigned)j, fns);
+    const int k = j - jq * Ns;
     const float2* src = in + b * bs;
     float2 acc = make_float2(0.f, 0.f);
     for (int r = 0; r < R; ++r) {
@@ -490,7 +510,7 @@ __device__ __forceinline__ void fft_pass_any(const float2* __restrict__ in, floa
       }
       acc = cadd(acc, cmul(cmul(v, w), u));
     }
-    const int idxD = (j / Ns) * Ns * R + k;
+    const int idxD = jq * Ns * R + k;
     out[b * bs + (idxD + s * Ns) * es] = acc;
   }
 }

@@ -34,6 +34,7 @@ struct Session {
   size_t bytes = 0;           // admitted device bytes
   int queued = 0;             // frames submitted and not yet completed
   bool shared = false;        // the server's single stream
+  bool tuned = false;         // launch shapes picked (autotune on the first frame)
 };
 
 struct Frame {
@@ -78,6 +79,10 @@ int issue(lps_server* S, Frame& f) {
   int rc = lps_set_mask(P, f.mask.data(), &nl);
   if (rc) return rc;
   if ((rc = lps_set_data(P, f.kdata, nl))) return rc;
+  if (S->cfg.autotune && !s.tuned) {
+    if ((rc = lps_autotune(P, nullptr))) return rc;
+    s.tuned = true;
+  }
   if ((rc = lps_reconstruct_frame(P, nullptr, nullptr, nullptr, nullptr, nullptr, nullptr))) return rc;
   if (launch_combine(P->L, P->S, s.out, P->g.N, s.st) != cudaSuccess) {
     set_err("launch of the L + S kernel failed");
@@ -137,6 +142,7 @@ int lps_server_create(const lps_server_config* cfg, lps_server** out) {
   ARG(cfg->hbm_budget_bytes > 0 && cfg->max_inflight >= 0, "bad server config");
   for (int r : cfg->reserved) ARG(r == 0, "reserved fields must be zero");
   ARG(cfg->single_stream == 0 || cfg->single_stream == 1, "single_stream must be 0 or 1");
+  ARG(cfg->autotune == 0 || cfg->autotune == 1, "autotune must be 0 or 1");
   lps_server* S = new lps_server();
   S->cfg = *cfg;
   if (cudaStreamCreateWithFlags(&S->ref_st, cudaStreamNonBlocking) != cudaSuccess ||

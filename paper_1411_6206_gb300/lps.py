@@ -85,7 +85,7 @@ class TuneResult(C.Structure):
 
 class ServerConfig(C.Structure):
     _fields_ = [("hbm_budget_bytes", C.c_size_t), ("max_inflight", C.c_int), ("single_stream", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("autotune", C.c_int), ("reserved", C.c_int * 5)]
 
 
 class LpsError(RuntimeError):
@@ -130,6 +130,7 @@ _SIGS = {
     "lps_get_recon": ([_VP, _VP], C.c_int),
     "lps_autotune": ([_VP, _VP], C.c_int),
     "lps_autotune_clear_cache": ([], C.c_int),
+    "lps_apply_tune": ([_VP, C.POINTER(TuneResult)], C.c_int),
     "lps_batch_create": ([C.POINTER(Params), C.c_int, _VP, C.POINTER(_VP)], C.c_int),
     "lps_batch_destroy": ([_VP], C.c_int),
     "lps_batch_size": ([_VP], C.c_int),
@@ -367,6 +368,17 @@ def autotune(plan: int) -> TuneResult:
     return r
 
 
+def apply_tune(plan: int, dc_variant: int, radix_y=(), radix_z=(), lrs_tiles: int = 1):
+    t = TuneResult()
+    t.dc_variant = dc_variant
+    for i, r in enumerate(radix_y):
+        t.radix_y[i] = r
+    for i, r in enumerate(radix_z):
+        t.radix_z[i] = r
+    t.lrs_tiles = lrs_tiles
+    _check(load().lps_apply_tune(plan, C.byref(t)), "apply_tune")
+
+
 def autotune_clear_cache():
     _check(load().lps_autotune_clear_cache(), "autotune_clear_cache")
 
@@ -511,9 +523,10 @@ class Server:
     frames issued as slots free up (max_inflight = 0: no limit); single_stream runs every frame
     in arrival order on one stream (the plain frame-by-frame path)."""
 
-    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 0, single_stream: bool = False):
+    def __init__(self, hbm_budget_bytes: int, max_inflight: int = 0, single_stream: bool = False,
+                 autotune: bool = False):
         cfg = ServerConfig(hbm_budget_bytes=int(hbm_budget_bytes), max_inflight=int(max_inflight),
-                           single_stream=int(bool(single_stream)))
+                           single_stream=int(bool(single_stream)), autotune=int(bool(autotune)))
         h = _VP()
         _check(load().lps_server_create(C.byref(cfg), C.byref(h)), "server_create")
         self.handle = h.value

@@ -134,3 +134,25 @@ def test_autotuned_frame_matches_oracle(L, nz, nx, ny, nc):
     assert pl2.autotune().cached == 1
     pl.close()
     pl2.close()
+
+
+@pytest.mark.parametrize("variant,ry,rz", [(1, (8, 16), (16,)), (2, (16, 8), (4, 4)), (2, (2, 8, 8), (2, 8)),
+                                           (1, (4, 4, 8), (8, 2))])
+def test_installed_launch_shapes_keep_parity(L, variant, ry, rz):
+    """Every kernel variant and FFT radix ordering the autotuner can pick, installed by hand
+    (runtime-sized kernel with staged or global-memory coil maps) on the cardiac plane size,
+    against the oracle."""
+    nz, nx, ny, nc = 16, 32, 128, 3
+    case = make_case(nz, nx, ny, nc, seed=17, frac=0.3)
+    pl = L.Plan(nx, ny, nz, nc, max_iters=15)
+    pl.set_coils(dev(case["coils"]))
+    pl.set_mask(case["mask"])
+    pl.set_data(dev(case["d"]))
+    L.apply_tune(pl.handle, variant, ry, rz, lrs_tiles=1)
+    recon = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    pl.reconstruct_frame(recon=recon)
+    ref = O.priori_ls(up(case["d"]), up(case["coils"]), case["mask"], oracle_params(pl.params))
+    assert O.nrmse(recon.cpu().numpy(), ref.recon) <= E2E_TOL
+    with pytest.raises(L.LpsError):
+        L.apply_tune(pl.handle, 1, (8, 8), (16,))      # 64 != ny
+    pl.close()
