@@ -264,17 +264,13 @@ struct alignas(16) EigShared {
   float2 V[kMaxNc * kLd];
   float2 G[kMaxNc * kLd];
   float2 V1[kMaxNc * kLd];   // second eigenvector buffer of the Jacobi permutation
-  float sig[kMaxNc];       // sigma by rank
   float f[kMaxNc];         // sigma''_i / sigma_i
   double lam[kMaxNc];      // eigenvalues
-  double lams[kMaxNc];     // eigenvalues by rank
-  int rank[kMaxNc];
   int flags[4];
   float red[4][32];
   float4 red4[32];
   unsigned char tri[2][kMaxNc * (kMaxNc + 1) / 2];   // (i, j) of upper-triangle entry e
   double sprev[kMaxNc];    // sigma_prev
-  double s2[kMaxNc];       // sigma'' by rank
   // control scalars read once at entry
   double nuc_prev;
   float sig_prev1;         // nuclear norm of the previous iteration as float (finiteness test)
@@ -533,73 +529,86 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   __syncthreads();
   EIG_STAMP(4);
 
-  // 4. singular values, thresholds, prior pull, rank guard: one thread per eigenvalue; in
-  //    float64 after the float64 eigendecomposition, in float32 otherwise (float64 issues at
-  //    a small fraction of the float32 rate on this part).
-  if (tid < n) {
+  // 4. singular values, thresholds, prior pull, rank guard: warp 0, lane i = eigenvalue i
+  //    (n <= 32), ranks and sums by shuffles; in float64 after the float64 refinement, in
+  //    float32 otherwise (float64 issues at a small fraction of the float32 rate here).
+  if (tid < 32) {
+    const int i = tid;
+    const bool act = i < n;
+    const unsigned full = 0xffffffffu;
+    double s2d = 0.0;
     int r = 0;
-    const double li = sh.lam[tid];
     if (a.eig_fp64) {
+      const double li = act ? sh.lam[i] : -1.0e300;
       for (int j = 0; j < n; ++j) {
-        const double lj = sh.lam[j];
-        r += (lj > li) || (lj == li && j < tid);
+        const double lj = __shfl_sync(full, li, j);
+        r += (lj > li) || (lj == li && j < i);
+      }
+      const double s = act ? sqrt(fmax(li, 0.0)) : 0.0;
+      double sig1 = s;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sig1 = fmax(sig1, __shfl_xor_sync(full, sig1, o));
+      if (a.iter == 1 && !sh.lambdas_set) {
+        sh.lamL = (float)(a.lambda_L_rel * sig1);
+        sh.lamS = (float)(a.lambda_S_rel * (double)sh.haar_max);
+        if (i == 0) {
+          ctrl->lambda_L = sh.lamL;
+          ctrl->lambda_S = sh.lamS;
+          ctrl->sigma_max = sig1;
+          ctrl->lambdas_set = 1;
+        }
+      }
+      __syncwarp();
+      if (act) {
+        const double s1 = fmax(s - (double)sh.lamL, 0.0);
+        s2d = sh.has_sigma ? s1 - a.lambda_p * (s1 - sh.sprev[r]) : s1;
+        if (s <= a.rank_tau * sig1) s2d = 0.0;
+        sh.f[i] = s > 0.0 ? (float)(s2d / s) : 0.f;
       }
     } else {
-      const float lf = (float)li;
+      const float li = act ? (float)sh.lam[i] : -3.0e38f;
       for (int j = 0; j < n; ++j) {
-        const float lj = (float)sh.lam[j];
-        r += (lj > lf) || (lj == lf && j < tid);
+        const float lj = __shfl_sync(full, li, j);
+        r += (lj > li) || (lj == li && j < i);
+      }
+      const float s = act ? sqrtf(fmaxf(li, 0.f)) : 0.f;
+      float sig1 = s;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) sig1 = fmaxf(sig1, __shfl_xor_sync(full, sig1, o));
+      if (a.iter == 1 && !sh.lambdas_set) {
+        sh.lamL = (float)(a.lambda_L_rel * (double)sig1);
+        sh.lamS = (float)(a.lambda_S_rel * (double)sh.haar_max);
+        if (i == 0) {
+          ctrl->lambda_L = sh.lamL;
+          ctrl->lambda_S = sh.lamS;
+          ctrl->sigma_max = (double)sig1;
+          ctrl->lambdas_set = 1;
+        }
+      }
+      __syncwarp();
+      if (act) {
+        const float s1 = fmaxf(s - sh.lamL, 0.f);
+        float s2 = sh.has_sigma ? s1 - (float)a.lambda_p * (s1 - (float)sh.sprev[r]) : s1;
+        if (s <= (float)a.rank_tau * sig1) s2 = 0.f;
+        sh.f[i] = s > 0.f ? s2 / s : 0.f;
+        s2d = (double)s2;
       }
     }
-    sh.rank[tid] = r;
-    sh.lams[r] = li;
-    sh.sig[r] = sqrtf(fmaxf((float)li, 0.f));
-  }
-  __syncthreads();
-  if (tid == 0 && a.iter == 1 && !sh.lambdas_set) {
-    const double sig1 = a.eig_fp64 ? sqrt(fmax(sh.lams[0], 0.0)) : (double)sh.sig[0];
-    sh.lamL = (float)(a.lambda_L_rel * sig1);
-    sh.lamS = (float)(a.lambda_S_rel * (double)sh.haar_max);
-    ctrl->lambda_L = sh.lamL;
-    ctrl->lambda_S = sh.lamS;
-    ctrl->sigma_max = sig1;
-    ctrl->lambdas_set = 1;
-  }
-  __syncthreads();
-  if (tid < n) {
-    const int r = sh.rank[tid];
-    const bool has_sigma = sh.has_sigma != 0;
-    if (a.eig_fp64) {
-      const double s = sqrt(fmax(sh.lam[tid], 0.0));
-      const double sig1 = sqrt(fmax(sh.lams[0], 0.0));
-      const double s1 = fmax(s - (double)sh.lamL, 0.0);
-      double s2 = has_sigma ? s1 - a.lambda_p * (s1 - sh.sprev[r]) : s1;
-      if (s <= a.rank_tau * sig1) s2 = 0.0;
-      sh.s2[r] = s2;
-      sh.f[tid] = s > 0.0 ? (float)(s2 / s) : 0.f;
-    } else {
-      const float s = sh.sig[r];
-      const float sig1 = sh.sig[0];
-      const float s1 = fmaxf(s - sh.lamL, 0.f);
-      float s2 = has_sigma ? s1 - (float)a.lambda_p * (s1 - (float)sh.sprev[r]) : s1;
-      if (s <= (float)a.rank_tau * sig1) s2 = 0.f;
-      sh.s2[r] = (double)s2;
-      sh.f[tid] = s > 0.f ? s2 / s : 0.f;
+    if (act) a.sigma_out[r] = s2d;   // sigma'' in rank order
+    double nuc = s2d;
+    int rk = s2d > 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      nuc += __shfl_xor_sync(full, nuc, o);
+      rk += __shfl_xor_sync(full, rk, o);
+    }
+    if (i == 0) {
+      ctrl->nuclear_cur = nuc;
+      ctrl->rank_cur = rk;
+      if (a.part != 2) ctrl->sweeps_cur = sweeps;
     }
   }
   __syncthreads();
-  if (tid < n) a.sigma_out[tid] = sh.s2[tid];
-  if (tid == 32) {
-    double nuc = 0.0;
-    int rk = 0;
-    for (int r = 0; r < n; ++r) {
-      nuc += sh.s2[r];
-      rk += sh.s2[r] > 0.0;
-    }
-    ctrl->nuclear_cur = nuc;
-    ctrl->rank_cur = rk;
-    if (a.part != 2) ctrl->sweeps_cur = sweeps;
-  }
   EIG_STAMP(5);
   // 5. W = V diag(f) V^H and the eigenvectors for the next warm start
   for (int e = tid; e < nn; e += kEigThreads) {
