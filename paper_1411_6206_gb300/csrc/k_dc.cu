@@ -77,15 +77,40 @@ __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) 
   int go[EPT];    // offset z*nx*ny + y of the element in a coil plane starting at x*ny
   float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2 and ||Z_{k-1}||^2
   const bool iter_form = MODE == kDcUpdate && (a.W != nullptr || a.Lpre != nullptr);
+  // Every per-element global load is issued first, so that their latencies overlap: S_k,
+  // X_{k-1}, S_{k-1} and L_{k-1} of the iteration form give M_{k-1} (into bufA), and
+  // S_k - Z_{k-1} is kept for the change statistic.
+  float2 Dz[EPT];
+#pragma unroll
+  for (int k = 0; k < EPT; ++k) {
+    const int e = tid + k * kThreads;
+    acc[k] = make_float2(0.f, 0.f);
+    Zr[k] = Dz[k] = make_float2(0.f, 0.f);
+    pe[k] = -1;
+    go[k] = 0;
+    if (e < plane) {
+      const int z = e / ny, y = e - (e / ny) * ny;
+      pe[k] = z * nyp + y;
+      go[k] = (int)(z * xy) + y;
+      const long long gi = (long long)z * xy + (long long)x * ny + y;
+      if (iter_form) {
+        Zr[k] = a.S[gi];
+        const float2 Sp = a.Sprev[gi];
+        const float2 Zo = cadd(a.Lbuf[gi], Sp);
+        if (a.W) bufA[pe[k]] = csub(a.X[gi], Sp);
+        Dz[k] = csub(Zr[k], Zo);
+        z2 += cabs2(Zo);
+      } else if (MODE != kDcAdjoint) {
+        float2 v = a.L[gi];
+        if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
+        Zr[k] = v;
+      }
+    }
+  }
   if (iter_form && a.W) {
     // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns,
     // one pixel column and 4 output slices per task, into bufB.
     for (int i = tid; i < nz * nz; i += kThreads) wsh[i] = a.W[i];
-    for (int e = tid; e < plane; e += kThreads) {
-      const int z = e / ny, y = e - (e / ny) * ny;
-      const long long gi = (long long)z * xy + (long long)x * ny + y;
-      bufA[z * nyp + y] = csub(a.X[gi], a.Sprev[gi]);
-    }
     __syncthreads();
     const int nzb = (nz + 3) / 4;
     for (int task = tid; task < ny * nzb; task += kThreads) {
@@ -110,30 +135,17 @@ __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) 
     }
     __syncthreads();
   }
+  if (iter_form) {
 #pragma unroll
-  for (int k = 0; k < EPT; ++k) {
-    const int e = tid + k * kThreads;
-    acc[k] = make_float2(0.f, 0.f);
-    Zr[k] = make_float2(0.f, 0.f);
-    pe[k] = -1;
-    go[k] = 0;
-    if (e < plane) {
+    for (int k = 0; k < EPT; ++k) {
+      if (pe[k] < 0) continue;
+      const int e = tid + k * kThreads;
       const int z = e / ny, y = e - (e / ny) * ny;
-      pe[k] = z * nyp + y;
-      go[k] = (int)(z * xy) + y;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
-      if (iter_form) {
-        const float2 Lk = a.W ? bufB[z * nyp + y] : a.Lpre[gi];
-        Zr[k] = cadd(Lk, a.S[gi]);
-        const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
-        a.Lbuf[gi] = Lk;
-        dz2 += cabs2(csub(Zr[k], Zo));
-        z2 += cabs2(Zo);
-      } else if (MODE != kDcAdjoint) {
-        float2 v = a.L[gi];
-        if (MODE == kDcUpdate && a.S) v = cadd(v, a.S[gi]);
-        Zr[k] = v;
-      }
+      const float2 Lk = a.W ? bufB[pe[k]] : a.Lpre[gi];
+      Zr[k] = cadd(Lk, Zr[k]);
+      a.Lbuf[gi] = Lk;
+      dz2 += cabs2(cadd(Lk, Dz[k]));
     }
   }
   if (iter_form && a.W) __syncthreads();   // bufA and bufB are the FFT buffers of the coil loop

@@ -173,13 +173,30 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
     // Casorati matrix (the x-plane holds every slice of its pixels), or the precomputed L_k.
     float2* Mp = base;            // group 0's first buffer: M_{k-1} as [z][NYP]
     float2* Lsh = base + PLANEP;  // group 0's second buffer: L_k as [z][NYP]
-    if (a.W) {
-      for (int i = tid; i < NZ * NZ; i += NTH) wsh[i] = a.W[i];
-      for (int e = tid; e < PLANE; e += NTH) {
+    // Every per-element global load is issued here, before the product, so that their
+    // latencies overlap: S_k for each group; in group 0 also X_{k-1}, S_{k-1} and L_{k-1},
+    // giving M_{k-1} (into shared memory) and S_k - Z_{k-1} (kept for the change statistic).
+    float2 Dz[EPT];
+#pragma unroll
+    for (int k = 0; k < EPT; ++k) {
+      const int e = gtid + k * NT;
+      Zr[k] = Dz[k] = make_float2(0.f, 0.f);
+      acc[k] = make_float2(0.f, 0.f);
+      if (PLANE % NT == 0 || e < PLANE) {
         const int z = e / NY, y = e % NY;
         const long long gi = (long long)z * xy + (long long)x * NY + y;
-        Mp[z * NYP + y] = csub(a.X[gi], a.Sprev[gi]);
+        Zr[k] = a.S[gi];
+        if (grp == 0) {
+          const float2 Sp = a.Sprev[gi];
+          const float2 Zo = cadd(a.Lbuf[gi], Sp);
+          if (a.W) Mp[z * NYP + y] = csub(a.X[gi], Sp);
+          Dz[k] = csub(Zr[k], Zo);
+          z2 += cabs2(Zo);
+        }
       }
+    }
+    if (a.W) {
+      for (int i = tid; i < NZ * NZ; i += NTH) wsh[i] = a.W[i];
       __syncthreads();
       // one pixel column y and 8 output slices per task: M[i][y] read once per 8 products,
       // W rows broadcast across the warp
@@ -206,18 +223,14 @@ __global__ void __launch_bounds__(NCG* NT, 1) k_dc_fixed(const DcArgs a) {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int e = gtid + k * NT;
-      acc[k] = make_float2(0.f, 0.f);
-      Zr[k] = make_float2(0.f, 0.f);
       if (PLANE % NT == 0 || e < PLANE) {
         const int z = e / NY, y = e % NY;
         const long long gi = (long long)z * xy + (long long)x * NY + y;
         const float2 Lk = a.W ? Lsh[z * NYP + y] : a.Lpre[gi];
-        Zr[k] = cadd(Lk, a.S[gi]);
+        Zr[k] = cadd(Lk, Zr[k]);
         if (grp == 0) {
-          const float2 Zo = cadd(a.Lbuf[gi], a.Sprev[gi]);
           a.Lbuf[gi] = Lk;
-          dz2 += cabs2(csub(Zr[k], Zo));
-          z2 += cabs2(Zo);
+          dz2 += cabs2(cadd(Lk, Dz[k]));
         }
       }
     }
