@@ -64,6 +64,20 @@ struct Cx<double> {
   using T4 = double4_16a;
 };
 
+// Approximate reciprocal square root and reciprocal with subnormals flushed to zero (PTX
+// rsqrt.approx.ftz / rcp.approx.ftz): the rotation parameters need neither the subnormal
+// range nor the extra instructions that preserve it.
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rcp_ftz(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // Rotation of a pair (p, q): J = [[c, se], [-conj(se), c]] with se = s a_pq/|a_pq| and
 // t = tan(theta) from tau = (a_qq - a_pp)/(2|a_pq|), t = sign(tau)/(|tau| + sqrt(1 + tau^2))
 // (the smaller root). Packed as {c, se.x, se.y, t|a_pq|}; t|a_pq| = 0 means no rotation.
@@ -84,35 +98,35 @@ __device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T
   r.z = R(0);
   r.w = R(0);
   *relmax = R(0);
-  if (g2 > lim * lim) {
-    if constexpr (sizeof(R) == 4) {
-      // approximate intrinsics: c and s are derived from one t, so c^2 + |s|^2 = 1 to
-      // float32 precision whatever the rounding of t; a slightly inexact t only leaves a
-      // residue in a_pq that the next sweep removes
-      const float ig = rsqrtf(g2);
-      const float g = g2 * ig;
-      const float tau = (aqq - app) * 0.5f * ig;
-      const float h = fmaf(tau, tau, 1.0f);
-      const float t = copysignf(1.0f, tau) * __fdividef(1.0f, fabsf(tau) + h * rsqrtf(h));
-      const float c = rsqrtf(fmaf(t, t, 1.0f));
-      const float sg = t * c * ig;
-      r.x = c;
-      r.y = sg * apq.x;
-      r.z = sg * apq.y;
-      r.w = t * g;
-      *relmax = g;
-    } else {
-      const R g = sqrt(g2);
-      const R tau = (aqq - app) / (R(2) * g);
-      const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-      const R c = R(1) / sqrt(R(1) + t * t);
-      const R sg = t * c / g;
-      r.x = c;
-      r.y = sg * apq.x;
-      r.z = sg * apq.y;
-      r.w = t * g;
-      *relmax = g;
-    }
+  if constexpr (sizeof(R) == 4) {
+    // float32: computed for every pair and selected at the end (no divergent branch in the
+    // Jacobi step); approximate intrinsics: c and s are derived from one t, so
+    // c^2 + |s|^2 = 1 to float32 precision whatever the rounding of t; a slightly inexact t
+    // only leaves a residue in a_pq that the next sweep removes
+    const bool rot = g2 > lim * lim;
+    const float ig = rsqrt_ftz(rot ? g2 : 1.0f);   // g2 itself whenever the pair rotates
+    const float g = g2 * ig;
+    const float tau = (aqq - app) * 0.5f * ig;
+    const float h = fmaf(tau, tau, 1.0f);
+    const float t = copysignf(1.0f, tau) * rcp_ftz(fabsf(tau) + h * rsqrt_ftz(h));
+    const float c = rsqrt_ftz(fmaf(t, t, 1.0f));
+    const float sg = t * c * ig;
+    r.x = rot ? c : R(1);
+    r.y = rot ? sg * apq.x : R(0);
+    r.z = rot ? sg * apq.y : R(0);
+    r.w = rot ? t * g : R(0);
+    *relmax = rot ? g : R(0);
+  } else if (g2 > lim * lim) {
+    const R g = sqrt(g2);
+    const R tau = (aqq - app) / (R(2) * g);
+    const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
+    const R c = R(1) / sqrt(R(1) + t * t);
+    const R sg = t * c / g;
+    r.x = c;
+    r.y = sg * apq.x;
+    r.z = sg * apq.y;
+    r.w = t * g;
+    *relmax = g;
   }
   return r;
 }
@@ -138,7 +152,8 @@ __device__ __forceinline__ int next_pos(int p, int np) {
 // order). Each thread keeps one task over all steps, since the tasks address positions:
 // either a block (k1 <= k2) of the 2 x 2 blocks of A, which it rotates on both sides with
 // the rotations of pairs k1 and k2 and writes (with its mirror) at the moved positions, or
-// two rows of V at pair k2. In float32 every thread computes the rotations it needs itself
+// two rows of V at pair k2. The three kinds of task (off-diagonal blocks, diagonal blocks,
+// V rows) start on warp boundaries, so that no warp splits between their code paths. In float32 every thread computes the rotations it needs itself
 // from the diagonal blocks, so one barrier per step suffices; in float64 (a small fraction of
 // the float32 issue rate, with square root and division in software) the nh rotations are
 // computed once per step into `rots` behind a second barrier. Returns the sweeps done.
@@ -150,18 +165,22 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
   using C4 = typename Cx<R>::T4;
   const int np = n + (n & 1);
   const int nh = np >> 1;
-  const int nblk = nh * (nh + 1) / 2;
-  const int vbase = ((nblk + 31) >> 5) << 5;   // V tasks start on a warp boundary
+  const int noff = nh * (nh - 1) / 2;           // off-diagonal blocks k1 < k2 from thread 0
+  const int dbase = ((noff + 31) >> 5) << 5;      // diagonal blocks
+  const int vbase = ((dbase + nh + 31) >> 5) << 5;   // V row pairs (at most 416 threads: n <= 32)
   const int tid = threadIdx.x;
   int role = 0, k1 = 0, k2 = 0, r0 = 0;
-  if (tid < nblk) {
+  if (tid < noff) {
     role = 1;
     int t = tid;
-    while (t >= nh - k1) {
-      t -= nh - k1;
+    while (t >= nh - 1 - k1) {
+      t -= nh - 1 - k1;
       ++k1;
     }
-    k2 = k1 + t;
+    k2 = k1 + 1 + t;
+  } else if (tid >= dbase && tid < dbase + nh) {
+    role = 1;
+    k1 = k2 = tid - dbase;
   } else if (tid >= vbase && tid < vbase + nh * nh) {
     role = 2;
     const int t = tid - vbase;
@@ -266,9 +285,9 @@ struct alignas(16) EigShared {
   float2 V1[kMaxNc * kLd];   // second eigenvector buffer of the Jacobi permutation
   float f[kMaxNc];         // sigma''_i / sigma_i
   double lam[kMaxNc];      // eigenvalues
+  float lamf[kMaxNc];      // eigenvalues as float32 (float32 path)
+  float sprevf[kMaxNc];    // sigma_prev as float32
   int flags[4];
-  float red[4][32];
-  float4 red4[32];
   unsigned char tri[2][kMaxNc * (kMaxNc + 1) / 2];   // (i, j) of upper-triangle entry e
   double sprev[kMaxNc];    // sigma_prev
   // control scalars read once at entry
@@ -278,30 +297,6 @@ struct alignas(16) EigShared {
   int lambdas_set, rank_prev, sweeps_prev, has_sigma, v_valid;
 };
 
-
-// Sum four per-thread floats over the block in a fixed order; valid in every thread.
-__device__ __forceinline__ float4 block_sum4(float4 v, float4* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    v.x += __shfl_xor_sync(0xffffffffu, v.x, o);
-    v.y += __shfl_xor_sync(0xffffffffu, v.y, o);
-    v.z += __shfl_xor_sync(0xffffffffu, v.z, o);
-    v.w += __shfl_xor_sync(0xffffffffu, v.w, o);
-  }
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
-  const int nw = blockDim.x >> 5;
-  for (int i = 0; i < nw; ++i) {
-    const float4 q = red[i];
-    r.x += q.x;
-    r.y += q.y;
-    r.z += q.z;
-    r.w += q.w;
-  }
-  return r;
-}
 
 // One chunk sum of a Gram entry over the partials: task = part * nn + e sums partials
 // part, part + ksub, part + 2 ksub, ... of entry e, sixteen loads in flight at a time.
@@ -360,15 +355,20 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     case 8: sh.v_valid = a.persist->v_valid; break;
     default: break;
   }
-  if (tid >= 32 && tid < 32 + n) sh.sprev[tid - 32] = a.sigma_prev[tid - 32];
+  if (tid >= 32 && tid < 32 + n) {
+    const double v = a.sigma_prev[tid - 32];
+    sh.sprev[tid - 32] = v;
+    sh.sprevf[tid - 32] = (float)v;
+  }
   if (!a.finalize) {
     const float2* vsrc = a.Vin ? a.Vin : a.V;
     for (int e = tid; e < nn; e += kEigThreads) sh.V[(e / n) * kLd + e % n] = vsrc[e];
   }
   // statistics of iteration iter-1: the last warp
+  const bool stats_on = a.iter > 1 && a.part != 2;
   const int sw = (kEigThreads >> 5) - 1;
   float4 st4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if ((tid >> 5) == sw && a.iter > 1 && a.part != 2) {
+  if ((tid >> 5) == sw && stats_on) {
     // x: ||E Z - d||^2, z: ||Z_k - Z_{k-1}||^2, w: ||Z_{k-1}||^2 (data consistency);
     // y: l1 off the prior support (sparse step)
     const int lane = tid & 31;
@@ -400,7 +400,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   if (sh.flags[2]) return;
 
   // 1. statistics record and the stopping rule (the second part of the float64 mode has done it)
-  if (a.iter > 1 && a.part != 2 && (tid >> 5) == sw) {
+  if (stats_on && (tid >> 5) == sw) {
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       st4.x += __shfl_xor_sync(0xffffffffu, st4.x, o);
@@ -412,14 +412,13 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       const float r2 = st4.x, l1 = st4.y;
       const float rel = sqrtf(st4.z / fmaxf(st4.w, 1e-30f));
       const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
-      const bool stop = nonfinite || (tol_on && rel < (float)a.tol);
+      const bool stop = nonfinite || (tol_on && rel < a.tol_f);
       const double nuc = sh.nuc_prev;
       IterRec& rec = a.hist[a.iter - 2];
       rec.resid2 = r2;
       rec.nuclear = nuc;
       rec.l1 = l1;
-      rec.objective = 0.5 * (double)r2 + (double)sh.lamL * nuc + (double)sh.lamS * (double)l1;
-      rec.rel_change = (double)rel;
+      rec.rel_change = rel;
       rec.rank = sh.rank_prev;
       rec.sweeps = sh.sweeps_prev;
       ctrl->iters_done = a.iter - 1;
@@ -429,7 +428,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
   }
   if (a.finalize) return;
-  if (tol_on && a.iter > 1 && a.part != 2) {
+  if (tol_on && stats_on) {
     __syncthreads();
     if (sh.flags[3]) return;
   }
@@ -520,7 +519,10 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       if (tid == 32) ctrl->sweeps_cur = sweeps;
       return;
     }
-    for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = (double)Af[i * kLd + i].x;
+    for (int i = tid; i < n; i += kEigThreads) {
+      sh.lam[i] = (double)Af[i * kLd + i].x;
+      sh.lamf[i] = Af[i * kLd + i].x;
+    }
   } else {
     // float64 mode, second part: the Rayleigh-Ritz eigenvalues and refined eigenvectors
     // (V was loaded with the warm start above)
@@ -566,15 +568,20 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
         sh.f[i] = s > 0.0 ? (float)(s2d / s) : 0.f;
       }
     } else {
-      const float li = act ? (float)sh.lam[i] : -3.0e38f;
+      // float32: every lane reads all eigenvalues from shared memory (broadcast loads in
+      // flight together) for its rank and the largest eigenvalue; selects instead of
+      // branches; float32 copies of sigma_prev, lambda_p and tau
+      const float li = act ? sh.lamf[i] : -3.0e38f;
+      float lmax = -3.0e38f;
+#pragma unroll 8
       for (int j = 0; j < n; ++j) {
-        const float lj = __shfl_sync(full, li, j);
-        r += (lj > li) || (lj == li && j < i);
+        const float lj = sh.lamf[j];
+        r += (int)(lj > li) | ((int)(lj == li) & (int)(j < i));
+        lmax = fmaxf(lmax, lj);
       }
+      // sqrt is monotone and correctly rounded: max_i sqrt(l_i) = sqrt(max_i l_i)
       const float s = act ? sqrtf(fmaxf(li, 0.f)) : 0.f;
-      float sig1 = s;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) sig1 = fmaxf(sig1, __shfl_xor_sync(full, sig1, o));
+      const float sig1 = sqrtf(fmaxf(lmax, 0.f));
       if (a.iter == 1 && !sh.lambdas_set) {
         sh.lamL = (float)(a.lambda_L_rel * (double)sig1);
         sh.lamS = (float)(a.lambda_S_rel * (double)sh.haar_max);
@@ -586,21 +593,26 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
         }
       }
       __syncwarp();
-      if (act) {
-        const float s1 = fmaxf(s - sh.lamL, 0.f);
-        float s2 = sh.has_sigma ? s1 - (float)a.lambda_p * (s1 - (float)sh.sprev[r]) : s1;
-        if (s <= (float)a.rank_tau * sig1) s2 = 0.f;
-        sh.f[i] = s > 0.f ? s2 / s : 0.f;
-        s2d = (double)s2;
-      }
+      const float s1 = fmaxf(s - sh.lamL, 0.f);
+      const float sp = sh.sprevf[act ? r : 0];
+      float s2 = sh.has_sigma ? s1 - a.lambda_p_f * (s1 - sp) : s1;
+      s2 = (s <= a.rank_tau_f * sig1 || !act) ? 0.f : s2;
+      const float fi = s > 0.f ? s2 / s : 0.f;
+      if (act) sh.f[i] = fi;
+      s2d = (double)s2;
     }
     if (act) a.sigma_out[r] = s2d;   // sigma'' in rank order
-    double nuc = s2d;
-    int rk = s2d > 0.0;
+    const int rk = __popc(__ballot_sync(full, s2d > 0.0));
+    double nuc;
+    if (a.eig_fp64) {
+      nuc = s2d;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      nuc += __shfl_xor_sync(full, nuc, o);
-      rk += __shfl_xor_sync(full, rk, o);
+      for (int o = 16; o > 0; o >>= 1) nuc += __shfl_xor_sync(full, nuc, o);
+    } else {
+      float nf = (float)s2d;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) nf += __shfl_xor_sync(full, nf, o);
+      nuc = (double)nf;
     }
     if (i == 0) {
       ctrl->nuclear_cur = nuc;

@@ -391,6 +391,9 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize, int i) {
   e.lambda_p = P->p.lambda_p;
   e.rank_tau = P->p.rank_tau;
   e.tol = P->p.tol;
+  e.lambda_p_f = (float)P->p.lambda_p;
+  e.rank_tau_f = (float)P->p.rank_tau;
+  e.tol_f = (float)P->p.tol;
   e.iter = iter;
   e.finalize = finalize;
   e.eig_fp64 = P->p.eig_precision == LPS_EIG_FP64;
@@ -565,7 +568,7 @@ int read_stats(lps_plan* P, lps_stats* s) {
     s->resid_norm2 = r.resid2;
     s->nuclear = r.nuclear;
     s->l1_off_support = r.l1;
-    s->objective = r.objective;
+    s->objective = iter_objective(r, c.lambda_L, c.lambda_S);
     s->rel_change = r.rel_change;
   }
   // support count from the last low-rank/sparse partials
@@ -976,7 +979,7 @@ int lps_get_history(lps_plan* P, lps_iter_record* out, int max, int* count) {
     out[i].resid_norm2 = r[i].resid2;
     out[i].nuclear = r[i].nuclear;
     out[i].l1_off_support = r[i].l1;
-    out[i].objective = r[i].objective;
+    out[i].objective = iter_objective(r[i], P->h_ctrl->lambda_L, P->h_ctrl->lambda_S);
     out[i].rel_change = r[i].rel_change;
     out[i].rank = r[i].rank;
     out[i].eig_sweeps = r[i].sweeps;

@@ -48,10 +48,18 @@ struct DevCtrl {
   double nuclear_cur;
 };
 
+// Per-iteration record as the eigen kernel writes it (no float64 arithmetic on the device:
+// the host widens the float32 fields and forms the objective from them and the lambdas).
 struct IterRec {
-  double resid2, nuclear, l1, objective, rel_change;
+  double nuclear;
+  float resid2, l1, rel_change;
   int rank, sweeps;
 };
+
+// objective of Sec. 3: ||E(L+S) - d||^2 / 2 + lambda_L ||L||_* + lambda_S ||T S||_1 (off the prior support)
+inline double iter_objective(const IterRec& r, float lambda_L, float lambda_S) {
+  return 0.5 * (double)r.resid2 + (double)lambda_L * r.nuclear + (double)lambda_S * (double)r.l1;
+}
 
 struct Geom {
   int nx, ny, nz, ncoil;
@@ -143,6 +151,7 @@ struct EigArgs {
   DevPersist* persist;      // v_valid is set once eigenvectors exist
   DevCtrl* ctrl;
   double lambda_L_rel, lambda_S_rel, lambda_p, rank_tau, tol;
+  float lambda_p_f, rank_tau_f, tol_f;   // the same three rounded to float32 (float32 path)
   int iter;                 // iteration k whose SVT this launch computes (1-based)
   int finalize;             // 1: only record the stats of iteration `iter`-1
   int eig_fp64;
