@@ -87,7 +87,7 @@ __device__ __forceinline__ float rcp_ftz(float x) {
 // rotations of pairs of near-zero eigenvalues that only exchange rounding noise.
 template <typename R>
 __device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T* A, int p, int q, R eps,
-                                                         R floor_, R* relmax) {
+                                                         R floor_) {
   const R app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
   const auto apq = A[p * kLd + q];
   const R g2 = apq.x * apq.x + apq.y * apq.y;
@@ -97,25 +97,24 @@ __device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T
   r.y = R(0);
   r.z = R(0);
   r.w = R(0);
-  *relmax = R(0);
   if constexpr (sizeof(R) == 4) {
     // float32: computed for every pair and selected at the end (no divergent branch in the
-    // Jacobi step); approximate intrinsics: c and s are derived from one t, so
-    // c^2 + |s|^2 = 1 to float32 precision whatever the rounding of t; a slightly inexact t
-    // only leaves a residue in a_pq that the next sweep removes
+    // Jacobi step), with the same t written as t = sign(d) 2|a_pq| / (|d| + sqrt(d^2 + 4|a_pq|^2)),
+    // d = a_qq - a_pp, through u = t/|a_pq|: c = 1/sqrt(1 + u^2 |a_pq|^2), s e^{i arg a_pq} =
+    // c u a_pq, t|a_pq| = u |a_pq|^2 (three dependent approximate intrinsics). c and s derive
+    // from one u, so c^2 + |s|^2 = 1 to float32 precision whatever the rounding of u; a slightly
+    // inexact u only leaves a residue in a_pq that the next sweep removes.
     const bool rot = g2 > lim * lim;
-    const float ig = rsqrt_ftz(rot ? g2 : 1.0f);   // g2 itself whenever the pair rotates
-    const float g = g2 * ig;
-    const float tau = (aqq - app) * 0.5f * ig;
-    const float h = fmaf(tau, tau, 1.0f);
-    const float t = copysignf(1.0f, tau) * rcp_ftz(fabsf(tau) + h * rsqrt_ftz(h));
-    const float c = rsqrt_ftz(fmaf(t, t, 1.0f));
-    const float sg = t * c * ig;
+    const float d = aqq - app;
+    const float q2 = fmaf(4.0f, g2, d * d);
+    const float rq = rsqrt_ftz(rot ? q2 : 1.0f);   // q2 itself whenever the pair rotates
+    const float u = copysignf(2.0f, d) * rcp_ftz(fmaf(q2, rq, fabsf(d)));
+    const float c = rsqrt_ftz(fmaf(u * u, g2, 1.0f));
+    const float cu = c * u;
     r.x = rot ? c : R(1);
-    r.y = rot ? sg * apq.x : R(0);
-    r.z = rot ? sg * apq.y : R(0);
-    r.w = rot ? t * g : R(0);
-    *relmax = rot ? g : R(0);
+    r.y = rot ? cu * apq.x : R(0);
+    r.z = rot ? cu * apq.y : R(0);
+    r.w = rot ? u * g2 : R(0);
   } else if (g2 > lim * lim) {
     const R g = sqrt(g2);
     const R tau = (aqq - app) / (R(2) * g);
@@ -126,7 +125,6 @@ __device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T
     r.y = sg * apq.x;
     r.z = sg * apq.y;
     r.w = t * g;
-    *relmax = g;
   }
   return r;
 }
@@ -197,23 +195,21 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
     __syncthreads();
     for (int t = tid; t < n * n; t += blockDim.x) {
       const int p = t / n, q = t - (t / n) * n;
-      R rm;
-      if (p < q && rot_params<R>(A, p, q, eps, floor_, &rm).w != R(0)) flags[sweep & 1] = 1;
+      if (p < q && rot_params<R>(A, p, q, eps, floor_).w != R(0)) flags[sweep & 1] = 1;
     }
     __syncthreads();
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
-      R rm;
       constexpr bool kShared = sizeof(R) == 8;
       if constexpr (kShared) {
-        if (tid < nh) rots[tid] = rot_params<R>(A, 2 * tid, 2 * tid + 1, eps, floor_, &rm);
+        if (tid < nh) rots[tid] = rot_params<R>(A, 2 * tid, 2 * tid + 1, eps, floor_);
         __syncthreads();
       }
       auto rot_of = [&](int k) -> C4 {
         if constexpr (kShared) {
           return rots[k];
         } else {
-          return rot_params<R>(A, 2 * k, 2 * k + 1, eps, floor_, &rm);
+          return rot_params<R>(A, 2 * k, 2 * k + 1, eps, floor_);
         }
       };
       if (role == 1) {
