@@ -80,7 +80,7 @@ extern "C" {
 #define LPS_BF16_REFINE        2  /* bf16 operands (8-bit significand)                       */
 
 #define LPS_EIG_FP32           0  /* Gram eigendecomposition by float32 Jacobi             */
-#define LPS_EIG_FP64           1  /* float32 Jacobi polished by float64 Jacobi sweeps      */
+#define LPS_EIG_FP64           1  /* float32 Jacobi refined by a float64 Rayleigh-Ritz step */
 
 #define LPS_SUPPORT_THRESHOLD  0  /* T^(t) = {i : |c_i| > lambda_S} of the last iteration  */
 #define LPS_SUPPORT_NONZERO    1  /* T^(t) = supp of the shrunk coefficients (literal)     */
@@ -230,7 +230,7 @@ typedef struct lps_tune_result {
                               maps from global memory (half the shared memory)              */
   int radix_y[8];          /* FFT passes along y of the runtime-sized kernel (0-terminated) */
   int radix_z[8];          /* FFT passes along z                                            */
-  int lrs_tiles;           /* 8x8 tiles per CTA of the low-rank/sparse kernel               */
+  int lrs_tiles;           /* 8x8 tiles per CTA of the sparse-step kernel                   */
   int candidates;          /* configurations timed                                          */
   int cached;              /* 1: taken from the cache, nothing timed                        */
   double dc_us, lrs_us;    /* best measured time per launch (microseconds)                  */
@@ -304,8 +304,9 @@ int lps_server_result(lps_server* server, int session, void* out);
 /* Kernel timing of the per-frame graph. With profiling on, the graph records CUDA events
  * around every kernel it launches; lps_get_kernel_times synchronises the stream and returns,
  * for the last lps_reconstruct_frame, the launch count and summed device time of each class:
- * [0] data consistency (step 4), [1] low-rank/sparse update (steps 1-3 on the Casorati
- * matrix), [2] Gram eigendecomposition and singular-value steps, [3] step (0) kernels,
+ * [0] data consistency (step 4, with the reprojection L_k = (X - S) W of steps 1-2 in its
+ * prologue), [1] sparse step (3), [2] Gram eigendecomposition and singular-value steps
+ * (1)-(2), [3] step (0) kernels,
  * [4] Casorati Gram on the tensor cores and [5] reprojection on the tensor cores (precision
  * modes only). */
 #define LPS_KERNEL_CLASSES 6

@@ -5,6 +5,8 @@
 //   - NCG coil groups of NT threads run concurrently, each on its own coils, shared-memory
 //     buffers, TMA double buffer and named barrier; their coil sums are added in a fixed order
 //     at the end (deterministic);
+//   - in the iteration form the prologue completes steps (1)-(2) for the plane,
+//     L_k = (X_{k-1} - S_{k-1}) W, and the change statistic ||Z_k - Z_{k-1}||;
 //   - the plane Gram epilogue assigns one warp per (i <= j) column pair, lanes across y.
 #include "lps_internal.cuh"
 

@@ -271,7 +271,7 @@ cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long l
 
 int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : 32 / g.nc; }
 
-// Threads of one low-rank/sparse CTA: 8 per (tile, slice), rounded up to whole warps (the
+// Threads of one sparse-step CTA: 8 per (tile, slice), rounded up to whole warps (the
 // Haar shuffles need full warps; lanes beyond the tiles are inactive).
 int lrs_threads(const Geom& g) { return (8 * g.nc * lrs_tpc(g) + 31) / 32 * 32; }
 

@@ -571,7 +571,7 @@ int read_stats(lps_plan* P, lps_stats* s) {
     s->objective = iter_objective(r, c.lambda_L, c.lambda_S);
     s->rel_change = r.rel_change;
   }
-  // support count from the last low-rank/sparse partials
+  // support count from the last sparse-step partials
   const int nb = lrs_blocks(P->g);
   std::vector<float> part((size_t)nb * 2);
   CK(cudaMemcpy(part.data(), P->lrs_part, part.size() * sizeof(float), cudaMemcpyDeviceToHost));

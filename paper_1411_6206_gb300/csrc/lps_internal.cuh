@@ -11,7 +11,7 @@ namespace lps {
 
 constexpr int kThreads = 256;          // threads per CTA of the per-plane and per-tile kernels
 constexpr int kMaxPasses = 8;          // radix passes per transform length
-constexpr int kTile = 8;               // in-plane tile edge of the low-rank/sparse kernel
+constexpr int kTile = 8;               // in-plane tile edge of the sparse-step kernel
 constexpr int kMaxNc = 32;             // largest Casorati column count
 constexpr long long kSpinLimit = 1LL << 26;   // bounded waits: iterations before giving up
 
@@ -77,7 +77,7 @@ struct Geom {
   FftPlan py, pz, px;
   int dc_generic;           // 1: always the runtime-sized data-consistency kernel (autotuner)
   int dc_direct;            // runtime-sized kernel reads coil maps from global memory (no staging)
-  int lrs_tpc;              // 8x8 tiles per CTA of the low-rank/sparse kernel (0: 32 / nc)
+  int lrs_tpc;              // 8x8 tiles per CTA of the sparse-step kernel (0: 32 / nc)
 };
 
 // ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
@@ -142,7 +142,7 @@ struct EigArgs {
   int nparts;
   const float* dc_part;     // [nx][4]
   const float* lrs_part;    // [lrs_parts][2]
-  int lrs_parts;            // CTAs of the low-rank/sparse kernel
+  int lrs_parts;            // CTAs of the sparse-step kernel
   float2* W;                // [nc][nc]
   float2* V;                // [nc][nc] warm-start eigenvectors
   const double* sigma_prev;

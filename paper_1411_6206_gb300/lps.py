@@ -65,7 +65,7 @@ class IterRecord(C.Structure):
 class KernelTimes(C.Structure):
     _fields_ = [("launches", C.c_int * KERNEL_CLASSES), ("ms", C.c_double * KERNEL_CLASSES)]
 
-    CLASSES = ("data_consistency", "lowrank_sparse", "eig_svt", "init", "gram_tc", "reproj_tc")
+    CLASSES = ("data_consistency", "sparse_step", "eig_svt", "init", "gram_tc", "reproj_tc")
 
     def as_dict(self):
         return {n: {"launches": self.launches[i], "ms": self.ms[i]} for i, n in enumerate(self.CLASSES)}
