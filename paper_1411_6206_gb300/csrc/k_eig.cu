@@ -190,12 +190,14 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
   const int np2 = next_pos(p2, np), nq2 = next_pos(q2, np);
   int sweep = 0;
   for (;;) {
-    // converged when no off-diagonal entry exceeds its rotation threshold
+    // converged when no off-diagonal entry exceeds twice its rotation threshold (a sweep still
+    // rotates every pair above the threshold itself): the residual stays at the rounding level
+    // of the float32 Gram, and sweeps that would only move rounding noise are not started
     if (tid == 0) flags[sweep & 1] = 0;
     __syncthreads();
     for (int t = tid; t < n * n; t += blockDim.x) {
       const int p = t / n, q = t - (t / n) * n;
-      if (p < q && rot_params<R>(A, p, q, eps, floor_).w != R(0)) flags[sweep & 1] = 1;
+      if (p < q && rot_params<R>(A, p, q, R(2) * eps, R(2) * floor_).w != R(0)) flags[sweep & 1] = 1;
     }
     __syncthreads();
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
