@@ -71,6 +71,8 @@ SHAPES = [
     (8, 24, 32, 2, 1),       # same plane, six clusters
     (16, 128, 128, 8, 1),    # cardiac workload plane (compile-time specialised kernel)
     (32, 192, 192, 12, 1),   # precision workload plane (compile-time specialised kernel)
+    (8, 24, 32, 2, 0),       # compile-time plane 32 x 8, per-slice 2D encode
+    (16, 16, 128, 3, 0),     # compile-time plane 128 x 16, per-slice 2D encode
 ]
 
 
@@ -96,7 +98,7 @@ def test_forward_adjoint_match_oracle(L, nz, nx, ny, nc, fz):
     pl.close()
 
 
-@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES[:4] + SHAPES[-4:])
+@pytest.mark.parametrize("nz,nx,ny,nc,fz", SHAPES[:4] + SHAPES[-6:])
 def test_data_consistency_step(L, nz, nx, ny, nc, fz):
     case = make_case(nz, nx, ny, nc, seed=3, fft_z=fz)
     pl = plan_for(L, case, nz, nx, ny, nc, fft_z=fz)
