@@ -69,6 +69,12 @@ extern "C" {
 
 /* ---- options ---------------------------------------------------------------------- */
 #define LPS_LAYOUT_SLICES      0  /* Casorati columns = the nz slices of a volume (Sec. 2) */
+/* Casorati columns = the frames of a 2D + time segment (nx x ny images): nz counts the
+ * frames, mask row z holds frame z's ky lines and every frame is encoded by its own 2D DFT
+ * (fft_z must be 0; frames that are 3D volumes return LPS_ERR_UNSUPPORTED). Coil maps are
+ * given per frame ([c][frame][x][y]). With the recursion, the prior of a segment comes from
+ * the previous segment of the session. */
+#define LPS_LAYOUT_FRAMES      1
 
 #define LPS_FP32               0  /* every stage in float32 (Gram and reprojection on FMA) */
 /* Precision modes: the two dense contractions (Casorati Gram and low-rank reprojection) run
@@ -91,7 +97,7 @@ typedef struct lps_plan lps_plan;   /* opaque; owns its device workspace */
 
 typedef struct lps_params {
   int nx, ny, nz, ncoil;   /* volume size (nx: fully sampled readout axis) and coils       */
-  int layout;              /* LPS_LAYOUT_SLICES                                             */
+  int layout;              /* LPS_LAYOUT_SLICES | LPS_LAYOUT_FRAMES                         */
   int fft_z;               /* 1: 3D Fourier encode, (ky,kz) line mask; 0: 2D per slice     */
   int wavelet_levels;      /* Haar levels J, 1..3 (nx, ny multiples of 2^J)                */
   int max_iters;           /* iterations of Algorithm 1 per frame (1..4096)                */

@@ -151,8 +151,14 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->nx % 8 == 0 && p->ny % 8 == 0, "nx and ny must be multiples of 8");
   ARG(p->nx <= 1024 && p->ny <= 1024, "nx, ny <= 1024");
   ARG(p->ncoil >= 1 && p->ncoil <= 64, "ncoil must be in 1..64");
-  ARG(p->layout == LPS_LAYOUT_SLICES, "only LPS_LAYOUT_SLICES is implemented");
+  ARG(p->layout == LPS_LAYOUT_SLICES || p->layout == LPS_LAYOUT_FRAMES, "layout must be SLICES or FRAMES");
   ARG(p->fft_z == 0 || p->fft_z == 1, "fft_z must be 0 or 1");
+  if (p->layout == LPS_LAYOUT_FRAMES && p->fft_z != 0) {
+    // a column is one 2D frame with its own ky lines: the per-slice 2D encode; frames that are
+    // 3D volumes (a 3D encode per column) are not implemented
+    set_err("LPS_LAYOUT_FRAMES takes 2D frames (fft_z = 0)");
+    return LPS_ERR_UNSUPPORTED;
+  }
   ARG(p->wavelet_levels >= 1 && p->wavelet_levels <= 3, "wavelet_levels must be 1..3");
   ARG(p->max_iters >= 1 && p->max_iters <= 4096, "max_iters must be 1..4096");
   ARG(std::isfinite(p->lambda_L_rel) && p->lambda_L_rel >= 0, "lambda_L_rel must be finite, >= 0");

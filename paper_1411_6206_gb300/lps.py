@@ -27,6 +27,7 @@ ERR_ADMISSION = -6
 ERR_STATE = -7
 ERR_UNSUPPORTED = -8
 
+LAYOUT_SLICES, LAYOUT_FRAMES = 0, 1
 EIG_FP32, EIG_FP64 = 0, 1
 FP32, TF32_REFINE, BF16_REFINE = 0, 1, 2
 KERNEL_CLASSES = 6

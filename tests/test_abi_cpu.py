@@ -46,7 +46,7 @@ def test_params_defaults_and_status_strings(lps):
 
 @pytest.mark.parametrize("bad,code", [
     (dict(nx=12), -1), (dict(ny=0), -1), (dict(ncoil=0), -1), (dict(wavelet_levels=4), -1),
-    (dict(lambda_p=1.5), -1), (dict(layout=1), -1), (dict(precision=3), -1),
+    (dict(lambda_p=1.5), -1), (dict(layout=2), -1), (dict(layout=1), -8), (dict(precision=3), -1),
     (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1),
 ])
 def test_plan_create_rejects_bad_params(lps, bad, code):
@@ -64,6 +64,19 @@ def test_estimate_device_bytes(lps):
     N = 128 * 128 * 16
     assert 8 * N * 12 < b < 8 * N * 40
     assert lps.support_words(p) == N // 32
+
+
+def test_frames_layout_is_the_per_frame_2d_encode(lps):
+    """Layout "frames" (columns = frames of a 2D + time segment) takes the per-frame 2D encode:
+    accepted with fft_z = 0 and planned like the slice layout with the per-slice encode; the
+    header and the binding agree on the constants."""
+    hdr = open(os.path.join(ROOT, "include", "lps_api.h")).read()
+    assert re.search(r"#define LPS_LAYOUT_SLICES\s+0\b", hdr) and re.search(r"#define LPS_LAYOUT_FRAMES\s+1\b", hdr)
+    assert (lps.LAYOUT_SLICES, lps.LAYOUT_FRAMES) == (0, 1)
+    kw = dict(nx=64, ny=64, nz=12, ncoil=4, fft_z=0)
+    bf = lps.estimate_device_bytes(lps.params_init(layout=lps.LAYOUT_FRAMES, **kw))
+    bs = lps.estimate_device_bytes(lps.params_init(layout=lps.LAYOUT_SLICES, **kw))
+    assert bf == bs > 0
 
 
 @pytest.mark.parametrize("J", [1, 2, 3])

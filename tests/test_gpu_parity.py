@@ -207,6 +207,32 @@ def test_frame_end_to_end(L, nz, nx, ny, nc, iters):
     pl.close()
 
 
+def test_frames_layout_2d_time_segment_matches_oracle(L):
+    """Layout "frames": the Casorati columns are the T frames of a 2D + time segment (the
+    beating-heart family on one slice), each with its own ky lines and 2D encode and the same
+    coil maps. Equal bitwise to the slice layout with the per-slice encode, and within the
+    end-to-end bound of the oracle run on the same samples."""
+    from paper_1411_6206_gb300 import phantom as P
+    T, nx, ny, nc, iters = 8, 32, 32, 2, 20
+    w = P.Workload("segment", nx, ny, 1, nc, T, iters, 4.0, 11, phantom="heart")
+    x = P.phantom_sequence(w)[:, 0]                     # [T][nx][ny]
+    c1 = P.coil_maps(nx, ny, 1, nc, 29)[:, 0]           # one map per coil, the same in every frame
+    coils = c64(np.repeat(c1[:, None], T, axis=1))
+    mask = P.vd_mask(ny, T, int(round(0.3 * ny * T)), 4, 31, 0)
+    d = O.E(x, up(coils), mask, 0) + P.noise(nc, int(mask.sum()), nx, 1e-3, 37)
+    case = dict(coils=coils, mask=mask, d=c64(d), nlines=int(mask.sum()))
+    outs = []
+    for layout in (L.LAYOUT_FRAMES, L.LAYOUT_SLICES):
+        pl, st, recon, Lg, Sg, sup, sig = run_frame(L, case, T, nx, ny, nc, iters, fft_z=0, layout=layout)
+        assert pl.params.layout == layout and st.iters == iters
+        outs.append((recon, sig))
+        params = pl.params
+        pl.close()
+    assert np.array_equal(outs[0][0], outs[1][0]) and np.array_equal(outs[0][1], outs[1][1])
+    ref = O.priori_ls(up(case["d"]), up(coils), mask, oracle_params(params))
+    assert O.nrmse(outs[0][0], ref.recon) <= E2E_TOL
+
+
 @pytest.mark.parametrize("rule", [0, 1])
 def test_support_and_sigma_after_one_iteration(L, rule):
     """Support bits of one iteration from a common state differ only inside the tie band;
