@@ -51,19 +51,6 @@ __device__ __forceinline__ C scl_(C a, R s) { return mkc(a.x * s, a.y * s); }
 template <typename C>
 __device__ __forceinline__ C conj_(C a) { return mkc(a.x, -a.y); }
 
-template <typename R>
-struct Cx;
-template <>
-struct Cx<float> {
-  using T = float2;
-  using T4 = float4;
-};
-template <>
-struct Cx<double> {
-  using T = double2;
-  using T4 = double4_16a;
-};
-
 // Approximate reciprocal square root and reciprocal with subnormals flushed to zero (PTX
 // rsqrt.approx.ftz / rcp.approx.ftz): the rotation parameters need neither the subnormal
 // range nor the extra instructions that preserve it.
@@ -85,47 +72,29 @@ __device__ __forceinline__ float rcp_ftz(float x) {
 // rotation moves the eigenvalues by O(eps^2 a) and the vectors by O(eps), the rounding level
 // of the arithmetic; `floor` (about one unit in the last place of the trace) stops
 // rotations of pairs of near-zero eigenvalues that only exchange rounding noise.
-template <typename R>
-__device__ __forceinline__ typename Cx<R>::T4 rot_params(const typename Cx<R>::T* A, int p, int q, R eps,
-                                                         R floor_) {
-  const R app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
-  const auto apq = A[p * kLd + q];
-  const R g2 = apq.x * apq.x + apq.y * apq.y;
-  const R lim = fmax(eps * fmax(fabs(app), fabs(aqq)), floor_);
-  typename Cx<R>::T4 r;
-  r.x = R(1);
-  r.y = R(0);
-  r.z = R(0);
-  r.w = R(0);
-  if constexpr (sizeof(R) == 4) {
-    // float32: computed for every pair and selected at the end (no divergent branch in the
-    // Jacobi step), with the same t written as t = sign(d) 2|a_pq| / (|d| + sqrt(d^2 + 4|a_pq|^2)),
-    // d = a_qq - a_pp, through u = t/|a_pq|: c = 1/sqrt(1 + u^2 |a_pq|^2), s e^{i arg a_pq} =
-    // c u a_pq, t|a_pq| = u |a_pq|^2 (three dependent approximate intrinsics). c and s derive
-    // from one u, so c^2 + |s|^2 = 1 to float32 precision whatever the rounding of u; a slightly
-    // inexact u only leaves a residue in a_pq that the next sweep removes.
-    const bool rot = g2 > lim * lim;
-    const float d = aqq - app;
-    const float q2 = fmaf(4.0f, g2, d * d);
-    const float rq = rsqrt_ftz(rot ? q2 : 1.0f);   // q2 itself whenever the pair rotates
-    const float u = copysignf(2.0f, d) * rcp_ftz(fmaf(q2, rq, fabsf(d)));
-    const float c = rsqrt_ftz(fmaf(u * u, g2, 1.0f));
-    const float cu = c * u;
-    r.x = rot ? c : R(1);
-    r.y = rot ? cu * apq.x : R(0);
-    r.z = rot ? cu * apq.y : R(0);
-    r.w = rot ? u * g2 : R(0);
-  } else if (g2 > lim * lim) {
-    const R g = sqrt(g2);
-    const R tau = (aqq - app) / (R(2) * g);
-    const R t = (tau >= R(0) ? R(1) : R(-1)) / (fabs(tau) + sqrt(R(1) + tau * tau));
-    const R c = R(1) / sqrt(R(1) + t * t);
-    const R sg = t * c / g;
-    r.x = c;
-    r.y = sg * apq.x;
-    r.z = sg * apq.y;
-    r.w = t * g;
-  }
+__device__ __forceinline__ float4 rot_params(const float2* A, int p, int q, float eps, float floor_) {
+  const float app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
+  const float2 apq = A[p * kLd + q];
+  const float g2 = apq.x * apq.x + apq.y * apq.y;
+  const float lim = fmaxf(eps * fmaxf(fabsf(app), fabsf(aqq)), floor_);
+  // Computed for every pair and selected at the end (no divergent branch in the Jacobi
+  // step), with the same t written as t = sign(d) 2|a_pq| / (|d| + sqrt(d^2 + 4|a_pq|^2)),
+  // d = a_qq - a_pp, through u = t/|a_pq|: c = 1/sqrt(1 + u^2 |a_pq|^2), s e^{i arg a_pq} =
+  // c u a_pq, t|a_pq| = u |a_pq|^2 (three dependent approximate intrinsics). c and s derive
+  // from one u, so c^2 + |s|^2 = 1 to float32 precision whatever the rounding of u; a slightly
+  // inexact u only leaves a residue in a_pq that the next sweep removes.
+  float4 r;
+  const bool rot = g2 > lim * lim;
+  const float d = aqq - app;
+  const float q2 = fmaf(4.0f, g2, d * d);
+  const float rq = rsqrt_ftz(rot ? q2 : 1.0f);   // q2 itself whenever the pair rotates
+  const float u = copysignf(2.0f, d) * rcp_ftz(fmaf(q2, rq, fabsf(d)));
+  const float c = rsqrt_ftz(fmaf(u * u, g2, 1.0f));
+  const float cu = c * u;
+  r.x = rot ? c : 1.f;
+  r.y = rot ? cu * apq.x : 0.f;
+  r.z = rot ? cu * apq.y : 0.f;
+  r.w = rot ? u * g2 : 0.f;
   return r;
 }
 
@@ -151,16 +120,14 @@ __device__ __forceinline__ int next_pos(int p, int np) {
 // either a block (k1 <= k2) of the 2 x 2 blocks of A, which it rotates on both sides with
 // the rotations of pairs k1 and k2 and writes (with its mirror) at the moved positions, or
 // two rows of V at pair k2. The three kinds of task (off-diagonal blocks, diagonal blocks,
-// V rows) start on warp boundaries, so that no warp splits between their code paths. In float32 every thread computes the rotations it needs itself
-// from the diagonal blocks, so one barrier per step suffices; in float64 (a small fraction of
-// the float32 issue rate, with square root and division in software) the nh rotations are
-// computed once per step into `rots` behind a second barrier. Returns the sweeps done.
-template <typename R>
-__device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx<R>::T*& V,
-                      typename Cx<R>::T*& Vn, int n, R eps, R floor_, int max_sweeps, int* flags,
-                      typename Cx<R>::T4* rots) {
-  using C = typename Cx<R>::T;
-  using C4 = typename Cx<R>::T4;
+// V rows) start on warp boundaries, so that no warp splits between their code paths. Every
+// thread computes the rotations it needs itself from the diagonal blocks, so one barrier per
+// step suffices. Returns the sweeps done.
+__device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n, float eps, float floor_,
+                      int max_sweeps, int* flags) {
+  using C = float2;
+  using C4 = float4;
+  using R = float;
   const int np = n + (n & 1);
   const int nh = np >> 1;
   const int noff = nh * (nh - 1) / 2;           // off-diagonal blocks k1 < k2 from thread 0
@@ -197,23 +164,12 @@ __device__ int jacobi(typename Cx<R>::T*& A, typename Cx<R>::T*& An, typename Cx
     __syncthreads();
     for (int t = tid; t < n * n; t += blockDim.x) {
       const int p = t / n, q = t - (t / n) * n;
-      if (p < q && rot_params<R>(A, p, q, R(2) * eps, R(2) * floor_).w != R(0)) flags[sweep & 1] = 1;
+      if (p < q && rot_params(A, p, q, 2.f * eps, 2.f * floor_).w != 0.f) flags[sweep & 1] = 1;
     }
     __syncthreads();
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
-      constexpr bool kShared = sizeof(R) == 8;
-      if constexpr (kShared) {
-        if (tid < nh) rots[tid] = rot_params<R>(A, 2 * tid, 2 * tid + 1, eps, floor_);
-        __syncthreads();
-      }
-      auto rot_of = [&](int k) -> C4 {
-        if constexpr (kShared) {
-          return rots[k];
-        } else {
-          return rot_params<R>(A, 2 * k, 2 * k + 1, eps, floor_);
-        }
-      };
+      auto rot_of = [&](int k) -> C4 { return rot_params(A, 2 * k, 2 * k + 1, eps, floor_); };
       if (role == 1) {
         const C b00 = A[p1 * kLd + p2], b01 = A[p1 * kLd + q2];
         const C b10 = A[q1 * kLd + p2], b11 = A[q1 * kLd + q2];
@@ -496,7 +452,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     float2* Afn = sh.A1;
     float2* Vf = sh.V;
     float2* Vfn = sh.V1;
-    sweeps = jacobi<float>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags, nullptr);
+    sweeps = jacobi(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
     if (Vf != sh.V) {
       for (int e = tid; e < np * np; e += kEigThreads) {
         const int i = e / np, j = e - (e / np) * np;
