@@ -3,8 +3,9 @@
 // The singular values and right singular vectors of M = X - S (N_r x nc, N_r >> nc) are
 // those of its Gram matrix G = M^H M = V diag(sigma^2) V^H. One CTA:
 //   1. records the statistics of the previous iteration (residual, nuclear norm, l1 off the
-//      prior support, objective, relative change) and applies the stopping rule (Sec. 3:
-//      stop when the relative change of the solution falls below the tolerance);
+//      prior support, relative change; the host forms the objective from them) and applies
+//      the stopping rule (Sec. 3: stop when the relative change of the solution falls below
+//      the tolerance);
 //   2. sums the Gram partials of the data-consistency step in float32 (one or two
 //      interleaved chunk sums per entry, combined in a fixed order);
 //   3. diagonalises G by cyclic two-sided Jacobi rotations in round-robin order, starting
