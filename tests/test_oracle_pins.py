@@ -381,23 +381,171 @@ def test_recovery_improves_over_iterations():
 
 
 def test_sequence_passes_prior():
+    """Recursion of Sec. 3 (Fig. 2): frame t runs Algorithm 1 with the support and singular
+    values of frame t-1. With lambda_p = 1, step (2) sets sigma'' to the prior exactly, so
+    frame 2's singular values must be frame 1's; and on the prior support step (3) keeps the
+    coefficients unshrunk, so T(S) of frame 2 equals its c there and equals soft(c) elsewhere.
+    A recursion that dropped either prior (or passed frame 2's own) fails one of the two."""
     w = P.SMALL
     pr = P.problem(w, frames=2)
     datas = [O.E(pr["x"][t], pr["coils"], pr["masks"][t]) + pr["noise"][t] for t in range(2)]
-    p = O.Params(max_iters=5)
+    p = O.Params(max_iters=5, lambda_p=1.0, rank_tau=0.0)
     seq = O.sequence(datas, pr["coils"], pr["masks"], p)
+    assert len(seq) == 2
+    sup1 = seq[0].support
+    assert sup1.any() and not sup1.all()
+    # sigma: the singular values of L of frame 2 are frame 1's sigma'' (independent SVD)
+    s_L2 = np.linalg.svd(O.casorati(seq[1].L), compute_uv=False)
+    assert np.allclose(np.sort(s_L2)[::-1], np.sort(seq[0].sigma)[::-1], atol=1e-10 * seq[0].sigma.max())
+    # support: coefficients of S of frame 2 on frame 1's support are the unshrunk c
+    cS = O.T(seq[1].S, w_levels := p.wavelet_levels)
+    c2 = seq[1].c
+    assert np.abs(cS[sup1] - c2[sup1]).max() < 1e-12 * np.abs(c2).max()
+    off = ~sup1
+    lam = seq[1].lambda_S
+    assert np.allclose(np.abs(cS[off]), np.maximum(np.abs(c2[off]) - lam, 0.0), atol=1e-12 * np.abs(c2).max())
+    # the kept coefficients include some below the threshold (otherwise the test proves nothing)
+    assert (np.abs(c2[sup1]) < lam).any()
+    # frame 1 is plain L+S: the same call without a prior
     r1 = O.priori_ls(datas[0], pr["coils"], pr["masks"][0], p)
-    r2 = O.priori_ls(datas[1], pr["coils"], pr["masks"][1], p,
-                     O.Prior(support=r1.support, sigma=r1.sigma))
-    assert np.array_equal(seq[1].L, r2.L) and np.array_equal(seq[1].S, r2.S)
-    assert seq[0].support.any()
+    assert np.array_equal(seq[0].L, r1.L) and np.array_equal(seq[0].S, r1.S)
 
 
-def test_support_threshold_rule_and_ties():
-    c = np.array([[[1.0 + 0j, 0.5, 0.5000001, 0.0]]])
-    lam = 0.5
-    sup = np.abs(c) > lam
-    assert sup.tolist() == [[[True, False, True, False]]]
+def two_block_image(nz, nx, ny, s, v1, v2, blocks):
+    """Image whose Casorati matrix is s[0] u1 v1^H + s[1] u2 v2^H, with u_k the normalised
+    indicator of an aligned 8 x 8 in-plane block (so its J = 3 Haar transform is a single
+    coefficient of value 1 at the block's approximation position)."""
+    x = np.zeros((nz, nx, ny), complex)
+    for sk, vk, (bx, by) in zip(s, (v1, v2), blocks):
+        for z in range(nz):
+            x[z, bx:bx + 8, by:by + 8] += sk * np.conj(vk[z]) / 8.0
+    return x
+
+
+def test_initial_lambdas_closed_form():
+    """R2: lambda_L = rel_L sigma_1(X_0) and lambda_S = rel_S max|T(X_0)|, with X_0 = E^H d.
+    Full mask and one unit coil make E^H E = I, so X_0 is the image itself. The image is a
+    rank-2 Casorati matrix with singular values (5, 3) whose columns live on two 8 x 8 blocks,
+    so sigma_1 = 5 (not ||X||_F = sqrt(34), not the nuclear norm 8) and the Haar coefficients
+    are 5 conj(v1[z]) and 3 conj(v2[z]), so max|T X_0| = 5 * 0.8 = 4 (the image-domain
+    maximum is 0.5)."""
+    nz, nx, ny = 4, 16, 16
+    v1 = np.array([3, 4j, 0, 0]) / 5.0
+    v2 = np.array([0, 0, 1, -1j]) / np.sqrt(2)
+    x = two_block_image(nz, nx, ny, (5.0, 3.0), v1, v2, ((0, 0), (8, 8)))
+    coils = np.ones((1, nz, nx, ny), complex)
+    mask = np.ones((nz, ny), np.uint8)
+    d = O.E(x, coils, mask)
+    p = O.Params(lambda_L_rel=0.01, lambda_S_rel=0.005, max_iters=1)
+    r = O.priori_ls(d, coils, mask, p)
+    assert abs(r.lambda_L - 0.01 * 5.0) < 1e-12
+    assert abs(r.lambda_S - 0.005 * 4.0) < 1e-12
+    # the same through initial_lambdas directly
+    lL, lS = O.initial_lambdas(x, p)
+    assert abs(lL - 0.05) < 1e-12 and abs(lS - 0.02) < 1e-12
+
+
+def support_case(rule, keep=None):
+    """A state (X, S, L_prev) with X - L_prev = T^{-1}(c) for a designed coefficient array c:
+    one iteration from it computes c = T(X - L_prev) (step 3) and the output support from c.
+    Magnitudes relative to lambda_S = 1: 2.0 and 1.5 above it, 1.0 exactly at it, 0.6 below,
+    0 elsewhere."""
+    nz, nx, ny = 2, 16, 16
+    c = np.zeros((nz, nx, ny), complex)
+    pos = {"above2": (0, 3, 5), "above15": (1, 9, 2), "at": (0, 12, 12), "below": (1, 0, 0)}
+    c[pos["above2"]] = 2.0 * np.exp(0.3j)
+    c[pos["above15"]] = -1.5j
+    c[pos["at"]] = 1.0
+    c[pos["below"]] = 0.6 * np.exp(-2.0j)
+    D = O.Tinv(c, 3)
+    assert np.abs(O.T(D, 3) - c).max() < 1e-14
+    coils = np.ones((1, nz, nx, ny), complex)
+    mask = np.ones((nz, ny), np.uint8)
+    d = O.E(D, coils, mask)
+    p = O.Params(max_iters=1, lambda_p=0.0, rank_tau=0.0, support_rule=rule)
+    prior = None if keep is None else O.Prior(support=keep, sigma=None)
+    # lambda_S is set to the rounded magnitude of the "at" coefficient as step (3) computes it
+    # (c = T(X - L_prev) = T(D)), so that the tie is exact in floating point
+    lam = float(np.abs(O.T(D, 3)[pos["at"]]))
+    assert abs(lam - 1.0) < 1e-14
+    r = O.priori_ls(d, coils, mask, p, prior, iters=1,
+                    state=(D, np.zeros_like(D), np.zeros_like(D), 0.0, lam))
+    assert np.abs(r.c[pos["at"]]) == r.lambda_S
+    return r, pos
+
+
+def test_output_support_threshold_rule():
+    """R5: T^(t) = {i : |c_i| > lambda_S} for c of the last iteration; a tie at lambda_S is
+    off-support. A '>=' rule takes the tie; a support read from the shrunk c' (|c'| = |c| -
+    lambda_S off the prior) drops the 1.5 lambda_S coefficient."""
+    r, pos = support_case("threshold")
+    want = np.zeros(r.c.shape, bool)
+    want[pos["above2"]] = want[pos["above15"]] = True
+    assert np.array_equal(r.support, want)
+
+
+def test_output_support_nonzero_rule():
+    """The literal rule supp T(S^(t)): nonzero shrunk coefficients. Off the prior support that
+    is |c| > lambda_S; on it every nonzero c is kept unshrunk, so the 0.6 lambda_S coefficient
+    on the prior support is in the support under this rule and out of it under the threshold
+    rule."""
+    keep = np.zeros((2, 16, 16), bool)
+    r0, pos = support_case("nonzero")
+    keep[pos["below"]] = True
+    keep[pos["above2"]] = True
+    r, _ = support_case("nonzero", keep)
+    want = np.zeros(r.c.shape, bool)
+    want[pos["above2"]] = want[pos["above15"]] = want[pos["below"]] = True
+    assert np.array_equal(r.support, want)
+    want0 = np.zeros(r.c.shape, bool)
+    want0[pos["above2"]] = want0[pos["above15"]] = True
+    assert np.array_equal(r0.support, want0)
+    rt, _ = support_case("threshold", keep)
+    assert not rt.support[pos["below"]] and rt.support[pos["above2"]]
+
+
+def rel_change_case():
+    """Full mask, one unit coil (E^H E = I), lambda_S = 0, lambda_L = 2, no prior, no rank
+    guard, and an image whose Casorati matrix is U diag(5, 3, 1) V^H. Every iterate stays of
+    the form U diag(.) V^H (T is orthonormal and lambda_S = 0, so S_k = X_{k-1} - L_{k-1}), and
+    step (4) returns X_k = x. With (5, 3, 1) written s and svt(a) = max(a - 2, 0):
+      k = 1: L = svt(s) = (3, 1, 0), S = 0,               Z = (3, 1, 0)
+      k = 2: L = (3, 1, 0),          S = s - L_1 = (2, 2, 1), Z = (5, 3, 1)
+      k = 3: L = svt(s - S_2) = (1, 0, 0), S = (2, 2, 1),  Z = (3, 2, 1)
+      k = 4: L = (1, 0, 0),          S = s - L_3 = (4, 3, 1), Z = (5, 3, 1)
+      k = 5: L = svt(s - S_4) = 0,   S = (4, 3, 1),        Z = (4, 3, 1)
+    with Z_0 = L_0 + S_0 = x, so the relative changes ||Z_k - Z_{k-1}|| / ||Z_{k-1}|| are
+    3/sqrt(35), 3/sqrt(10), 1/sqrt(7), sqrt(5/14), 1/sqrt(35) and the nuclear norms 4, 4, 1, 1, 0."""
+    nz, nx, ny = 3, 16, 8
+    rng = np.random.default_rng(21)
+    U, _ = np.linalg.qr(rng.standard_normal((nx * ny, 3)) + 1j * rng.standard_normal((nx * ny, 3)))
+    V, _ = np.linalg.qr(rng.standard_normal((3, 3)) + 1j * rng.standard_normal((3, 3)))
+    M = (U * np.array([5.0, 3.0, 1.0])) @ V.conj().T
+    x = M.T.reshape(nz, nx, ny)
+    coils = np.ones((1, nz, nx, ny), complex)
+    mask = np.ones((nz, ny), np.uint8)
+    return x, coils, mask, O.E(x, coils, mask)
+
+
+@pytest.mark.parametrize("tol,stop_at", [(0.0, 5), (0.6, 1), (0.4, 3)])
+def test_rel_change_and_tol_stop_closed_form(tol, stop_at):
+    """Sec. 3 stopping rule: stop at the first iteration whose relative change of the
+    solution Z = L + S, ||Z_k - Z_{k-1}|| / ||Z_{k-1}||, is below the tolerance. The closed
+    forms fail if X is normed instead of Z (X_k = x for every k, so the change would be 0),
+    if Z_{k-1} is taken after the update, or if the new Z is the denominator."""
+    x, coils, mask, d = rel_change_case()
+    lam_rel = 2.0 / 5.0   # lambda_L = 2 (sigma_1 = 5)
+    p = O.Params(lambda_L_rel=lam_rel, lambda_S_rel=0.0, lambda_p=0.0, rank_tau=0.0, max_iters=5, tol=tol)
+    r = O.priori_ls(d, coils, mask, p)
+    assert abs(r.lambda_L - 2.0) < 1e-12 and r.lambda_S == 0.0
+    want = [3.0 / np.sqrt(35.0), 3.0 / np.sqrt(10.0), 1.0 / np.sqrt(7.0), np.sqrt(5.0 / 14.0), 1.0 / np.sqrt(35.0)]
+    got = [h["rel_change"] for h in r.history]
+    assert r.iters == stop_at and len(got) == stop_at
+    for g, w_ in zip(got, want):
+        assert abs(g - w_) < 1e-12
+    nuc = [4.0, 4.0, 1.0, 1.0, 0.0]
+    for h, n_ in zip(r.history, nuc):
+        assert abs(h["nuclear"] - n_) < 1e-12
 
 
 @pytest.mark.parametrize("fft_z", [1, 0])
