@@ -233,7 +233,9 @@ int lps_get_recon(lps_plan* plan, void* out);
 typedef struct lps_tune_result {
   int dc_variant;          /* 0: compile-time plane kernel, 1: runtime-sized kernel with the
                               coil planes staged in shared memory, 2: the same reading coil
-                              maps from global memory (half the shared memory)              */
+                              maps from global memory (half the shared memory); 128 x 16
+                              planes also: 3: register-transform kernel, 4 coil groups (the
+                              default there), 4: the same with 8 coil groups                */
   int radix_y[8];          /* FFT passes along y of the runtime-sized kernel (0-terminated) */
   int radix_z[8];          /* FFT passes along z                                            */
   int lrs_tiles;           /* 8x8 tiles per CTA of the sparse-step kernel                   */
@@ -245,7 +247,7 @@ int lps_autotune(lps_plan* plan, lps_tune_result* out);
 int lps_autotune_clear_cache(void);
 /* Install a launch shape (for instance one measured by lps_autotune in an earlier process):
  * dc_variant, radix_y / radix_z (variants 1 and 2; their products must be ny and nz) and
- * lrs_tiles are used, the other fields ignored. Synchronises the plan's stream; the frame
+ * lrs_tiles are used, the other fields ignored. Variants 3 and 4 need a 128 x 16 plane. Synchronises the plan's stream; the frame
  * graph is captured again at the next frame. */
 int lps_apply_tune(lps_plan* plan, const lps_tune_result* tune);
 
@@ -341,10 +343,14 @@ int lps_session_import(lps_plan* plan, const void* buf, size_t bytes);
  *   kdata  device complex64 [ncoil][nlines][nx], nlines = set entries of mask
  *   image  device complex64 [nz][nx][ny], written
  *   stream cudaStream_t (NULL = legacy default stream); the work is enqueued there.
+ * coils, kdata or image not in device memory, or a mask in device memory, is
+ * LPS_ERR_INVALID_ARG (checked on the host before anything is enqueued), as are a mask with no
+ * sampled entry and an nlines that differs from the mask's count; lps_last_error() says which.
  * The first call on a device looks up the array's device address once (with that device
  * current); make that first call before any stream capture. All calls share the array and
  * it keeps the last call's contents: calls whose work overlaps on the GPU (other streams or
- * other host threads) race on it and must be ordered by the caller. */
+ * other host threads) race on it and must be ordered by the caller; calls queued one after
+ * another on the same stream are ordered and need no synchronisation between them. */
 #define LPS_NOALLOC_SCRATCH_BYTES (16u << 20)
 int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z, const uint8_t* mask, const void* coils,
                         const void* kdata, int nlines, void* image, void* stream);

@@ -340,8 +340,14 @@ static cudaError_t launch_dc_s(const DcArgs& a, cudaStream_t st) {
 
 cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st);
 
-// Plane sizes with a compile-time specialisation go to k_dc_fixed; the rest to k_dc.
+// The update of a 128 x 16 plane goes to the register-transform kernel (k_dc_reg) unless the
+// plan selected another variant; other plane sizes with a compile-time specialisation go to
+// k_dc_fixed; the rest to k_dc.
 cudaError_t launch_dc(const DcArgs& a, int mode, cudaStream_t st) {
+  if (mode == kDcUpdate) {
+    const cudaError_t er = launch_dc_reg(a, st);
+    if (er != cudaErrorNotSupported) return er;
+  }
   const cudaError_t ef = launch_dc_fixed(a, mode, st);
   if (ef != cudaErrorNotSupported) return ef;
   if (dc_smem_bytes(a.g) > 227 * 1024) return cudaErrorInvalidValue;

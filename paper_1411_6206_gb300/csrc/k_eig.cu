@@ -25,18 +25,6 @@ namespace lps {
 constexpr int kEigThreads = 512;
 constexpr int kLd = kMaxNc + 1;   // leading dimension of the shared matrices
 
-#ifdef LPS_EIG_PHASE_TIMING
-__device__ unsigned long long g_eig_phase[4096][8];
-#define EIG_STAMP(k)                                                            \
-  do {                                                                          \
-    if (threadIdx.x == 0 && a.iter < 4096) g_eig_phase[a.iter][k] = clock64(); \
-  } while (0)
-#else
-#define EIG_STAMP(k) \
-  do {               \
-  } while (0)
-#endif
-
 __device__ __forceinline__ float2 mkc(float x, float y) { return make_float2(x, y); }
 __device__ __forceinline__ double2 mkc(double x, double y) { return make_double2(x, y); }
 template <typename C>
@@ -288,7 +276,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   const int np = n + (n & 1);
   pdl_trigger();
   pdl_wait();   // the Gram partials, statistics and control block come from earlier kernels
-  EIG_STAMP(0);
   const int nn = n * n;
   const int nut = n * (n + 1) / 2;
   const bool tol_on = a.tol > 0.0;
@@ -387,7 +374,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     __syncthreads();
     if (sh.flags[3]) return;
   }
-  EIG_STAMP(1);
 
   int sweeps = 0;
   if (a.part != 2) {
@@ -413,7 +399,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       sh.G[i * kLd + j] = s;
     }
     __syncthreads();
-    EIG_STAMP(2);
 
     // 3. Jacobi, warm-started from the previous eigenvectors
     if (warm) {
@@ -446,7 +431,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       if (i >= n || j >= n) sh.A0[i * kLd + j] = make_float2(0.f, 0.f);
     }
     __syncthreads();
-    EIG_STAMP(3);
     float trace = 0.f;
     for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
     float2* Af = sh.A0;
@@ -484,7 +468,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = a.lam64[i];
   }
   __syncthreads();
-  EIG_STAMP(4);
 
   // 4. singular values, thresholds, prior pull, rank guard: warp 0, lane i = eigenvalue i
   //    (n <= 32), ranks and sums by shuffles; in float64 after the float64 refinement, in
@@ -576,7 +559,6 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
   }
   __syncthreads();
-  EIG_STAMP(5);
   // 5. W = V diag(f) V^H and the eigenvectors for the next warm start
   for (int e = tid; e < nn; e += kEigThreads) {
     const int i = e / n, j = e - (e / n) * n;
@@ -589,14 +571,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     a.V[i * n + j] = sh.V[i * kLd + j];
   }
   if (tid == 0) a.persist->v_valid = 1;
-  EIG_STAMP(6);
 }
 
-#ifdef LPS_EIG_PHASE_TIMING
-extern "C" int lps_probe_eig_phases(unsigned long long* out, int n) {
-  return (int)cudaMemcpyFromSymbol(out, g_eig_phase, (size_t)n * 8 * sizeof(unsigned long long));
-}
-#endif
 
 cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(EigShared);

@@ -12,7 +12,10 @@
 // the process exits. All calls share it and it keeps the last call's contents, so calls
 // whose work overlaps on the GPU (different streams, or different host threads) race on it;
 // callers must order such calls. Everything a call reads from the array is written by that
-// call first.
+// call first. Calls queued back to back on one stream need no host synchronisation between
+// them: the tables are uploaded with cudaMemcpyAsync from pageable host memory, which returns
+// only once the source has been consumed, so the next call may rewrite the host staging
+// buffers, and its device writes are ordered after the previous call's kernels.
 #include "lps_api.h"
 #include "lps_internal.cuh"
 
@@ -22,6 +25,7 @@
 
 namespace lps {
 int make_geom(const lps_params* p, Geom* g);
+void set_err(const char* fmt, ...);
 }
 
 using namespace lps;
@@ -38,11 +42,35 @@ float2 g_tw[3 * 1024];                              // host staging of the twidd
 
 size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 
+// Memory kind of a pointer under unified addressing: 1 device (or managed), 0 host, -1 the
+// query failed. cudaPointerGetAttributes allocates nothing.
+int pointer_kind(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return -1;
+  }
+  return (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) ? 1 : 0;
+}
+
 }  // namespace
 
 extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z, const uint8_t* mask,
                                    const void* coils, const void* kdata, int nlines, void* image, void* stream) {
-  if (!mask || !coils || !kdata || !image) return LPS_ERR_INVALID_ARG;
+  if (!mask || !coils || !kdata || !image) {
+    set_err("lps_adjoint_noalloc: mask, coils, kdata and image must be non-NULL");
+    return LPS_ERR_INVALID_ARG;
+  }
+  // The kernels read coils and kdata and write image directly, and the host reads the mask:
+  // anything else is refused here, before any copy or launch.
+  if (pointer_kind(coils) != 1 || pointer_kind(kdata) != 1 || pointer_kind(image) != 1) {
+    set_err("lps_adjoint_noalloc: coils, kdata and image must be device memory");
+    return LPS_ERR_INVALID_ARG;
+  }
+  if (pointer_kind(mask) == 1) {
+    set_err("lps_adjoint_noalloc: mask must be host memory");
+    return LPS_ERR_INVALID_ARG;
+  }
   lps_params p;
   lps_params_init(&p);
   p.nx = nx;
@@ -55,7 +83,14 @@ extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z,
   if (rc) return rc;
   int m = 0;
   for (int i = 0; i < ny * nz; ++i) m += mask[i] != 0;
-  if (m == 0 || m != nlines) return LPS_ERR_INVALID_ARG;
+  if (m == 0) {
+    set_err("lps_adjoint_noalloc: mask has no sampled entry");
+    return LPS_ERR_INVALID_ARG;
+  }
+  if (m != nlines) {
+    set_err("lps_adjoint_noalloc: nlines %d != %d set mask entries", nlines, m);
+    return LPS_ERR_INVALID_ARG;
+  }
   const int mpad = (m + 1) & ~1;
   g.mpad = mpad;
   // scratch layout: [persist][tw_x][tw_y][tw_z][lines][hybrid samples]
@@ -66,16 +101,27 @@ extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z,
   const size_t o_lines = o_tz + align256((size_t)nz * sizeof(float2));
   const size_t o_hyb = o_lines + align256((size_t)ny * nz * sizeof(int));
   const size_t need = o_hyb + ((size_t)nx * ncoil * mpad + 4) * sizeof(float2);
-  if (need > LPS_NOALLOC_SCRATCH_BYTES) return LPS_ERR_UNSUPPORTED;   // beyond the fixed scratch
+  if (need > LPS_NOALLOC_SCRATCH_BYTES) {   // beyond the fixed scratch
+    set_err("lps_adjoint_noalloc: needs %zu bytes of scratch > LPS_NOALLOC_SCRATCH_BYTES (%u)", need,
+            (unsigned)LPS_NOALLOC_SCRATCH_BYTES);
+    return LPS_ERR_UNSUPPORTED;
+  }
 
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LPS_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    set_err("lps_adjoint_noalloc: no current device (or device index >= %d)", kMaxDevices);
+    return LPS_ERR_CUDA;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lock(g_mutex);
   if (!g_dev_scratch[dev]) {
     // once per device, with that device current: the device address of the array
     void* ptr = nullptr;
-    if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) return LPS_ERR_CUDA;
+    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess || !ptr) {
+      set_err("lps_adjoint_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return LPS_ERR_CUDA;
+    }
     g_dev_scratch[dev] = static_cast<unsigned char*>(ptr);
   }
   unsigned char* base = g_dev_scratch[dev];
@@ -109,8 +155,10 @@ extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z,
       cudaMemcpyAsync(tw_x, g_tw, (size_t)nx * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(tw_y, g_tw + nx, (size_t)ny * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemcpyAsync(tw_z, g_tw + nx + ny, (size_t)nz * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(lines, g_lines, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess)
+      cudaMemcpyAsync(lines, g_lines, (size_t)m * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_err("lps_adjoint_noalloc: table upload failed: %s", cudaGetErrorString(cudaGetLastError()));
     return LPS_ERR_CUDA;
+  }
 
   XfftArgs x{};
   x.g = g;
@@ -119,7 +167,11 @@ extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z,
   x.tw_x = tw_x;
   x.persist = persist;
   x.inverse = 1;
-  if (launch_xfft(x, st) != cudaSuccess) return LPS_ERR_CUDA;
+  cudaError_t le = launch_xfft(x, st);
+  if (le != cudaSuccess) {
+    set_err("lps_adjoint_noalloc: kx transform launch failed: %s", cudaGetErrorString(le));
+    return LPS_ERR_CUDA;
+  }
   DcArgs d{};
   d.g = g;
   d.coils = static_cast<const float2*>(coils);
@@ -129,6 +181,10 @@ extern "C" int lps_adjoint_noalloc(int nx, int ny, int nz, int ncoil, int fft_z,
   d.tw_z = tw_z;
   d.persist = persist;
   d.X = static_cast<float2*>(image);
-  if (launch_dc(d, kDcAdjoint, st) != cudaSuccess) return LPS_ERR_CUDA;
+  le = launch_dc(d, kDcAdjoint, st);
+  if (le != cudaSuccess) {
+    set_err("lps_adjoint_noalloc: adjoint launch failed: %s", cudaGetErrorString(le));
+    return LPS_ERR_CUDA;
+  }
   return LPS_OK;
 }

@@ -201,6 +201,9 @@ int validate(const lps_params* p, Geom* gout) {
     gd.dc_direct = 1;
     g.dc_direct = dc_smem_bytes(gd) <= 113 * 1024 ? 1 : 0;
   }
+  // 128 x 16 planes: the update runs on the register-transform kernel (four coil groups; their
+  // sums in shared memory when there are more than four coils)
+  if (g.ny == 128 && g.nz == 16) g.dc_reg_groups = g.ncoil > 4 ? 104 : 4;
   if (dc_ept(g) < 0 || dc_smem_bytes(g) > 227 * 1024) {
     set_err("x-plane of %d x %d does not fit one CTA", p->ny, p->nz);
     return LPS_ERR_UNSUPPORTED;
@@ -942,14 +945,6 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
   return LPS_OK;
 }
 
-#ifdef LPS_EIG_PHASE_TIMING
-// probe-only: launch the eigen kernel `reps` times back to back (iteration ids 4000 + r)
-int lps_probe_eig_repeat(lps_plan* P, int reps) {
-  for (int r = 0; r < reps; ++r) LK(launch_eig(eig_args(P, 4000 + r, 0, 0), P->st));
-  CK(cudaStreamSynchronize(P->st));
-  return LPS_OK;
-}
-#endif
 
 int lps_set_profiling(lps_plan* P, int on) {
   ARG(P != nullptr, "plan is NULL");

@@ -111,10 +111,20 @@ struct TuneEntry {
 std::mutex g_tune_mutex;
 std::map<TuneKey, TuneEntry> g_tune_cache;
 
+// dc_reg_groups value of a register-transform variant (3: four coil groups, their sums in
+// shared memory when there are more coils than groups; 4: eight groups), 0 otherwise.
+int reg_groups_of(int variant, int ncoil) {
+  if (variant == 3) return ncoil > 4 ? 104 : 4;
+  if (variant == 4) return 8;
+  return 0;
+}
+
 void install(lps_plan* P, const TuneEntry& t) {
-  P->g.dc_generic = t.res.dc_variant != 0;
+  const bool runtime = t.res.dc_variant == 1 || t.res.dc_variant == 2;
+  P->g.dc_generic = runtime;
   P->g.dc_direct = t.res.dc_variant == 2;
-  if (t.res.dc_variant) {
+  P->g.dc_reg_groups = reg_groups_of(t.res.dc_variant, P->g.ncoil);
+  if (runtime) {
     P->g.py = t.py;
     P->g.pz = t.pz;
   }
@@ -237,15 +247,22 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
     a.ctrl = ctrl;
     return time_launches(P, e0, e1, 5, [&] { return launch_dc(a, kDcUpdate, P->st); }, us);
   };
-  // data-consistency kernel
+  // data-consistency kernel: the compile-time plane kernel, the register-transform kernel in
+  // both group counts where the plane has one, then the runtime-sized candidates
   if (dc_has_fixed(g0)) {
-    Geom g = g0;
-    g.dc_generic = 0;
-    double us;
-    if ((rc = dc_time(g, &us))) goto done;
-    ++count;
-    best.res.dc_variant = 0;
-    best.res.dc_us = us;
+    for (int variant : {0, 3, 4}) {
+      Geom g = g0;
+      g.dc_generic = 0;
+      g.dc_reg_groups = reg_groups_of(variant, g.ncoil);
+      if (variant != 0 && !dc_reg_applies(g)) continue;
+      double us;
+      if ((rc = dc_time(g, &us))) goto done;
+      ++count;
+      if (us < best.res.dc_us) {
+        best.res.dc_variant = variant;
+        best.res.dc_us = us;
+      }
+    }
   }
   {
     const std::vector<FftPlan> cy = fft_candidates(g0.ny, 6);
@@ -256,6 +273,7 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
           Geom g = g0;
           g.dc_generic = 1;
           g.dc_direct = direct;
+          g.dc_reg_groups = 0;
           g.py = py;
           g.pz = pz;
           double us;
@@ -298,8 +316,9 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
   }
   best.res.candidates = count;
   for (int i = 0; i < 8; ++i) {
-    best.res.radix_y[i] = (best.res.dc_variant && i < best.py.np) ? best.py.r[i] : 0;
-    best.res.radix_z[i] = (best.res.dc_variant && i < best.pz.np) ? best.pz.r[i] : 0;
+    const bool runtime = best.res.dc_variant == 1 || best.res.dc_variant == 2;
+    best.res.radix_y[i] = (runtime && i < best.py.np) ? best.py.r[i] : 0;
+    best.res.radix_z[i] = (runtime && i < best.pz.np) ? best.pz.r[i] : 0;
   }
   install(P, best);
   {
@@ -317,14 +336,16 @@ done:
 
 int lps_apply_tune(lps_plan* P, const lps_tune_result* t) {
   ARG(P != nullptr && t != nullptr, "NULL argument");
-  ARG(t->dc_variant >= 0 && t->dc_variant <= 2, "dc_variant must be 0, 1 or 2");
+  ARG(t->dc_variant >= 0 && t->dc_variant <= 4, "dc_variant must be 0..4");
   ARG(t->lrs_tiles >= 1 && t->lrs_tiles <= 32 / P->g.nc, "lrs_tiles must be in 1..32/nz");
   TuneEntry e{};
   e.res = *t;
-  if (t->dc_variant == 0) {
+  if (t->dc_variant == 0 || t->dc_variant >= 3) {
     Geom g = P->g;
     g.dc_generic = 0;
+    g.dc_reg_groups = reg_groups_of(t->dc_variant, g.ncoil);
     ARG(dc_has_fixed(g), "no compile-time kernel for this plane size");
+    ARG(t->dc_variant == 0 || dc_reg_applies(g), "no register-transform kernel for this plane size");
   } else {
     auto plan_of = [&](const int* r, int n, FftPlan& f) -> bool {
       f = FftPlan{};

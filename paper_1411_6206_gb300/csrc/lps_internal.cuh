@@ -78,6 +78,7 @@ struct Geom {
   int dc_generic;           // 1: always the runtime-sized data-consistency kernel (autotuner)
   int dc_direct;            // runtime-sized kernel reads coil maps from global memory (no staging)
   int lrs_tpc;              // 8x8 tiles per CTA of the sparse-step kernel (0: 32 / nc)
+  int dc_reg_groups;        // register-transform DC kernel (128 x 16 planes): coil groups, 0 = off
 };
 
 // ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
@@ -206,6 +207,8 @@ int lrs_blocks(const Geom& g);
 int lrs_tpc(const Geom& g);
 int lrs_threads(const Geom& g);
 bool dc_has_fixed(const Geom& g);
+bool dc_reg_applies(const Geom& g);
+cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);
 cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st);

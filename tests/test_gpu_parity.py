@@ -12,7 +12,7 @@ import pytest
 
 from oracle import lps_oracle as O
 from tests.abi_layout import bits_to_mallat, mallat_to_bits
-from tests.gpu_cases import c64, make_case, oracle_params, rel, up
+from tests.gpu_cases import c64, frame_support_band, make_case, oracle_params, rel, up
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -114,6 +114,35 @@ def test_data_consistency_step(L, nz, nx, ny, nc, fz):
     pl.close()
 
 
+@pytest.mark.parametrize("variant", [0, 3, 4])
+@pytest.mark.parametrize("nc,fz", [(8, 1), (3, 1), (12, 1), (8, 0)])
+def test_dc_kernel_variants_on_128x16_plane(L, variant, nc, fz):
+    """Every data-consistency kernel of the 128 x 16 plane, installed by hand: the compile-time
+    kernel with staged coil planes (0) and the register-transform kernel with 4 (3) and 8 (4)
+    coil groups, with one or several coils per group, 3D and per-slice encodes. Step (4)
+    alone against the oracle to the operator bound, then a 12-iteration frame to the
+    end-to-end bound."""
+    nz, nx, ny = 16, 16, 128
+    case = make_case(nz, nx, ny, nc, seed=60 + nc + 7 * fz, fft_z=fz)
+    pl = plan_for(L, case, nz, nx, ny, nc, fft_z=fz, max_iters=12)
+    L.apply_tune(pl.handle, variant, (), (), lrs_tiles=1)
+    rng = np.random.default_rng(3)
+    Z = c64(rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny)))
+    X = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    r2 = L.data_consistency(pl.handle, dev(Z), X)
+    coils, d = up(case["coils"]), up(case["d"])
+    R = O.E(up(Z), coils, case["mask"], fz) - d
+    Xref = up(Z) - O.EH(R, coils, case["mask"], fz)
+    assert rel(X.cpu().numpy(), Xref) < OP_TOL
+    assert abs(r2 - np.vdot(R, R).real) < 1e-5 * np.vdot(R, R).real
+    pl.set_data(dev(case["d"]))
+    recon = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+    pl.reconstruct_frame(recon=recon)
+    ref = O.priori_ls(d, coils, case["mask"], oracle_params(pl.params))
+    assert O.nrmse(recon.cpu().numpy(), ref.recon) <= E2E_TOL
+    pl.close()
+
+
 def one_iteration_case(L, nz, nx, ny, nc, with_prior, lam_p=0.5, seed=11, J=3, eig=0):
     case = make_case(nz, nx, ny, nc, seed=seed)
     pl = plan_for(L, case, nz, nx, ny, nc, lambda_p=lam_p, wavelet_levels=J, eig_precision=eig)
@@ -149,9 +178,14 @@ def one_iteration_case(L, nz, nx, ny, nc, with_prior, lam_p=0.5, seed=11, J=3, e
 def test_one_iteration_from_state(L, nz, nx, ny, nc, with_prior):
     pl, ref, Xg, Lg, Sg = one_iteration_case(L, nz, nx, ny, nc, with_prior)
     tol = svt_tol(ref.sigma_in, ref.lambda_L, np.linalg.norm(ref.L))
-    assert rel(Lg, ref.L) < tol
-    assert rel(Sg, ref.S) < 10 * OP_TOL or np.linalg.norm(ref.S) < 1e-6
-    assert rel(Xg, ref.X) < tol
+    eL, eS, eX = rel(Lg, ref.L), rel(Sg, ref.S), rel(Xg, ref.X)
+    print(f"one iteration {nz}x{nx}x{ny}x{nc} prior={with_prior}: svt_tol {tol:.3e}, "
+          f"L {eL:.3e}, S {eS:.3e}, X {eX:.3e}")
+    assert eL < tol
+    # step (3) thresholds T(X_{k-1} - L_{k-1}) of the common state: no Gram is involved, so the
+    # sparse part takes the operator bound
+    assert eS < OP_TOL or np.linalg.norm(ref.S) < 1e-6
+    assert eX < tol
     pl.close()
 
 
@@ -159,7 +193,7 @@ def test_one_iteration_from_state(L, nz, nx, ny, nc, with_prior):
 def test_one_iteration_other_wavelet_levels(L, J):
     pl, ref, Xg, Lg, Sg = one_iteration_case(L, 8, 16, 16, 2, True, J=J)
     assert rel(Lg, ref.L) < OP_TOL
-    assert rel(Sg, ref.S) < 10 * OP_TOL
+    assert rel(Sg, ref.S) < OP_TOL
     pl.close()
 
 
@@ -187,8 +221,10 @@ def check_support(sup_words, ref, nz, nx, ny, J, band=1e-5):
     if not diff.any():
         return 0
     cabs = np.abs(ref.c)
-    near = np.abs(cabs - ref.lambda_S) <= band * cabs.max()
-    assert not (diff & ~near).any(), f"{int((diff & ~near).sum())} support bits differ off the tie band"
+    dist = np.abs(cabs - ref.lambda_S) / cabs.max()
+    near = dist <= band
+    assert not (diff & ~near).any(), (f"{int((diff & ~near).sum())} of {int(diff.sum())} differing support bits "
+                                      f"lie off the tie band; farthest at {dist[diff].max():.3e} max|c|")
     return int(diff.sum())
 
 
@@ -432,6 +468,16 @@ def test_full_size_frames_match_oracle(L, wname):
         err = O.nrmse(recon.cpu().numpy(), ref.recon)
         assert err <= E2E_TOL, (t, err)
         assert st.iters == w.iters
+        # the frame's output support T^(t): bits equal except within the tie band of lambda_S,
+        # the measured coefficient perturbation of the final iterate (at most 0.1 % of the bits)
+        Xg = torch.empty_like(recon)
+        Lg = torch.empty_like(recon)
+        L.get_state(pl.handle, Xg, Lg, None)
+        band = frame_support_band(Xg.cpu().numpy(), Lg.cpu().numpy(), ref)
+        ndiff = check_support(sup, ref, w.nz, w.nx, w.ny, 3, band=band)
+        print(f"{wname} frame {t + 1}: NRMSE {err:.3e}, support bits {int(ref.support.sum())}, "
+              f"differing {ndiff} (tie band {band:.2e} max|c|)")
+        assert ndiff <= 1e-3 * max(1, int(ref.support.sum()))
         # the next frame's prior is the GPU's own output (an input of Algorithm 1)
         prior = O.Prior(support=bits_to_mallat(sup, w.nz, w.nx, w.ny, 3), sigma=sig.copy())
     pl.close()
