@@ -17,7 +17,8 @@
 //   column phase: inverse transform along z in registers, multiply by conj(C_c), accumulate.
 // The intermediate slot of (s, j) in a row is 8 s + (j ^ (s & 7)): with a row stride of
 // 136 (= 8 mod 16) complex values, every shared access of the row phase touches 16
-// distinct 8-byte bank pairs per half-warp (no conflicts), as do the column accesses.
+// distinct 8-byte bank pairs per half-warp (no conflicts), as do the column accesses; the
+// twiddles sit in two layouts and the line map rows 136 shorts apart for the same reason.
 // The prologue forms L_k = (X_{k-1} - S_{k-1}) W (steps 1-2) and the change statistic; the
 // epilogue sums the groups in a fixed order, writes X_k and the plane Gram (summed over
 // 4-CTA clusters through distributed shared memory), exactly as the staged-coil kernel does.
@@ -31,7 +32,7 @@ namespace lps {
 
 namespace {
 
-constexpr int kNY = 128, kNZ = 16, kRS = 136, kGT = 128, kLMS = 130;
+constexpr int kNY = 128, kNZ = 16, kRS = 136, kGT = 128, kLMS = 136;
 constexpr int kPlane = kNY * kNZ;
 constexpr int kRegCluster = 4;   // x-planes per cluster (the Gram partial count nx / 4)
 
@@ -45,7 +46,7 @@ struct RegLayout {
   static constexpr size_t abuf = ACCS ? gbuf : 0;
   static constexpr size_t zs = kNZ * kRS;
   static constexpr size_t bytes() {
-    return (gbuf + abuf + zs + kNY + kNZ * kNZ) * sizeof(float2) + ((kNZ * kLMS * sizeof(short) + 15) & ~15) +
+    return (gbuf + abuf + zs + 2 * kNY + kNZ * kNZ) * sizeof(float2) + ((kNZ * kLMS * sizeof(short) + 15) & ~15) +
            64 * sizeof(float);
   }
 };
@@ -63,8 +64,12 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   float2* gbuf = reinterpret_cast<float2*>(smem);   // [G][kNZ][kRS]
   float2* abuf = gbuf + Lay::gbuf;                  // ACCS: [G][kNZ][kRS] coil sums
   float2* zs = abuf + Lay::abuf;                    // [kNZ][kRS]: Z, later M = X - S
-  float2* twy = zs + Lay::zs;                       // [kNY] exp(-2 pi i q / 128)
-  float2* wsh = twy + kNY;                          // [kNZ][kNZ]
+  // twiddles w128^{js} (j < 8, s < 16) in two layouts, so that the index that varies across
+  // the threads of a row is the contiguous one: tsj[s][j] (pass 1: j = t8) and tjs[j][s]
+  // (inverse pass: s = t8 + 8h)
+  float2* tsj = zs + Lay::zs;                       // [16][8]
+  float2* tjs = tsj + kNY;                          // [8][16]
+  float2* wsh = tjs + kNY;                          // [kNZ][kNZ]
   short* lmap = reinterpret_cast<short*>(wsh + kNZ * kNZ);   // [kNZ][kLMS]: line index or -1
   float* red = reinterpret_cast<float*>(reinterpret_cast<unsigned char*>(lmap) +
                                         ((kNZ * kLMS * sizeof(short) + 15) & ~15));
@@ -76,22 +81,34 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   const long long xy = (long long)nx * kNY;
   const long long xoff = (long long)x * kNY;
 
-  for (int i = tid; i < kNY; i += NTH) twy[i] = a.tw_y[i];
+  for (int i = tid; i < kNY; i += NTH) {
+    const int sa = i >> 3, ja = i & 7;   // tsj[sa][ja] = w^(ja sa)
+    const int jb = i >> 4, sb = i & 15;  // tjs[jb][sb] = w^(jb sb)
+    tsj[i] = a.tw_y[ja * sa];
+    tjs[i] = a.tw_y[jb * sb];
+  }
   for (int i = tid; i < kNZ * kLMS; i += NTH) lmap[i] = -1;
-  pdl_trigger();
-  pdl_wait();   // L, S, X, W, the control block and the line table come from earlier work
-  const int conv = a.ctrl ? a.ctrl->converged : 0;
-  if (conv) return;   // converged earlier in this frame: nothing is read or written
+  // sampled-line map: (kz, ky) -> line index (lines are kz * (ny + 1) + ky in raster order);
+  // the mask and its line table are set before any frame work
   const int m = a.persist->nlines;
-
-  // ---- prologue: Z = L_k + S_k of the plane into zs -------------------------------------
+  __syncthreads();   // the map was cleared above by other threads
+  for (int l = tid; l < m; l += NTH) {
+    const int p = a.lines[l];
+    const int kz = p / (kNY + 1), ky = p - kz * (kNY + 1);
+    lmap[kz * kLMS + ky] = (short)l;
+  }
+  // Iteration form with W (float32 path): this launch is released by the eigen kernel after
+  // that kernel's own wait, so the previous iteration's data-consistency kernel and the sparse
+  // step (joined by an event) have completed: their outputs (X_{k-1}, L_{k-1}, S_{k-1}, S_k)
+  // are read before this wait, while the eigendecomposition still runs; W and the control
+  // block after it.
   const bool iter_form = a.W != nullptr || a.Lpre != nullptr;
+  const bool early = a.W != nullptr;
   float dz2 = 0.f, z2 = 0.f;   // ||Z_k - Z_{k-1}||^2, ||Z_{k-1}||^2 (this thread's elements)
   float2 Sk[EPT], Dz[EPT];
-  if (iter_form) {
-    float2* Mp = gbuf;             // group 0's buffer: M_{k-1} = X_{k-1} - S_{k-1}
-    float2* Lsh = gbuf + kNZ * kRS;   // group 1's buffer (or zs when G == 1): L_k
-    if (G == 1) Lsh = zs;
+  float2* Mp = gbuf;                // group 0's buffer: M_{k-1} = X_{k-1} - S_{k-1}
+  float2* Lsh = gbuf + kNZ * kRS;   // group 1's buffer: L_k
+  auto prologue_loads = [&]() {
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       const int e = tid + k * NTH, z = e / kNY, y = e % kNY;
@@ -103,6 +120,16 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
       Dz[k] = csub(Sk[k], Zo);
       z2 += cabs2(Zo);
     }
+  };
+  if (early) prologue_loads();
+  pdl_trigger();
+  pdl_wait();   // W and the control block (without W also L, S and X) come from earlier work
+  const int conv = a.ctrl ? a.ctrl->converged : 0;
+  if (conv) return;   // converged earlier in this frame: nothing is written
+
+  // ---- prologue: Z = L_k + S_k of the plane into zs -------------------------------------
+  if (iter_form) {
+    if (!early) prologue_loads();
     if (a.W) {
       for (int i = tid; i < kNZ * kNZ; i += NTH) wsh[i] = a.W[i];
       __syncthreads();
@@ -121,7 +148,6 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
           o[j].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, o[j].y));
         }
       }
-      if (G == 1) __syncthreads();   // Lsh aliases zs only with one group (Mp is read above)
 #pragma unroll
       for (int j = 0; j < OUTS; ++j) Lsh[(zb + j) * kRS + y] = o[j];
     }
@@ -133,13 +159,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
       const float2 Lk = a.W ? Lsh[z * kRS + y] : a.Lpre[gi];
       a.Lbuf[gi] = Lk;
       dz2 += cabs2(cadd(Lk, Dz[k]));
-      Sk[k] = cadd(Lk, Sk[k]);   // Z
-    }
-    __syncthreads();   // Lsh may alias zs
-#pragma unroll
-    for (int k = 0; k < EPT; ++k) {
-      const int e = tid + k * NTH;
-      zs[(e / kNY) * kRS + e % kNY] = Sk[k];
+      zs[z * kRS + y] = cadd(Lk, Sk[k]);   // Z
     }
   } else {
 #pragma unroll
@@ -150,13 +170,6 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
       if (a.S) v = cadd(v, a.S[gi]);
       zs[z * kRS + y] = v;
     }
-  }
-  // sampled-line map: (kz, ky) -> line index (lines are kz * (ny + 1) + ky in raster order)
-  __syncthreads();   // the map was cleared above by other threads
-  for (int l = tid; l < m; l += NTH) {
-    const int p = a.lines[l];
-    const int kz = p / (kNY + 1), ky = p - kz * (kNY + 1);
-    lmap[kz * kLMS + ky] = (short)l;
   }
   __syncthreads();
 
@@ -174,7 +187,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
 #pragma unroll
   for (int z = 0; z < NACC; ++z) acc[z] = make_float2(0.f, 0.f);
   float2* A = abuf + grp * kNZ * kRS;   // ACCS: this group's sums (thread gt owns column gt)
-  if (ACCS) {
+  if (ACCS && grp >= ncoil) {
 #pragma unroll
     for (int z = 0; z < kNZ; ++z) A[z * kRS + gt] = make_float2(0.f, 0.f);
   }
@@ -188,6 +201,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     const float2* Cc = a.coils + (long long)c * g.N + xoff + gt;
     const float2* dh = a.dhyb + ((long long)x * ncoil + c) * g.mpad;
     // column phase: v[z] = sc C_c Z at (z, y = gt), transform along z
+    const bool first = c == grp;
 #pragma unroll
     for (int z = 0; z < kNZ; ++z) v[z] = cscale(cmul(__ldg(Cc + z * xy), zs[z * kRS + gt]), sc);
     if (FFTZ) dft16(v, false);
@@ -199,7 +213,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     for (int r = 0; r < 16; ++r) v[r] = R[t8 + 8 * r];
     dft16(v, false);
 #pragma unroll
-    for (int s = 1; s < 16; ++s) v[s] = cmul(v[s], twy[t8 * s]);
+    for (int s = 1; s < 16; ++s) v[s] = cmul(v[s], tsj[8 * s + t8]);
     __syncwarp();
 #pragma unroll
     for (int s = 0; s < 16; ++s) R[8 * s + (t8 ^ (s & 7))] = v[s];
@@ -233,7 +247,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
       // inverse: radix 8 over q, twiddle conj(w128^{js}), back into the same slots
       dft8(w, true);
 #pragma unroll
-      for (int j = 1; j < 8; ++j) w[j] = cmulc(twy[j * s], w[j]);
+      for (int j = 1; j < 8; ++j) w[j] = cmulc(tjs[16 * j + s], w[j]);
 #pragma unroll
       for (int j = 0; j < 8; ++j) R[8 * s + (j ^ t8)] = w[j];
     }
@@ -256,7 +270,8 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
       if constexpr (ONE) {
         B[z * kRS + gt] = make_float2(t.x * sc, t.y * sc);   // fmaf(t, sc, 0) rounds the same
       } else if constexpr (ACCS) {
-        float2 u = A[z * kRS + gt];
+        // the first coil's term initialises the sum (0 + t sc rounds the same)
+        float2 u = first ? make_float2(0.f, 0.f) : A[z * kRS + gt];
         u.x = fmaf(t.x, sc, u.x);
         u.y = fmaf(t.y, sc, u.y);
         A[z * kRS + gt] = u;

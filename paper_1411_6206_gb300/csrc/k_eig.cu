@@ -40,17 +40,12 @@ __device__ __forceinline__ C scl_(C a, R s) { return mkc(a.x * s, a.y * s); }
 template <typename C>
 __device__ __forceinline__ C conj_(C a) { return mkc(a.x, -a.y); }
 
-// Approximate reciprocal square root and reciprocal with subnormals flushed to zero (PTX
-// rsqrt.approx.ftz / rcp.approx.ftz): the rotation parameters need neither the subnormal
-// range nor the extra instructions that preserve it.
+// Approximate reciprocal square root with subnormals flushed to zero (PTX rsqrt.approx.ftz):
+// the rotation parameters need neither the subnormal range nor the extra instructions that
+// preserve it.
 __device__ __forceinline__ float rsqrt_ftz(float x) {
   float r;
   asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ float rcp_ftz(float x) {
-  float r;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
@@ -67,23 +62,26 @@ __device__ __forceinline__ float4 rot_params(const float2* A, int p, int q, floa
   const float g2 = apq.x * apq.x + apq.y * apq.y;
   const float lim = fmaxf(eps * fmaxf(fabsf(app), fabsf(aqq)), floor_);
   // Computed for every pair and selected at the end (no divergent branch in the Jacobi
-  // step), with the same t written as t = sign(d) 2|a_pq| / (|d| + sqrt(d^2 + 4|a_pq|^2)),
-  // d = a_qq - a_pp, through u = t/|a_pq|: c = 1/sqrt(1 + u^2 |a_pq|^2), s e^{i arg a_pq} =
-  // c u a_pq, t|a_pq| = u |a_pq|^2 (three dependent approximate intrinsics). c and s derive
-  // from one u, so c^2 + |s|^2 = 1 to float32 precision whatever the rounding of u; a slightly
-  // inexact u only leaves a residue in a_pq that the next sweep removes.
+  // step), from r = sqrt(d^2 + 4|a_pq|^2), d = a_qq - a_pp, through two dependent approximate
+  // reciprocal square roots: with rq = 1/r, cos^2(theta) = x = (1 + |d| rq)/2, so
+  // c = x / sqrt(x), s e^{i arg a_pq} = sign(d) rq / sqrt(x) a_pq (|s| = |a_pq| / (r c)) and
+  // t|a_pq| = sign(d) |a_pq|^2 rq / x (t = tan(theta), the smaller root). In exact arithmetic
+  // c^2 + |s|^2 = x + |a_pq|^2 rq^2 / x = 1; in float32 it holds to a few units in the last
+  // place, as does the annihilation of a_pq; a residue left in a_pq is removed by the next
+  // sweep.
   float4 r;
   const bool rot = g2 > lim * lim;
   const float d = aqq - app;
   const float q2 = fmaf(4.0f, g2, d * d);
   const float rq = rsqrt_ftz(rot ? q2 : 1.0f);   // q2 itself whenever the pair rotates
-  const float u = copysignf(2.0f, d) * rcp_ftz(fmaf(q2, rq, fabsf(d)));
-  const float c = rsqrt_ftz(fmaf(u * u, g2, 1.0f));
-  const float cu = c * u;
+  const float x = fmaf(0.5f * fabsf(d), rq, 0.5f);
+  const float ix = rsqrt_ftz(x);
+  const float c = x * ix;
+  const float fs = copysignf(rq * ix, d);
   r.x = rot ? c : 1.f;
-  r.y = rot ? cu * apq.x : 0.f;
-  r.z = rot ? cu * apq.y : 0.f;
-  r.w = rot ? u * g2 : 0.f;
+  r.y = rot ? fs * apq.x : 0.f;
+  r.z = rot ? fs * apq.y : 0.f;
+  r.w = rot ? fs * ix * g2 : 0.f;
   return r;
 }
 
@@ -112,8 +110,25 @@ __device__ __forceinline__ int next_pos(int p, int np) {
 // V rows) start on warp boundaries, so that no warp splits between their code paths. Every
 // thread computes the rotations it needs itself from the diagonal blocks, so one barrier per
 // step suffices. Returns the sweeps done.
-__device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n, float eps, float floor_,
+// Threads that hold a task of the Jacobi step below (whole warps): off-diagonal blocks from
+// thread 0, diagonal blocks and V row pairs each from the next warp boundary.
+__host__ __device__ __forceinline__ int jacobi_threads(int n) {
+  const int np = n + (n & 1), nh = np >> 1;
+  const int noff = nh * (nh - 1) / 2;
+  const int dbase = ((noff + 31) >> 5) << 5;
+  const int vbase = ((dbase + nh + 31) >> 5) << 5;
+  return ((vbase + nh * nh + 31) >> 5) << 5;
+}
+
+__device__ __forceinline__ void jsync(int nthr) { asm volatile("bar.sync 1, %0;" ::"r"(nthr) : "memory"); }
+
+// Called by threads 0 .. jacobi_threads(n) - 1 only (named barrier 1): the other warps of the
+// CTA have no task and wait at the CTA barrier that follows.
+template <int NCT>
+__device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n_rt, float eps, float floor_,
                       int max_sweeps, int* flags) {
+  const int n = NCT ? NCT : n_rt;
+  const int nthr = jacobi_threads(n);
   using C = float2;
   using C4 = float4;
   using R = float;
@@ -150,12 +165,19 @@ __device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n, f
     // rotates every pair above the threshold itself): the residual stays at the rounding level
     // of the float32 Gram, and sweeps that would only move rounding noise are not started
     if (tid == 0) flags[sweep & 1] = 0;
-    __syncthreads();
-    for (int t = tid; t < n * n; t += blockDim.x) {
+    jsync(nthr);
+    for (int t = tid; t < n * n; t += nthr) {
       const int p = t / n, q = t - (t / n) * n;
-      if (p < q && rot_params(A, p, q, 2.f * eps, 2.f * floor_).w != 0.f) flags[sweep & 1] = 1;
+      if (p < q) {
+        // the rotation test of rot_params at twice the thresholds (no rotation parameters)
+        const float app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
+        const float2 apq = A[p * kLd + q];
+        const float g2 = apq.x * apq.x + apq.y * apq.y;
+        const float lim = fmaxf(2.f * eps * fmaxf(fabsf(app), fabsf(aqq)), 2.f * floor_);
+        if (g2 > lim * lim) flags[sweep & 1] = 1;
+      }
     }
-    __syncthreads();
+    jsync(nthr);
     if (!flags[sweep & 1] || sweep >= max_sweeps) break;
     for (int st = 0; st < np - 1; ++st) {
       auto rot_of = [&](int k) -> C4 { return rot_params(A, 2 * k, 2 * k + 1, eps, floor_); };
@@ -207,7 +229,7 @@ __device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n, f
         Vn[(r0 + 1) * kLd + np2] = sub_(scl_<C, R>(vp1, r.x), mul_(vq1, conj_(se)));
         Vn[(r0 + 1) * kLd + nq2] = add_(mul_(vp1, se), scl_<C, R>(vq1, r.x));
       }
-      __syncthreads();
+      jsync(nthr);
       C* t = A;
       A = An;
       An = t;
@@ -228,9 +250,10 @@ struct alignas(16) EigShared {
   float2 V1[kMaxNc * kLd];   // second eigenvector buffer of the Jacobi permutation
   float f[kMaxNc];         // sigma''_i / sigma_i
   double lam[kMaxNc];      // eigenvalues
-  float lamf[kMaxNc];      // eigenvalues as float32 (float32 path)
   float sprevf[kMaxNc];    // sigma_prev as float32
   int flags[4];
+  int jac_sweeps, jac_odd;   // Jacobi sweeps done; 1 if A and V ended in the second buffers
+  float lrs_l1;              // l1 off the prior support of the previous iteration
   unsigned char tri[2][kMaxNc * (kMaxNc + 1) / 2];   // (i, j) of upper-triangle entry e
   double sprev[kMaxNc];    // sigma_prev
   // control scalars read once at entry
@@ -267,15 +290,21 @@ __device__ __forceinline__ float2 gram_chunk(const float2* __restrict__ gram_par
   return make_float2(sx, sy);
 }
 
+// NCT: the column count fixed at compile time (its loops unroll and their loads pipeline);
+// 0 takes it from the geometry at run time.
+template <int NCT>
 __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   EigShared& sh = *reinterpret_cast<EigShared*>(smem_raw);
   DevCtrl* ctrl = a.ctrl;
   const int tid = threadIdx.x;
-  const int n = a.g.nc;
+  const int n = NCT ? NCT : a.g.nc;
   const int np = n + (n & 1);
-  pdl_trigger();
+  // The successor (the data-consistency kernel) is released only after this wait: once it
+  // runs, every kernel before this one has completed, so it may read their outputs (X, L and
+  // the sparse parts of the previous iteration) before its own wait.
   pdl_wait();   // the Gram partials, statistics and control block come from earlier kernels
+  pdl_trigger();
   const int nn = n * n;
   const int nut = n * (n + 1) / 2;
   const bool tol_on = a.tol > 0.0;
@@ -306,21 +335,45 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     const float2* vsrc = a.Vin ? a.Vin : a.V;
     for (int e = tid; e < nn; e += kEigThreads) sh.V[(e / n) * kLd + e % n] = vsrc[e];
   }
-  // statistics of iteration iter-1: the last warp
+  // statistics of iteration iter-1: the last warp sums the data-consistency partials (x:
+  // ||E Z - d||^2, z: ||Z_k - Z_{k-1}||^2, w: ||Z_{k-1}||^2), the warp before it the sparse
+  // step's l1 off the prior support; eight loads per lane are in flight at a time
   const bool stats_on = a.iter > 1 && a.part != 2;
   const int sw = (kEigThreads >> 5) - 1;
   float4 st4 = make_float4(0.f, 0.f, 0.f, 0.f);
-  if ((tid >> 5) == sw && stats_on) {
-    // x: ||E Z - d||^2, z: ||Z_k - Z_{k-1}||^2, w: ||Z_{k-1}||^2 (data consistency);
-    // y: l1 off the prior support (sparse step)
+  if (stats_on && (tid >> 5) == sw) {
     const int lane = tid & 31;
-    for (int i = lane; i < a.g.nx; i += 32) {
-      const float4 q = reinterpret_cast<const float4*>(a.dc_part)[i];
-      st4.x += q.x;
-      st4.z += q.y;
-      st4.w += q.z;
+    const float4* dc4 = reinterpret_cast<const float4*>(a.dc_part);
+    for (int i0 = 0; i0 < a.g.nx; i0 += 256) {
+      float4 q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + lane + 32 * u;
+        q[u] = i < a.g.nx ? dc4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        st4.x += q[u].x;
+        st4.z += q[u].y;
+        st4.w += q[u].z;
+      }
     }
-    for (int i = lane; i < a.lrs_parts; i += 32) st4.y += a.lrs_part[2 * i];
+  } else if (stats_on && (tid >> 5) == sw - 1) {
+    const int lane = tid & 31;
+    float l1 = 0.f;
+    for (int i0 = 0; i0 < a.lrs_parts; i0 += 256) {
+      float q[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int i = i0 + lane + 32 * u;
+        q[u] = i < a.lrs_parts ? a.lrs_part[2 * i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) l1 += q[u];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+    if (lane == 0) sh.lrs_l1 = l1;
   }
   // Gram partials: all n x n entries, ksub interleaved chunks per entry
   const int ksub = nn <= kEigThreads / 2 ? 2 : 1;
@@ -351,7 +404,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       st4.w += __shfl_xor_sync(0xffffffffu, st4.w, o);
     }
     if ((tid & 31) == 0) {
-      const float r2 = st4.x, l1 = st4.y;
+      const float r2 = st4.x, l1 = sh.lrs_l1;
       const float rel = sqrtf(st4.z / fmaxf(st4.w, 1e-30f));
       const bool nonfinite = !isfinite(r2) || !isfinite(l1) || !isfinite(sh.sig_prev1);
       const bool stop = nonfinite || (tol_on && rel < a.tol_f);
@@ -376,6 +429,8 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   }
 
   int sweeps = 0;
+  float2* Af = sh.A0;    // eigenvalues on the diagonal after the Jacobi
+  float2* Vres = sh.V;   // eigenvectors (columns)
   if (a.part != 2) {
     // 2. Gram matrix: combine the chunk sums in a fixed order; exact Hermitian symmetry
     if (tid < ksub * nn) sub[tid] = gacc0;
@@ -406,6 +461,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       for (int e = tid; e < nn; e += kEigThreads) {
         const int i = e / n, j = e - (e / n) * n;
         float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
         for (int k = 0; k < n; ++k) s = cadd(s, cmul(sh.G[i * kLd + k], sh.V[k * kLd + j]));
         sh.A1[i * kLd + j] = s;
       }
@@ -413,6 +469,7 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       for (int e = tid; e < nut; e += kEigThreads) {
         const int i = sh.tri[0][e], j = sh.tri[1][e];
         float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
         for (int k = 0; k < n; ++k) s = cadd(s, cmulc(sh.V[k * kLd + i], sh.A1[k * kLd + j]));
         if (i == j) s.y = 0.f;
         sh.A0[i * kLd + j] = s;
@@ -432,19 +489,25 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     }
     __syncthreads();
     float trace = 0.f;
+#pragma unroll 8
     for (int i = 0; i < n; ++i) trace += fabsf(sh.A0[i * kLd + i].x);
-    float2* Af = sh.A0;
     float2* Afn = sh.A1;
     float2* Vf = sh.V;
     float2* Vfn = sh.V1;
-    sweeps = jacobi(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
-    if (Vf != sh.V) {
-      for (int e = tid; e < np * np; e += kEigThreads) {
-        const int i = e / np, j = e - (e / np) * np;
-        sh.V[i * kLd + j] = Vf[i * kLd + j];
+    if (tid < jacobi_threads(n)) {
+      sweeps = jacobi<NCT>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
+      if (tid == 0) {
+        // own fields: other Jacobi threads may still read flags[] in their last convergence test
+        sh.jac_sweeps = sweeps;
+        sh.jac_odd = Af != sh.A0;   // the results sit in the second buffers (odd step count)
       }
     }
     __syncthreads();
+    sweeps = sh.jac_sweeps;
+    if (sh.jac_odd) {
+      Af = sh.A1;
+      Vres = sh.V1;
+    }
 
     if (a.part == 1) {
       // float64 mode, first part: hand the Gram, the float32 eigenvectors and eigenvalues to the
@@ -452,22 +515,19 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       for (int e = tid; e < nn; e += kEigThreads) {
         const int i = e / n, j = e - (e / n) * n;
         a.Gout[e] = sh.G[i * kLd + j];
-        a.V[e] = sh.V[i * kLd + j];
+        a.V[e] = Vres[i * kLd + j];
       }
       for (int i = tid; i < n; i += kEigThreads) a.lam64[i] = (double)Af[i * kLd + i].x;
       if (tid == 32) ctrl->sweeps_cur = sweeps;
       return;
     }
-    for (int i = tid; i < n; i += kEigThreads) {
-      sh.lam[i] = (double)Af[i * kLd + i].x;
-      sh.lamf[i] = Af[i * kLd + i].x;
-    }
+    // float32 path: warp 0 reads the eigenvalues from the diagonal of Af below
   } else {
     // float64 mode, second part: the Rayleigh-Ritz eigenvalues and refined eigenvectors
     // (V was loaded with the warm start above)
     for (int i = tid; i < n; i += kEigThreads) sh.lam[i] = a.lam64[i];
+    __syncthreads();
   }
-  __syncthreads();
 
   // 4. singular values, thresholds, prior pull, rank guard: warp 0, lane i = eigenvalue i
   //    (n <= 32), ranks and sums by shuffles; in float64 after the float64 refinement, in
@@ -509,11 +569,11 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
       // float32: every lane reads all eigenvalues from shared memory (broadcast loads in
       // flight together) for its rank and the largest eigenvalue; selects instead of
       // branches; float32 copies of sigma_prev, lambda_p and tau
-      const float li = act ? sh.lamf[i] : -3.0e38f;
+      const float li = act ? Af[i * kLd + i].x : -3.0e38f;
       float lmax = -3.0e38f;
 #pragma unroll 8
       for (int j = 0; j < n; ++j) {
-        const float lj = sh.lamf[j];
+        const float lj = Af[j * kLd + j].x;
         r += (int)(lj > li) | ((int)(lj == li) & (int)(j < i));
         lmax = fmaxf(lmax, lj);
       }
@@ -563,27 +623,41 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   for (int e = tid; e < nn; e += kEigThreads) {
     const int i = e / n, j = e - (e / n) * n;
     float2 s = make_float2(0.f, 0.f);
+#pragma unroll 8
     for (int k = 0; k < n; ++k) {
+      // f_k = 0 contributes exactly nothing (terms are not formed for it)
       const float fk = sh.f[k];
-      if (fk != 0.f) s = cadd(s, cscale(cmul(sh.V[i * kLd + k], cconj(sh.V[j * kLd + k])), fk));
+      const float2 t = cscale(cmul(Vres[i * kLd + k], cconj(Vres[j * kLd + k])), fk);
+      s = fk != 0.f ? cadd(s, t) : s;
     }
     a.W[i * n + j] = s;
-    a.V[i * n + j] = sh.V[i * kLd + j];
+    a.V[i * n + j] = Vres[i * kLd + j];
   }
   if (tid == 0) a.persist->v_valid = 1;
 }
 
 
-cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
+
+template <int NCT>
+static cudaError_t launch_eig_n(const EigArgs& a, cudaStream_t st) {
   const size_t smem = sizeof(EigShared);
   static bool attr_set = false;
   if (smem > 48 * 1024 && !attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_eig, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_eig<NCT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_eig, dim3(1), dim3(kEigThreads), smem, st, a);
+  cudaError_t e = launch_pdl(k_eig<NCT>, dim3(1), dim3(kEigThreads), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
+  switch (a.g.nc) {
+    case 8: return launch_eig_n<8>(a, st);
+    case 16: return launch_eig_n<16>(a, st);
+    case 32: return launch_eig_n<32>(a, st);
+    default: return launch_eig_n<0>(a, st);
+  }
 }
 
 // float64 Rayleigh-Ritz refinement of the float32 eigendecomposition (LPS_EIG_FP64), one warp
