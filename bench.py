@@ -47,8 +47,9 @@ def parse():
     ap.add_argument("--cpu-frames", type=int, default=2, help="oracle frames in the CPU baseline")
     ap.add_argument("--profile", type=int, default=1,
                     help="after the timed steps, one pass with CUDA events around every kernel (roofline)")
-    ap.add_argument("--workload", default="cardiac", choices=["cardiac", "precision"],
-                    help="cardiac: 128x128x16 x 20 frames, 8 coils (default); precision: 192x192x32 x 25, 12 coils")
+    ap.add_argument("--workload", default="cardiac", choices=["cardiac", "precision", "mix160"],
+                    help="cardiac: 128x128x16 x 20 frames, 8 coils (default); precision: 192x192x32 x 25, 12 coils; "
+                         "mix160: the 160x160x14 x 20, 16-coil member of the serving mix (autotuned runtime kernel)")
     ap.add_argument("--precision", default="fp32", choices=["fp32", "tf32", "bf16"],
                     help="Gram and reprojection arithmetic (tf32/bf16: tensor cores with one refinement step)")
     ap.add_argument("--eig", default=None, choices=["fp32", "fp64"],
@@ -58,6 +59,10 @@ def parse():
     ap.add_argument("--serve-seconds", type=float, default=6.5, help="arrival window of the serving study")
     ap.add_argument("--serve-sessions", type=int, default=16)
     ap.add_argument("--batch-problems", type=int, default=64)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the serving sweep of arrival rates")
+    ap.add_argument("--no-precision", action="store_true", help="skip the precision study (192x192x32, 12 coils)")
+    ap.add_argument("--no-small", action="store_true", help="skip the 32x32x8 single-coil latency study")
+    ap.add_argument("--precision-frames", type=int, default=5, help="frames per mode in the precision study")
     return ap.parse_args()
 
 
@@ -165,9 +170,23 @@ def plan_kw(args):
 
 def workload(frames, name="cardiac"):
     from paper_1411_6206_gb300 import phantom as P
-    w = P.CARDIAC if name == "cardiac" else P.PRECISION
+    if name == "mix160":
+        w = next(x for x in P.batched_mix(16, seed0=500) if (x.nx, x.nz, x.ncoil) == (160, 14, 16))
+    else:
+        w = P.CARDIAC if name == "cardiac" else P.PRECISION
     T = w.frames if frames is None else min(frames, w.frames)
     return w, T
+
+
+def dc_kernel_name(w, tuned):
+    """The data-consistency kernel a plan of workload w runs (default launch shapes or tuned)."""
+    if tuned is not None and tuned.dc_variant in (1, 2):
+        return "k_dc"
+    if (w.ny, w.nz) == (128, 16):
+        return "k_dc_reg"
+    if (w.ny, w.nz) in ((192, 32), (32, 8)):
+        return "k_dc_fixed"
+    return "k_dc"
 
 
 def dc_bytes_per_launch(w, m):
@@ -219,6 +238,11 @@ def run_ours(args):
             kd += torch.from_numpy(pr["noise"][t].astype(np.complex64)).to(dev)
             kdatas.append(kd)
     stream.synchronize()
+    tuned = None
+    if args.workload == "mix160":
+        plan.set_mask(masks[0])
+        plan.set_data(kdatas[0])
+        tuned = plan.autotune()
     nlines = [int(m.sum()) for m in masks]
     recon = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
@@ -340,14 +364,20 @@ def run_ours(args):
                 gbs = byts / (avg_ms * 1e-3) / 1e9
                 fl = dc_flops_per_launch(w) / (avg_ms * 1e-3) / 1e12
                 frac_hbm, frac_alu = gbs / hbm, fl / alu_peak
-                tr = profiled_traffic(f"k_dc_fixed_cardiac_{w.nx}x{w.ny}x{w.nz}x{w.ncoil}.txt")
+                kname = dc_kernel_name(w, tuned)
+                tr = profiled_traffic(f"{kname}_{args.workload}_{w.nx}x{w.ny}x{w.nz}x{w.ncoil}.txt")
                 if frac_alu >= frac_hbm:
                     roof = {"bound": "alu", "achieved": round(fl, 3), "peak": round(alu_peak, 2),
                             "unit": "TFLOP/s", "frac": round(frac_alu, 4), "traffic": tr}
                 else:
                     roof = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
                             "frac": round(frac_hbm, 4), "traffic": tr}
-                roof["kernel"] = "k_dc_fixed (data consistency, step 4)"
+                roof["kernel"] = f"{kname} (data consistency, step 4, with the reprojection of steps 1-2)"
+                ws_mb = (w.nx * w.ny * w.nz * 8 * (w.ncoil + 6) + w.nx * w.ncoil * m_last * 8) / 1e6
+                roof["regime"] = (f"working set ~{ws_mb:.0f} MB "
+                                  + ("stays in the 129 MB L2 across iterations (flushed once per step): the "
+                                     "fraction is of HBM peak, the kernel is latency-bound on L2-resident data"
+                                     if ws_mb < 129 else "exceeds the 129 MB L2"))
                 roof["algorithmic_bytes_per_launch"] = byts
                 roof["alt"] = {"hbm_frac": round(frac_hbm, 4), "hbm_gbs": round(gbs, 1),
                                "alu_frac": round(frac_alu, 4), "alu_tflops": round(fl, 3)}
@@ -522,58 +552,70 @@ def gpu_problem(w, frames, lps, PG, P, dev, cycle=None):
     return coils, out
 
 
+def serve_trace(n_sessions, rate, seconds, seed=5):
+    """Poisson arrivals (seeded) of `rate` frames/s per session over `seconds`: [(time, session)]."""
+    rng = np.random.default_rng(seed)
+    trace = []
+    for k in range(n_sessions):
+        t = 0.0
+        while True:
+            t += rng.exponential(1.0 / rate)
+            if t > seconds:
+                break
+            trace.append((t, k))
+    trace.sort()
+    return trace
+
+
+def serve_once(lps, ws_, inputs, trace, single_stream, max_inflight):
+    """One serving run over an arrival trace: every session's frames reconstructed recursively
+    with its state resident; returns frames/s over the span and p50/p99 latency."""
+    srv = lps.Server(150 * 10 ** 9, max_inflight=max_inflight, single_stream=single_stream, autotune=True)
+    sids = [srv.open(lps.params_init(nx=w.nx, ny=w.ny, nz=w.nz, ncoil=w.ncoil, max_iters=w.iters,
+                                     recursive=1), c) for w, (c, _) in zip(ws_, inputs)]
+    nframe = [0] * len(sids)
+    # warm-up: one frame per session (autotunes and captures the frame graphs)
+    tk = [srv.submit(sid, *inputs[k][1][0], srv.now()) for k, sid in enumerate(sids)]
+    for t in tk:
+        srv.wait(t)
+        srv.release(t)
+    t0 = srv.now() + 0.05
+    tickets = []
+    for a, k in trace:
+        while srv.now() < t0 + a:
+            time.sleep(0.0001)
+        fr = inputs[k][1][(1 + nframe[k]) % len(inputs[k][1])]
+        nframe[k] += 1
+        tickets.append(srv.submit(sids[k], fr[0], fr[1], t0 + a))
+    lat, comp = [], []
+    for t in tickets:
+        l_, c_ = srv.wait(t)
+        lat.append(l_)
+        comp.append(c_)
+        srv.release(t)
+    span = max(comp) - (t0 + trace[0][0])
+    srv.close()
+    return {"frames_per_s": round(len(tickets) / span, 2),
+            "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
+            "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
+            "frames": len(tickets)}
+
+
 def run_served(args):
     """Serving study: sessions drawn from the uneven size mix, frames arriving as independent
     Poisson processes of 20 frames/s per session, reconstructed recursively with every
     session's state resident; served (per-session streams, no slot limit) against the plain
-    path (every frame in arrival order on one stream) on the same arrival trace."""
-    import torch
+    path (every frame in arrival order on one stream) on the same arrival trace. With the
+    sweep, the same at lower per-session rates (offered load below capacity, where p50/p99 are
+    frame latencies rather than queue growth) and with a slot limit of 4 frames on the device."""
     from paper_1411_6206_gb300 import lps, phantom as P, phantom_gpu as PG
+    import torch
     dev = torch.device("cuda", 0)
     ws_ = P.batched_mix(args.serve_sessions, seed0=500)
     inputs = [gpu_problem(w, w.frames, lps, PG, P, dev, cycle=8) for w in ws_]
     rate = 20.0
-    rng = np.random.default_rng(5)
-    trace = []
-    for k in range(len(ws_)):
-        t = 0.0
-        while True:
-            t += rng.exponential(1.0 / rate)
-            if t > args.serve_seconds:
-                break
-            trace.append((t, k))
-    trace.sort()
-    res = {}
-    for mode in ("served", "plain"):
-        srv = lps.Server(150 * 10 ** 9, max_inflight=0, single_stream=(mode == "plain"), autotune=True)
-        sids = [srv.open(lps.params_init(nx=w.nx, ny=w.ny, nz=w.nz, ncoil=w.ncoil, max_iters=w.iters,
-                                         recursive=1), c) for w, (c, _) in zip(ws_, inputs)]
-        nframe = [0] * len(sids)
-        # warm-up: one frame per session (autotunes and captures the frame graphs)
-        tk = [srv.submit(sid, *inputs[k][1][0], srv.now()) for k, sid in enumerate(sids)]
-        for t in tk:
-            srv.wait(t)
-            srv.release(t)
-        t0 = srv.now() + 0.05
-        tickets = []
-        for a, k in trace:
-            while srv.now() < t0 + a:
-                time.sleep(0.0001)
-            fr = inputs[k][1][(1 + nframe[k]) % len(inputs[k][1])]
-            nframe[k] += 1
-            tickets.append(srv.submit(sids[k], fr[0], fr[1], t0 + a))
-        lat, comp = [], []
-        for t in tickets:
-            l_, c_ = srv.wait(t)
-            lat.append(l_)
-            comp.append(c_)
-            srv.release(t)
-        span = max(comp) - (t0 + trace[0][0])
-        res[mode] = {"frames_per_s": round(len(tickets) / span, 2),
-                     "p50_ms": round(1e3 * float(np.percentile(lat, 50)), 3),
-                     "p99_ms": round(1e3 * float(np.percentile(lat, 99)), 3),
-                     "frames": len(tickets)}
-        srv.close()
+    trace = serve_trace(len(ws_), rate, args.serve_seconds)
+    res = {mode: serve_once(lps, ws_, inputs, trace, mode == "plain", 0) for mode in ("served", "plain")}
     out = dict(res["served"])
     out["plain"] = res["plain"]
     out.update({"sessions": len(ws_), "arrival_rate_per_session": rate, "offered_frames_per_s": rate * len(ws_),
@@ -581,6 +623,16 @@ def run_served(args):
                 "sizes": [f"{w.nx}x{w.ny}x{w.nz}x{w.ncoil}c" for w in ws_],
                 "how": "Poisson arrivals (seeded), latency = result ready (device event) - arrival, "
                        "server clock; plain = same trace, one stream in arrival order"})
+    if not args.no_sweep:
+        sweep = []
+        for r, inflight in ((2.5, 0), (5.0, 0), (10.0, 0), (10.0, 4)):
+            tr = serve_trace(len(ws_), r, min(args.serve_seconds, 4.0), seed=7)
+            row = {"rate_per_session": r, "offered_frames_per_s": r * len(ws_), "max_inflight": inflight,
+                   "served": serve_once(lps, ws_, inputs, tr, False, inflight)}
+            if inflight == 0:
+                row["plain"] = serve_once(lps, ws_, inputs, tr, True, 0)
+            sweep.append(row)
+        out["sweep"] = sweep
     return out
 
 
@@ -642,6 +694,190 @@ def run_batched(args):
     return res
 
 
+def run_small(args):
+    """The 32 x 32 x 8 single-coil sequence (8 frames, 25% of the ky-kz lines, frame 1 at 50%,
+    30 iterations): latency-bound, reported per frame; NRMSE of frames 1-2 against the oracle
+    given the same samples and prior."""
+    import scipy.fft as sfft
+    import torch
+    from oracle import lps_oracle as O
+    from paper_1411_6206_gb300 import lps, phantom as P
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from abi_layout import bits_to_mallat
+    w = P.SMALL
+    T = w.frames
+    pr = P.problem(w, frames=T)
+    coils = pr["coils"].astype(np.complex64)
+    datas = [(O.E(pr["x"][t], coils.astype(np.complex128), pr["masks"][t]) + pr["noise"][t]).astype(np.complex64)
+             for t in range(T)]
+    st = torch.cuda.Stream()
+    pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1)
+    pl.set_coils(torch.from_numpy(coils).cuda())
+    kd = [torch.from_numpy(d).cuda() for d in datas]
+    out = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+
+    def seq():
+        pl.clear_prior()
+        for t in range(T):
+            pl.set_mask(pr["masks"][t])
+            pl.set_data(kd[t])
+            pl.reconstruct_frame(recon=out[t], stats=False)
+
+    for _ in range(3):
+        seq()
+    st.synchronize()
+    ms = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        seq()
+        e1.record(st)
+        st.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    # parity of frames 1-2 (each against the oracle with the prior the GPU passed on)
+    errs, prior = [], None
+    sup = np.empty(pl.support_words(), np.uint32)
+    sig = np.empty(w.nz)
+    p = O.Params(max_iters=w.iters)
+    one = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+    pl.clear_prior()
+    for t in range(2):
+        pl.set_mask(pr["masks"][t])
+        pl.set_data(kd[t])
+        pl.reconstruct_frame(recon=one, support=sup, sigma=sig, stats=False)
+        with sfft.set_workers(os.cpu_count() or 1):
+            r = O.priori_ls(datas[t].astype(np.complex128), coils.astype(np.complex128), pr["masks"][t], p, prior)
+        errs.append(round(O.nrmse(one.cpu().numpy(), r.recon), 8))
+        prior = O.Prior(support=bits_to_mallat(sup, w.nz, w.nx, w.ny, 3), sigma=sig.copy())
+    pl.close()
+    med = float(np.median(ms))
+    return {"workload": f"{w.nx}x{w.ny}x{w.nz} x {T} frames, {w.ncoil} coil, 25% of the ky-kz lines "
+                        f"(frame 1 at 50%), {w.iters} iterations/frame, recursive",
+            "us_per_frame": round(1e3 * med / T, 2), "frames_per_s": round(T / (med / 1e3), 1),
+            "repeats": len(ms), "nrmse_vs_oracle": errs,
+            "how": "CUDA events around the 8-frame sequence (median of 10, after 3 warm-up runs); the run "
+                   "is launch- and latency-bound, so no roofline fraction is reported"}
+
+
+def run_precision(args):
+    """Precision study on the 192 x 192 x 32 sequence (12 coils, R = 10): frames/s per arithmetic
+    (float32; tf32 and bf16 operands split hi + lo on the tensor cores with float32 accumulation
+    and the float64 Rayleigh-Ritz eigen step), the tensor-core kernels' achieved bandwidth and
+    algorithmic tensor rate, and NRMSE of frame 1 against the FP64 oracle."""
+    import scipy.fft as sfft
+    import torch
+    from oracle import lps_oracle as O
+    from paper_1411_6206_gb300 import lps, phantom as P
+    w = P.PRECISION
+    T = max(2, min(args.precision_frames, w.frames))
+    pr = P.problem(w, frames=T)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    coils = torch.from_numpy(np.ascontiguousarray(pr["coils"].astype(np.complex64))).to(dev)
+    masks = [np.ascontiguousarray(m) for m in pr["masks"]]
+    fwd = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=1)
+    fwd.set_coils(coils)
+    kd = []
+    with torch.cuda.stream(st):
+        for t in range(T):
+            n = fwd.set_mask(masks[t])
+            x = torch.from_numpy(np.ascontiguousarray(pr["x"][t].astype(np.complex64))).to(dev)
+            k = torch.empty((w.ncoil, n, w.nx), dtype=torch.complex64, device=dev)
+            lps.forward(fwd.handle, x, k)
+            k += torch.from_numpy(pr["noise"][t].astype(np.complex64)).to(dev)
+            kd.append(k)
+    st.synchronize()
+    fwd.close()
+    t0 = time.perf_counter()
+    with sfft.set_workers(os.cpu_count() or 1):
+        ref = O.priori_ls(kd[0].cpu().numpy().astype(np.complex128), pr["coils"].astype(np.complex64).astype(np.complex128),
+                          masks[0], O.Params(max_iters=w.iters))
+    oracle_s = time.perf_counter() - t0
+    hbm, _, src = peaks()
+    bf16_peak, tf32_peak, psrc = tensor_peaks()
+    N = w.nx * w.ny * w.nz
+    out = {"workload": f"{w.nx}x{w.ny}x{w.nz} x {T} frames, {w.ncoil} coils, R={w.accel:g} (frame 1 at 50%), "
+                       f"{w.iters} iterations/frame, recursive",
+           "oracle_frame1_s": round(oracle_s, 1)}
+    recon = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
+    for name in ("fp32", "tf32", "bf16"):
+        prec = {"fp32": lps.FP32, "tf32": lps.TF32_REFINE, "bf16": lps.BF16_REFINE}[name]
+        eig = lps.EIG_FP32 if name == "fp32" else lps.EIG_FP64
+        pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1, precision=prec,
+                      eig_precision=eig)
+        pl.set_coils(coils)
+
+        def seq():
+            pl.clear_prior()
+            for t in range(T):
+                pl.set_mask(masks[t])
+                pl.set_data(kd[t])
+                pl.reconstruct_frame(recon=recon, stats=False)
+
+        seq()
+        st.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        seq()
+        e1.record(st)
+        st.synchronize()
+        ms = e0.elapsed_time(e1)
+        lps.set_profiling(pl.handle, True)
+        seq()
+        st.synchronize()
+        kt = lps.get_kernel_times(pl.handle).as_dict()
+        lps.set_profiling(pl.handle, False)
+        # frame 1 alone against the oracle
+        pl.clear_prior()
+        pl.set_mask(masks[0])
+        pl.set_data(kd[0])
+        pl.reconstruct_frame(recon=recon, stats=False)
+        st.synchronize()
+        err = O.nrmse(recon.cpu().numpy(), ref.recon)
+        pl.close()
+        row = {"frames_per_s": round(T / (ms / 1e3), 2), "nrmse_frame1_vs_oracle": round(err, 9),
+               "eig": "fp32 Jacobi" if name == "fp32" else "fp32 Jacobi + fp64 Rayleigh-Ritz",
+               "us_per_launch": {k: round(1e3 * v["ms"] / max(1, v["launches"]), 2) for k, v in kt.items()
+                                 if v["launches"]}}
+        if name != "fp32":
+            peak = bf16_peak if name == "bf16" else tf32_peak
+            g_us = row["us_per_launch"].get("gram_tc")
+            r_us = row["us_per_launch"].get("reproj_tc")
+            # algorithmic work on the Casorati matrix (nx ny rows, nz columns): the Gram and the
+            # reprojection are 8 (nx ny) nz^2 real flops each; the Gram reads X and S, the
+            # reprojection reads X and S and writes L (complex64)
+            fl = 8.0 * w.nx * w.ny * w.nz * w.nz
+            row["gram_tc"] = {"us": g_us, "GB_s": round(2 * N * 8 / (g_us * 1e-6) / 1e9, 1),
+                              "hbm_frac": round(2 * N * 8 / (g_us * 1e-6) / 1e9 / hbm, 4),
+                              "algorithmic_TFLOP_s": round(fl / (g_us * 1e-6) / 1e12, 2),
+                              "tensor_frac": round(fl / (g_us * 1e-6) / 1e12 / peak, 5)}
+            row["reproj_tc"] = {"us": r_us, "GB_s": round(3 * N * 8 / (r_us * 1e-6) / 1e9, 1),
+                                "hbm_frac": round(3 * N * 8 / (r_us * 1e-6) / 1e9 / hbm, 4),
+                                "algorithmic_TFLOP_s": round(fl / (r_us * 1e-6) / 1e12, 2),
+                                "tensor_frac": round(fl / (r_us * 1e-6) / 1e12 / peak, 5)}
+        out[name] = row
+    out["peaks"] = {"hbm_GB_s": hbm, "bf16_TFLOP_s": bf16_peak, "tf32_TFLOP_s": tf32_peak,
+                    "source": f"{src}; tensor: {psrc}"}
+    out["how"] = ("frames/s: CUDA events around the sequence after one warm-up sequence; kernel times from a "
+                  "separate pass with events around every kernel; tensor_frac = algorithmic flops of the "
+                  "contraction over the dense peak of the operand type (the split operands add products "
+                  "executed on the pipe)")
+    return out
+
+
+def tensor_peaks():
+    """Dense bf16 peak (measured burst figure) and the tf32 peak derived from it by the nominal
+    1.1 / 2.25 ratio."""
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        bf = float(d["bf16_tflops"])
+        return bf, round(bf * 1.1 / 2.25, 1), "measured bf16 (MEASURED_PEAKS.json), tf32 = bf16 x 1.1/2.25"
+    except Exception:
+        return 1900.0, round(1900.0 * 1.1 / 2.25, 1), "fallback bf16 1.9 PFLOP/s, tf32 = bf16 x 1.1/2.25"
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -656,6 +892,10 @@ def main():
             out["served"] = run_served(args)
         if ws == 1 and not args.no_batched:
             out["batched"] = run_batched(args)
+        if ws == 1 and not args.no_small:
+            out["small"] = run_small(args)
+        if ws == 1 and not args.no_precision:
+            out["precision"] = run_precision(args)
         if ws == 1 and not args.no_cpu_baseline:
             cb, nr = cpu_baseline(args, w)
             out["cpu_baseline"] = cb
