@@ -63,6 +63,7 @@ def parse():
     ap.add_argument("--no-precision", action="store_true", help="skip the precision study (192x192x32, 12 coils)")
     ap.add_argument("--no-small", action="store_true", help="skip the 32x32x8 single-coil latency study")
     ap.add_argument("--precision-frames", type=int, default=5, help="frames per mode in the precision study")
+    ap.add_argument("--no-fig3", action="store_true", help="skip the PSNR-vs-sampling study (plain vs Priori L+S)")
     return ap.parse_args()
 
 
@@ -479,6 +480,38 @@ def cpu_baseline(args, w):
     return res, [round(e, 8) for e in errs]
 
 
+def cpu_parity(small_job, prec_job):
+    """Oracle comparisons of the GPU outputs kept by the small and precision studies (same
+    complex64 samples, coil maps, masks and priors on both sides)."""
+    import scipy.fft as sfft
+    from oracle import lps_oracle as O
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from abi_layout import bits_to_mallat
+    cores = os.cpu_count() or 1
+    out = {}
+    with sfft.set_workers(cores):
+        if small_job is not None:
+            w = small_job["w"]
+            C = small_job["coils"].astype(np.complex128)
+            p = O.Params(max_iters=w.iters)
+            errs = []
+            for t in range(2):
+                pri = small_job["prior"][t]
+                prior = None if pri is None else O.Prior(support=bits_to_mallat(pri[0], w.nz, w.nx, w.ny, 3),
+                                                         sigma=pri[1])
+                r = O.priori_ls(small_job["data"][t].astype(np.complex128), C, small_job["masks"][t], p, prior)
+                errs.append(round(O.nrmse(small_job["recon"][t], r.recon), 8))
+            out["small"] = errs
+        if prec_job is not None:
+            w = prec_job["w"]
+            t0 = time.perf_counter()
+            r = O.priori_ls(prec_job["data"].astype(np.complex128), prec_job["coils"].astype(np.complex128),
+                            prec_job["mask"], O.Params(max_iters=w.iters))
+            out["precision_oracle_s"] = round(time.perf_counter() - t0, 1)
+            out["precision"] = {k: round(O.nrmse(v, r.recon), 9) for k, v in prec_job["recon"].items()}
+    return out
+
+
 def run_reference(args):
     """The FP64 oracle as the reference arm: each step reconstructs the next frame of the
     recursive sequence on the host cores."""
@@ -694,32 +727,48 @@ def run_batched(args):
     return res
 
 
+def forward_frames(lps, w, pr, T, dev, stream):
+    """k-space of frames 0..T-1 of a problem by the library's forward operator, plus the
+    generator's noise: coil maps on the device, host masks, device samples."""
+    import torch
+    coils = torch.from_numpy(np.ascontiguousarray(pr["coils"].astype(np.complex64))).to(dev)
+    masks = [np.ascontiguousarray(m) for m in pr["masks"][:T]]
+    fwd = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=stream, max_iters=1)
+    fwd.set_coils(coils)
+    kd = []
+    with torch.cuda.stream(stream):
+        for t in range(T):
+            n = fwd.set_mask(masks[t])
+            x = torch.from_numpy(np.ascontiguousarray(pr["x"][t].astype(np.complex64))).to(dev)
+            k = torch.empty((w.ncoil, n, w.nx), dtype=torch.complex64, device=dev)
+            lps.forward(fwd.handle, x, k)
+            k += torch.from_numpy(pr["noise"][t].astype(np.complex64)).to(dev)
+            kd.append(k)
+    stream.synchronize()
+    fwd.close()
+    return coils, masks, kd
+
+
 def run_small(args):
     """The 32 x 32 x 8 single-coil sequence (8 frames, 25% of the ky-kz lines, frame 1 at 50%,
-    30 iterations): latency-bound, reported per frame; NRMSE of frames 1-2 against the oracle
-    given the same samples and prior."""
-    import scipy.fft as sfft
+    30 iterations): latency-bound, reported per frame. Returns the study and the GPU outputs of
+    frames 1-2 (with the prior passed between them) for the CPU leg's oracle comparison."""
     import torch
-    from oracle import lps_oracle as O
     from paper_1411_6206_gb300 import lps, phantom as P
-    sys.path.insert(0, os.path.join(ROOT, "tests"))
-    from abi_layout import bits_to_mallat
     w = P.SMALL
     T = w.frames
     pr = P.problem(w, frames=T)
-    coils = pr["coils"].astype(np.complex64)
-    datas = [(O.E(pr["x"][t], coils.astype(np.complex128), pr["masks"][t]) + pr["noise"][t]).astype(np.complex64)
-             for t in range(T)]
-    st = torch.cuda.Stream()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    coils, masks, kd = forward_frames(lps, w, pr, T, dev, st)
     pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1)
-    pl.set_coils(torch.from_numpy(coils).cuda())
-    kd = [torch.from_numpy(d).cuda() for d in datas]
-    out = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+    pl.set_coils(coils)
+    out = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
 
     def seq():
         pl.clear_prior()
         for t in range(T):
-            pl.set_mask(pr["masks"][t])
+            pl.set_mask(masks[t])
             pl.set_data(kd[t])
             pl.reconstruct_frame(recon=out[t], stats=False)
 
@@ -734,29 +783,28 @@ def run_small(args):
         e1.record(st)
         st.synchronize()
         ms.append(e0.elapsed_time(e1))
-    # parity of frames 1-2 (each against the oracle with the prior the GPU passed on)
-    errs, prior = [], None
+    # frames 1-2 with the prior the GPU passes on, kept for the oracle comparison
+    job = {"w": w, "coils": coils.cpu().numpy(), "masks": masks[:2], "data": [k.cpu().numpy() for k in kd[:2]],
+           "recon": [], "prior": [None]}
     sup = np.empty(pl.support_words(), np.uint32)
     sig = np.empty(w.nz)
-    p = O.Params(max_iters=w.iters)
-    one = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
+    one = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
     pl.clear_prior()
     for t in range(2):
-        pl.set_mask(pr["masks"][t])
+        pl.set_mask(masks[t])
         pl.set_data(kd[t])
         pl.reconstruct_frame(recon=one, support=sup, sigma=sig, stats=False)
-        with sfft.set_workers(os.cpu_count() or 1):
-            r = O.priori_ls(datas[t].astype(np.complex128), coils.astype(np.complex128), pr["masks"][t], p, prior)
-        errs.append(round(O.nrmse(one.cpu().numpy(), r.recon), 8))
-        prior = O.Prior(support=bits_to_mallat(sup, w.nz, w.nx, w.ny, 3), sigma=sig.copy())
+        job["recon"].append(one.cpu().numpy())
+        job["prior"].append((sup.copy(), sig.copy()))
     pl.close()
     med = float(np.median(ms))
-    return {"workload": f"{w.nx}x{w.ny}x{w.nz} x {T} frames, {w.ncoil} coil, 25% of the ky-kz lines "
-                        f"(frame 1 at 50%), {w.iters} iterations/frame, recursive",
-            "us_per_frame": round(1e3 * med / T, 2), "frames_per_s": round(T / (med / 1e3), 1),
-            "repeats": len(ms), "nrmse_vs_oracle": errs,
-            "how": "CUDA events around the 8-frame sequence (median of 10, after 3 warm-up runs); the run "
-                   "is launch- and latency-bound, so no roofline fraction is reported"}
+    res = {"workload": f"{w.nx}x{w.ny}x{w.nz} x {T} frames, {w.ncoil} coil, 25% of the ky-kz lines "
+                       f"(frame 1 at 50%), {w.iters} iterations/frame, recursive",
+           "us_per_frame": round(1e3 * med / T, 2), "frames_per_s": round(T / (med / 1e3), 1),
+           "repeats": len(ms),
+           "how": "CUDA events around the 8-frame sequence (median of 10, after 3 warm-up runs); the run "
+                  "is launch- and latency-bound, so no roofline fraction is reported"}
+    return res, job
 
 
 def run_precision(args):
@@ -764,41 +812,20 @@ def run_precision(args):
     (float32; tf32 and bf16 operands split hi + lo on the tensor cores with float32 accumulation
     and the float64 Rayleigh-Ritz eigen step), the tensor-core kernels' achieved bandwidth and
     algorithmic tensor rate, and NRMSE of frame 1 against the FP64 oracle."""
-    import scipy.fft as sfft
     import torch
-    from oracle import lps_oracle as O
     from paper_1411_6206_gb300 import lps, phantom as P
     w = P.PRECISION
     T = max(2, min(args.precision_frames, w.frames))
     pr = P.problem(w, frames=T)
     dev = torch.device("cuda", 0)
     st = torch.cuda.Stream(device=dev)
-    coils = torch.from_numpy(np.ascontiguousarray(pr["coils"].astype(np.complex64))).to(dev)
-    masks = [np.ascontiguousarray(m) for m in pr["masks"]]
-    fwd = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=1)
-    fwd.set_coils(coils)
-    kd = []
-    with torch.cuda.stream(st):
-        for t in range(T):
-            n = fwd.set_mask(masks[t])
-            x = torch.from_numpy(np.ascontiguousarray(pr["x"][t].astype(np.complex64))).to(dev)
-            k = torch.empty((w.ncoil, n, w.nx), dtype=torch.complex64, device=dev)
-            lps.forward(fwd.handle, x, k)
-            k += torch.from_numpy(pr["noise"][t].astype(np.complex64)).to(dev)
-            kd.append(k)
-    st.synchronize()
-    fwd.close()
-    t0 = time.perf_counter()
-    with sfft.set_workers(os.cpu_count() or 1):
-        ref = O.priori_ls(kd[0].cpu().numpy().astype(np.complex128), pr["coils"].astype(np.complex64).astype(np.complex128),
-                          masks[0], O.Params(max_iters=w.iters))
-    oracle_s = time.perf_counter() - t0
+    coils, masks, kd = forward_frames(lps, w, pr, T, dev, st)
+    job = {"w": w, "coils": coils.cpu().numpy(), "mask": masks[0], "data": kd[0].cpu().numpy(), "recon": {}}
     hbm, _, src = peaks()
     bf16_peak, tf32_peak, psrc = tensor_peaks()
     N = w.nx * w.ny * w.nz
     out = {"workload": f"{w.nx}x{w.ny}x{w.nz} x {T} frames, {w.ncoil} coils, R={w.accel:g} (frame 1 at 50%), "
-                       f"{w.iters} iterations/frame, recursive",
-           "oracle_frame1_s": round(oracle_s, 1)}
+                       f"{w.iters} iterations/frame, recursive"}
     recon = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
     for name in ("fp32", "tf32", "bf16"):
         prec = {"fp32": lps.FP32, "tf32": lps.TF32_REFINE, "bf16": lps.BF16_REFINE}[name]
@@ -833,9 +860,9 @@ def run_precision(args):
         pl.set_data(kd[0])
         pl.reconstruct_frame(recon=recon, stats=False)
         st.synchronize()
-        err = O.nrmse(recon.cpu().numpy(), ref.recon)
+        job["recon"][name] = recon.cpu().numpy()
         pl.close()
-        row = {"frames_per_s": round(T / (ms / 1e3), 2), "nrmse_frame1_vs_oracle": round(err, 9),
+        row = {"frames_per_s": round(T / (ms / 1e3), 2),
                "eig": "fp32 Jacobi" if name == "fp32" else "fp32 Jacobi + fp64 Rayleigh-Ritz",
                "us_per_launch": {k: round(1e3 * v["ms"] / max(1, v["launches"]), 2) for k, v in kt.items()
                                  if v["launches"]}}
@@ -862,7 +889,52 @@ def run_precision(args):
                   "separate pass with events around every kernel; tensor_frac = algorithmic flops of the "
                   "contraction over the dense peak of the operand type (the split operands add products "
                   "executed on the pipe)")
-    return out
+    return out, job
+
+
+def run_fig3(args):
+    """Synthetic analogue of the paper's Fig. 3 (Sec. 4): mean PSNR against the ground-truth
+    phantom over frames 2-20 of the cardiac-shaped sequence, plain L+S (every frame without a
+    prior) against Priori L+S (the recursion of Sec. 3), at several undersampling factors;
+    frame 1 is sampled at 50% in both."""
+    import dataclasses
+    import torch
+    from paper_1411_6206_gb300 import lps, phantom as P
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    rows = []
+    for R in (4, 6, 8, 10, 12):
+        w = dataclasses.replace(P.CARDIAC, accel=float(R))
+        T = w.frames
+        pr = P.problem(w, frames=T)
+        coils, masks, kd = forward_frames(lps, w, pr, T, dev, st)
+        row = {"R": R, "sampling": round(1.0 / R, 4)}
+        for mode in ("plain", "priori"):
+            pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1)
+            pl.set_coils(coils)
+            out = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
+            ps = []
+            for t in range(T):
+                if mode == "plain" or t == 0:
+                    pl.clear_prior()
+                pl.set_mask(masks[t])
+                pl.set_data(kd[t])
+                pl.reconstruct_frame(recon=out, stats=False)
+                st.synchronize()
+                if t == 0:
+                    continue
+                x = pr["x"][t]
+                mse = float(np.mean(np.abs(out.cpu().numpy().astype(np.complex128) - x) ** 2))
+                ps.append(10.0 * np.log10(float(np.max(np.abs(x))) ** 2 / mse))
+            pl.close()
+            row[f"psnr_{mode}_db"] = round(float(np.mean(ps)), 3)
+        row["gain_db"] = round(row["psnr_priori_db"] - row["psnr_plain_db"], 3)
+        rows.append(row)
+    return {"rows": rows,
+            "how": "cardiac-shaped phantom family (128x128x16, 8 coils, beating heart on a rank-4 background), "
+                   "per-frame VD ky-kz masks at 1/R of the lines (frame 1 at 50%), 50 iterations per frame; "
+                   "PSNR = 10 log10(max|x|^2 / mean|recon - x|^2) against the phantom, mean over frames 2-20; "
+                   "plain = the prior cleared before every frame (plain L+S with its own lambdas)"}
 
 
 def tensor_peaks():
@@ -892,16 +964,26 @@ def main():
             out["served"] = run_served(args)
         if ws == 1 and not args.no_batched:
             out["batched"] = run_batched(args)
+        small_job = prec_job = None
         if ws == 1 and not args.no_small:
-            out["small"] = run_small(args)
+            out["small"], small_job = run_small(args)
         if ws == 1 and not args.no_precision:
-            out["precision"] = run_precision(args)
+            out["precision"], prec_job = run_precision(args)
+        if ws == 1 and not args.no_fig3:
+            out["fig3"] = run_fig3(args)
         if ws == 1 and not args.no_cpu_baseline:
             cb, nr = cpu_baseline(args, w)
             out["cpu_baseline"] = cb
             out["nrmse_vs_oracle"] = {"max": max(nr), "per_frame": nr,
                                       "how": "GPU recursive frames vs the FP64 oracle on the same "
                                              "samples and the same prior; bound 1e-3"}
+            par = cpu_parity(small_job, prec_job)
+            if "small" in par:
+                out["small"]["nrmse_vs_oracle"] = par["small"]
+            if "precision" in par:
+                for k, v in par["precision"].items():
+                    out["precision"][k]["nrmse_frame1_vs_oracle"] = v
+                out["precision"]["oracle_frame1_s"] = par["precision_oracle_s"]
         print(json.dumps(out), flush=True)
 
 
