@@ -892,6 +892,54 @@ def run_precision(args):
     return out, job
 
 
+def run_coils_fp16(args):
+    """The cardiac-shaped sequence with the coil maps stored in half precision (LPS_COILS_FP16):
+    frames/s and the data-consistency kernel's time per launch against float32 maps."""
+    import torch
+    from paper_1411_6206_gb300 import lps, phantom as P
+    w = P.CARDIAC
+    T = w.frames
+    pr = P.problem(w, frames=T)
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.Stream(device=dev)
+    coils, masks, kd = forward_frames(lps, w, pr, T, dev, st)
+    out = {}
+    recon = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for name, fmt in (("fp32", lps.COILS_FP32), ("fp16", lps.COILS_FP16)):
+        pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1, coil_format=fmt)
+        pl.set_coils(coils)
+
+        def seq():
+            pl.clear_prior()
+            for t in range(T):
+                pl.set_mask(masks[t])
+                pl.set_data(kd[t])
+                pl.reconstruct_frame(recon=recon[t], stats=False)
+
+        seq()
+        ms = []
+        for _ in range(3):
+            with torch.cuda.stream(st):
+                flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            seq()
+            e1.record(st)
+            st.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        lps.set_profiling(pl.handle, True)
+        seq()
+        st.synchronize()
+        kt = lps.get_kernel_times(pl.handle).as_dict()["data_consistency"]
+        pl.close()
+        out[name] = {"frames_per_s": round(T / (float(np.median(ms)) / 1e3), 2),
+                     "dc_us_per_launch": round(1e3 * kt["ms"] / max(1, kt["launches"]), 2)}
+    out["how"] = ("same inputs, float32 maps given to both plans (the fp16 plan rounds them); the effect of the "
+                  "rounding on the reconstruction is measured by tests/test_gpu_coils_fp16.py")
+    return out
+
+
 def run_fig3(args):
     """Synthetic analogue of the paper's Fig. 3 (Sec. 4): mean PSNR against the ground-truth
     phantom over frames 2-20 of the cardiac-shaped sequence, plain L+S (every frame without a
@@ -971,6 +1019,8 @@ def main():
             out["precision"], prec_job = run_precision(args)
         if ws == 1 and not args.no_fig3:
             out["fig3"] = run_fig3(args)
+        if ws == 1 and not args.no_small:
+            out["coils_fp16"] = run_coils_fp16(args)
         if ws == 1 and not args.no_cpu_baseline:
             cb, nr = cpu_baseline(args, w)
             out["cpu_baseline"] = cb

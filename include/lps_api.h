@@ -93,6 +93,16 @@ extern "C" {
 
 #define LPS_MAX_NC            32  /* largest Casorati column count (slices) supported      */
 
+/* Storage of the coil maps (the acquisition operator's C_c, Sec. 2). With LPS_COILS_FP16 the
+ * plan rounds the complex64 maps given to lps_set_coils to half precision (each of Re and Im
+ * to the nearest IEEE binary16) and every operator of the plan uses the rounded maps; the
+ * per-iteration data-consistency kernels of 128 x 16 planes and the runtime-sized kernel
+ * reading coil maps from global memory read them as 4-byte half pairs, half the coil-map
+ * bytes of an iteration. |Re|, |Im| must stay below 65504 (maps normalised to unit sum of
+ * squares do). Maps that are already half-representable give results equal to LPS_COILS_FP32. */
+#define LPS_COILS_FP32         0
+#define LPS_COILS_FP16         1
+
 typedef struct lps_plan lps_plan;   /* opaque; owns its device workspace */
 
 typedef struct lps_params {
@@ -111,7 +121,8 @@ typedef struct lps_params {
   int support_rule;        /* LPS_SUPPORT_THRESHOLD | LPS_SUPPORT_NONZERO                   */
   int recursive;           /* 1: each lps_reconstruct_frame installs its support and sigma
                               as the prior of the next call (the recursion of Sec. 3)        */
-  int reserved[8];         /* must be zero                                                  */
+  int coil_format;         /* LPS_COILS_FP32 (default) | LPS_COILS_FP16                      */
+  int reserved[7];         /* must be zero                                                  */
 } lps_params;
 
 typedef struct lps_stats {

@@ -20,8 +20,11 @@ namespace lps {
 // STAGE: coil planes staged in shared memory by TMA (1 CTA per SM for large planes); without,
 // the coil values are read from global memory (L2) where they are used, which halves the
 // shared memory so that two CTAs share an SM.
-template <int EPT, int MODE, bool STAGE>
+// HALF (direct reads of the update only): coil maps read as half-precision pairs
+// (LPS_COILS_FP16), widened exactly to float32.
+template <int EPT, int MODE, bool STAGE, bool HALF>
 __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) {
+  static_assert(!(HALF && (STAGE || MODE != kDcUpdate)), "half-precision coil maps: direct update only");
   const Geom& g = a.g;
   pdl_trigger();
   pdl_wait();
@@ -156,6 +159,8 @@ __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) 
     const int s = c & 1;
     float2* coil = s ? coilS1 : coilS0;
     const float2* gcoil = a.coils + (long long)c * g.N + (long long)x * ny;   // without staging
+    const __half2* hcoil = HALF ? a.coils_h + (long long)c * g.N + (long long)x * ny : nullptr;
+    auto gc = [&](int k) -> float2 { return HALF ? __half22float2(__ldg(hcoil + go[k])) : __ldg(gcoil + go[k]); };
     if (STAGE) {
       const bool bad = !mbar_wait_bounded(&mbar[s], (c >> 1) & 1, errp);
       if (__syncthreads_or(bad)) {
@@ -173,7 +178,7 @@ __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) 
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
         const int e = tid + k * kThreads;
-        if (e < plane) src[pe[k]] = cscale(cmul(STAGE ? coil[e] : __ldg(gcoil + go[k]), Zr[k]), sc);
+        if (e < plane) src[pe[k]] = cscale(cmul(STAGE ? coil[e] : gc(k), Zr[k]), sc);
       }
       __syncthreads();
       fft_run(&src, &dst, g.py, nz, 1, nyp, twy, false);
@@ -219,7 +224,7 @@ __global__ void __launch_bounds__(kThreads, STAGE ? 1 : 2) k_dc(const DcArgs a) 
       const int e = tid + k * kThreads;
       if (e < plane) {
         const float2 r = src[pe[k]];
-        const float2 cc = STAGE ? coil[e] : __ldg(gcoil + go[k]);
+        const float2 cc = STAGE ? coil[e] : gc(k);
         const float2 v = cmulc(cc, r);   // conj(C) * r
         acc[k].x = fmaf(v.x, sc, acc[k].x);
         acc[k].y = fmaf(v.y, sc, acc[k].y);
@@ -306,36 +311,42 @@ size_t dc_smem_bytes(const Geom& g) {
   return b;
 }
 
-template <int EPT, int MODE, bool STAGE>
+template <int EPT, int MODE, bool STAGE, bool HALF>
 static cudaError_t launch_dc_t(const DcArgs& a, cudaStream_t st) {
   const size_t smem = dc_smem_bytes(a.g);
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_dc<EPT, MODE, STAGE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_dc<EPT, MODE, STAGE, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)227 * 1024);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_dc<EPT, MODE, STAGE>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
+  cudaError_t e = launch_pdl(k_dc<EPT, MODE, STAGE, HALF>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
-template <int MODE, bool STAGE>
+template <int MODE, bool STAGE, bool HALF>
 static cudaError_t launch_dc_m(const DcArgs& a, cudaStream_t st) {
   switch (dc_ept(a.g)) {
-    case 1: return launch_dc_t<1, MODE, STAGE>(a, st);
-    case 2: return launch_dc_t<2, MODE, STAGE>(a, st);
-    case 4: return launch_dc_t<4, MODE, STAGE>(a, st);
-    case 8: return launch_dc_t<8, MODE, STAGE>(a, st);
-    case 16: return launch_dc_t<16, MODE, STAGE>(a, st);
-    case 24: return launch_dc_t<24, MODE, STAGE>(a, st);
+    case 1: return launch_dc_t<1, MODE, STAGE, HALF>(a, st);
+    case 2: return launch_dc_t<2, MODE, STAGE, HALF>(a, st);
+    case 4: return launch_dc_t<4, MODE, STAGE, HALF>(a, st);
+    case 8: return launch_dc_t<8, MODE, STAGE, HALF>(a, st);
+    case 16: return launch_dc_t<16, MODE, STAGE, HALF>(a, st);
+    case 24: return launch_dc_t<24, MODE, STAGE, HALF>(a, st);
     default: return cudaErrorInvalidValue;
   }
 }
 
+// Staged coil planes are copied in float32 (the rounded maps); the direct variant of the update
+// reads the half-precision copy when the plan keeps one.
 template <int MODE>
 static cudaError_t launch_dc_s(const DcArgs& a, cudaStream_t st) {
-  return a.g.dc_direct ? launch_dc_m<MODE, false>(a, st) : launch_dc_m<MODE, true>(a, st);
+  if (!a.g.dc_direct) return launch_dc_m<MODE, true, false>(a, st);
+  if constexpr (MODE == kDcUpdate) {
+    if (a.coils_h) return launch_dc_m<MODE, false, true>(a, st);
+  }
+  return launch_dc_m<MODE, false, false>(a, st);
 }
 
 cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st);

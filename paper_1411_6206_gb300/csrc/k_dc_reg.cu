@@ -51,7 +51,8 @@ struct RegLayout {
   }
 };
 
-template <int G, bool FFTZ, bool ONE, bool ACCS>
+// HALF: coil maps read as half-precision pairs (LPS_COILS_FP16), widened exactly to float32.
+template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF>
 __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   using Lay = RegLayout<G, ACCS>;
   static_assert(!(ONE && ACCS), "one coil per group needs no accumulator");
@@ -199,11 +200,13 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   }
   for (int c = grp; c < ncoil; c += G) {
     const float2* Cc = a.coils + (long long)c * g.N + xoff + gt;
+    const __half2* Ch = HALF ? a.coils_h + (long long)c * g.N + xoff + gt : nullptr;
+    auto coil = [&](int z) -> float2 { return HALF ? __half22float2(__ldg(Ch + z * xy)) : __ldg(Cc + z * xy); };
     const float2* dh = a.dhyb + ((long long)x * ncoil + c) * g.mpad;
     // column phase: v[z] = sc C_c Z at (z, y = gt), transform along z
     const bool first = c == grp;
 #pragma unroll
-    for (int z = 0; z < kNZ; ++z) v[z] = cscale(cmul(__ldg(Cc + z * xy), zs[z * kRS + gt]), sc);
+    for (int z = 0; z < kNZ; ++z) v[z] = cscale(cmul(coil(z), zs[z * kRS + gt]), sc);
     if (FFTZ) dft16(v, false);
 #pragma unroll
     for (int k = 0; k < kNZ; ++k) B[k * kRS + gt] = v[k];
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     if (FFTZ) dft16(v, true);
 #pragma unroll
     for (int z = 0; z < kNZ; ++z) {
-      const float2 t = cmulc(__ldg(Cc + z * xy), v[z]);
+      const float2 t = cmulc(coil(z), v[z]);
       if constexpr (ONE) {
         B[z * kRS + gt] = make_float2(t.x * sc, t.y * sc);   // fmaf(t, sc, 0) rounds the same
       } else if constexpr (ACCS) {
@@ -357,14 +360,14 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   }
 }
 
-template <int G, bool FFTZ, bool ONE, bool ACCS>
+template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF>
 cudaError_t launch_reg(const DcArgs& a, cudaStream_t st) {
   constexpr size_t smem = RegLayout<G, ACCS>::bytes();
   static_assert(smem <= 227 * 1024, "shared memory");
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_dc_reg<G, FFTZ, ONE, ACCS>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dc_reg<G, FFTZ, ONE, ACCS, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -382,7 +385,7 @@ cudaError_t launch_reg(const DcArgs& a, cudaStream_t st) {
   attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dc_reg<G, FFTZ, ONE, ACCS>, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dc_reg<G, FFTZ, ONE, ACCS, HALF>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -400,16 +403,21 @@ cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st) {
   if (!dc_reg_applies(a.g)) return cudaErrorNotSupported;
   const bool fz = a.g.fft_z != 0;
   // dc_reg_groups: 4 or 8 coil groups; 104: four groups with their coil sums in shared memory
-  // (used when there are more coils than groups)
+  // (used when there are more coils than groups). Half-precision coil maps: four groups.
   const bool accs = a.g.dc_reg_groups > 100;
+  if (a.coils_h && a.g.dc_reg_groups % 100 == 4) {
+    if (a.g.ncoil <= 4) return fz ? launch_reg<4, true, true, false, true>(a, st) : launch_reg<4, false, true, false, true>(a, st);
+    if (accs) return fz ? launch_reg<4, true, false, true, true>(a, st) : launch_reg<4, false, false, true, true>(a, st);
+    return fz ? launch_reg<4, true, false, false, true>(a, st) : launch_reg<4, false, false, false, true>(a, st);
+  }
   switch (a.g.dc_reg_groups % 100) {
     case 4:
-      if (a.g.ncoil <= 4) return fz ? launch_reg<4, true, true, false>(a, st) : launch_reg<4, false, true, false>(a, st);
-      if (accs) return fz ? launch_reg<4, true, false, true>(a, st) : launch_reg<4, false, false, true>(a, st);
-      return fz ? launch_reg<4, true, false, false>(a, st) : launch_reg<4, false, false, false>(a, st);
+      if (a.g.ncoil <= 4) return fz ? launch_reg<4, true, true, false, false>(a, st) : launch_reg<4, false, true, false, false>(a, st);
+      if (accs) return fz ? launch_reg<4, true, false, true, false>(a, st) : launch_reg<4, false, false, true, false>(a, st);
+      return fz ? launch_reg<4, true, false, false, false>(a, st) : launch_reg<4, false, false, false, false>(a, st);
     case 8:
-      if (a.g.ncoil <= 8) return fz ? launch_reg<8, true, true, false>(a, st) : launch_reg<8, false, true, false>(a, st);
-      return fz ? launch_reg<8, true, false, false>(a, st) : launch_reg<8, false, false, false>(a, st);
+      if (a.g.ncoil <= 8) return fz ? launch_reg<8, true, true, false, false>(a, st) : launch_reg<8, false, true, false, false>(a, st);
+      return fz ? launch_reg<8, true, false, false, false>(a, st) : launch_reg<8, false, false, false, false>(a, st);
     default: return cudaErrorNotSupported;
   }
 }

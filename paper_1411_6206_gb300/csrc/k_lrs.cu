@@ -263,6 +263,20 @@ __global__ void k_combine(const float2* __restrict__ L, const float2* __restrict
     out[i] = cadd(L[i], S[i]);
 }
 
+__global__ void k_round_half(float2* __restrict__ c, __half2* __restrict__ h, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const __half2 v = __float22half2_rn(c[i]);
+    h[i] = v;
+    c[i] = __half22float2(v);
+  }
+}
+
+cudaError_t launch_round_half(float2* c, __half2* h, long long n, cudaStream_t st) {
+  const int blocks = (int)std::min<long long>((n + kThreads - 1) / kThreads, 152 * 16);
+  k_round_half<<<blocks, kThreads, 0, st>>>(c, h, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long long n, cudaStream_t st) {
   const int blocks = (int)std::min<long long>((n + kThreads - 1) / kThreads, 152LL * 8);
   k_combine<<<blocks, kThreads, 0, st>>>(L, S, out, n);

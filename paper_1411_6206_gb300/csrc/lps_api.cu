@@ -171,6 +171,8 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->eig_precision == LPS_EIG_FP32 || p->eig_precision == LPS_EIG_FP64, "bad eig_precision");
   ARG(p->support_rule == 0 || p->support_rule == 1, "bad support_rule");
   ARG(p->recursive == 0 || p->recursive == 1, "recursive must be 0 or 1");
+  ARG(p->coil_format == LPS_COILS_FP32 || p->coil_format == LPS_COILS_FP16,
+      "coil_format must be LPS_COILS_FP32 or LPS_COILS_FP16");
   if (p->nz > LPS_MAX_NC) {
     set_err("nz = %d exceeds LPS_MAX_NC = %d", p->nz, LPS_MAX_NC);
     return LPS_ERR_UNSUPPORTED;
@@ -218,7 +220,7 @@ int free_plan(lps_plan* P) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->graph) cudaGraphDestroy(P->graph);
   void* bufs[] = {P->X, P->L, P->S, P->S2, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena,
-                  P->Lnew};
+                  P->Lnew, P->coils_h};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
@@ -293,6 +295,7 @@ DcArgs dc_args(lps_plan* P) {
   DcArgs a{};
   a.g = P->g;
   a.coils = P->coils;
+  a.coils_h = P->coils_h;
   a.dhyb = P->dhyb;
   a.lines = P->lines;
   a.tw_y = P->tw_y;
@@ -691,6 +694,7 @@ int lps_estimate_device_bytes(const lps_params* p, size_t* bytes) {
   b += 4 * N * 8;                              // X, L, S, recon
   if (p->precision != LPS_FP32) b += N * 8;    // reprojection output
   b += (size_t)g.ncoil * N * 8;                // coils
+  if (p->coil_format == LPS_COILS_FP16) b += (size_t)g.ncoil * N * 4;   // half-precision copy
   b += 3 * ((size_t)g.nx * g.ncoil * m + 4) * 8;   // hybrid data, k-space staging, scratch
   b += (size_t)gram_part_capacity(g) * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
   b += (size_t)g.nx * 4 + (size_t)g.ntiles * 16 + 2 * N / 8;
@@ -721,6 +725,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = dalloc(P, &P->R, N))) return fail(rc);
   if ((rc = dalloc(P, &P->istage, N))) return fail(rc);
   if ((rc = dalloc(P, &P->coils, N * g.ncoil))) return fail(rc);
+  if (p->coil_format == LPS_COILS_FP16 && (rc = dalloc(P, &P->coils_h, N * g.ncoil))) return fail(rc);
   if (p->precision != LPS_FP32 && (rc = dalloc(P, &P->Lnew, N))) return fail(rc);
   P->arena_bytes = arena_size(g, p->max_iters);
   if ((rc = dalloc(P, &P->arena, P->arena_bytes))) return fail(rc);
@@ -809,6 +814,7 @@ int lps_set_coils(lps_plan* P, const void* coils) {
   ARG(P != nullptr && coils != nullptr, "NULL argument");
   CK(cudaMemcpyAsync(P->coils, coils, (size_t)P->g.N * P->g.ncoil * sizeof(float2), cudaMemcpyDefault,
                      P->st));
+  if (P->coils_h) LK(launch_round_half(P->coils, P->coils_h, (long long)P->g.N * P->g.ncoil, P->st));
   P->have_coils = true;
   return LPS_OK;
 }

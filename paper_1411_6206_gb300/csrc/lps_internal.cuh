@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <utility>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 namespace lps {
@@ -99,6 +100,7 @@ struct DcArgs {
   float2* S_out;            // adjoint: zero S
   float2* recon;            // update: optional copy of Z = L + S
   const float2* coils;      // [ncoil][nz][nx][ny]
+  const __half2* coils_h;   // the same maps in half precision (LPS_COILS_FP16), else nullptr
   const float2* dhyb;       // [nx][ncoil][mpad] hybrid-space samples
   float2* hyb_out;          // forward: [nx][ncoil][mpad]
   const int* lines;         // padded in-plane position kz*nyp + ky of each line
@@ -212,6 +214,9 @@ cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);
 cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, cudaStream_t st);
+// Rounds n complex values to half precision: h = the rounded pairs, c rewritten with their
+// float32 values (so that every kernel reads the same maps).
+cudaError_t launch_round_half(float2* c, __half2* h, long long n, cudaStream_t st);
 cudaError_t launch_settle(const DevCtrl* ctrl, int k0, float2* S0, const float2* S1, long long n, uint32_t* sup0,
                           const uint32_t* sup1, long long nw, float* part0, const float* part1, int np,
                           cudaStream_t st);

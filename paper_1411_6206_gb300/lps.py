@@ -28,6 +28,7 @@ ERR_STATE = -7
 ERR_UNSUPPORTED = -8
 
 LAYOUT_SLICES, LAYOUT_FRAMES = 0, 1
+COILS_FP32, COILS_FP16 = 0, 1
 EIG_FP32, EIG_FP64 = 0, 1
 FP32, TF32_REFINE, BF16_REFINE = 0, 1, 2
 KERNEL_CLASSES = 6
@@ -43,7 +44,7 @@ class Params(C.Structure):
                 ("lambda_L_rel", C.c_double), ("lambda_S_rel", C.c_double),
                 ("lambda_p", C.c_double), ("rank_tau", C.c_double), ("tol", C.c_double),
                 ("precision", C.c_int), ("eig_precision", C.c_int), ("support_rule", C.c_int),
-                ("recursive", C.c_int), ("reserved", C.c_int * 8)]
+                ("recursive", C.c_int), ("coil_format", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class Stats(C.Structure):

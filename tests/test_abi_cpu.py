@@ -47,7 +47,7 @@ def test_params_defaults_and_status_strings(lps):
 @pytest.mark.parametrize("bad,code", [
     (dict(nx=12), -1), (dict(ny=0), -1), (dict(ncoil=0), -1), (dict(wavelet_levels=4), -1),
     (dict(lambda_p=1.5), -1), (dict(layout=2), -1), (dict(layout=1), -8), (dict(precision=3), -1),
-    (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1),
+    (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1), (dict(coil_format=2), -1),
 ])
 def test_plan_create_rejects_bad_params(lps, bad, code):
     kw = dict(nx=32, ny=32, nz=8, ncoil=2)
@@ -64,6 +64,17 @@ def test_estimate_device_bytes(lps):
     N = 128 * 128 * 16
     assert 8 * N * 12 < b < 8 * N * 40
     assert lps.support_words(p) == N // 32
+
+
+def test_half_precision_coil_maps_are_an_extra_copy(lps):
+    """LPS_COILS_FP16 keeps a half-precision copy of the maps next to the rounded complex64
+    ones: ncoil * N * 4 more bytes; the header and the binding agree on the constants."""
+    hdr = open(os.path.join(ROOT, "include", "lps_api.h")).read()
+    assert re.search(r"#define LPS_COILS_FP32\s+0\b", hdr) and re.search(r"#define LPS_COILS_FP16\s+1\b", hdr)
+    kw = dict(nx=128, ny=128, nz=16, ncoil=8)
+    b32 = lps.estimate_device_bytes(lps.params_init(coil_format=lps.COILS_FP32, **kw))
+    b16 = lps.estimate_device_bytes(lps.params_init(coil_format=lps.COILS_FP16, **kw))
+    assert b16 - b32 == 8 * 128 * 128 * 16 * 4
 
 
 def test_frames_layout_is_the_per_frame_2d_encode(lps):
