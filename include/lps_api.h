@@ -122,7 +122,10 @@ typedef struct lps_params {
   int recursive;           /* 1: each lps_reconstruct_frame installs its support and sigma
                               as the prior of the next call (the recursion of Sec. 3)        */
   int coil_format;         /* LPS_COILS_FP32 (default) | LPS_COILS_FP16                      */
-  int reserved[7];         /* must be zero                                                  */
+  int nx_total;            /* 0: the plan holds the whole volume; else the x extent of the
+                              volume of which it holds planes x0 .. x0+nx-1 (lps_slab_*)     */
+  int x0;                  /* first plane of the slab (multiple of 8)                       */
+  int reserved[5];         /* must be zero                                                  */
 } lps_params;
 
 typedef struct lps_stats {
@@ -340,6 +343,38 @@ int lps_get_kernel_times(lps_plan* plan, lps_kernel_times* out);
  * buffer. With buf NULL, *bytes receives the size needed. */
 int lps_session_export(lps_plan* plan, void* buf, size_t* bytes);
 int lps_session_import(lps_plan* plan, const void* buf, size_t bytes);
+
+/* ---- x-slab sharding of one problem -------------------------------------------------
+ * Not in the paper, which reconstructs each volume whole. Once the samples are moved to the
+ * hybrid (x, ky, kz) space, steps (3) and (4) of Algorithm 1 (Sec. 3) act on every x-plane
+ * alone (the Haar tiles are 8 planes wide), so a volume splits into slabs of whole tiles held
+ * by separate plans (one per GPU): a plan with nx_total > 0 holds planes x0 .. x0+nx-1 of a
+ * volume of nx_total planes; its coil maps and outputs are the slab's ([c][z][x0..][y]),
+ * lps_set_data takes whole readouts ([ncoil][nlines][nx_total]) and lps_forward returns the
+ * slab's share of E x (the slabs' outputs add up to E x). The only sums over all planes are
+ * the Casorati Gram of step (1) and a few scalars (residual, change and l1 statistics), plus
+ * the maximum of |T(X_0)| that fixes lambda_S: each iteration leaves the slab's share of them
+ * in a small record, the caller reduces the records of all slabs (for instance with one
+ * all-reduce), and the next iteration repeats the n x n eigendecomposition on every slab from
+ * the reduced record. The record is float32, device memory owned by the caller:
+ *   [0, sum_floats)  to be summed over the slabs: data-consistency statistics (4), sparse-step
+ *                    statistics (2, then 2 zeros), the Gram (2 nz^2, complex row-major);
+ *   [sum_floats, sum_floats + max_floats)  to be maximised over the slabs: max |T(X_0)|.
+ * Sequence per frame: lps_slab_begin (step 0), reduce; for k = 1..K: lps_slab_iterate(k),
+ * reduce; lps_slab_end. Work is enqueued on the plan's stream; the reduction must be ordered
+ * after the call that wrote the record and before the next call (same stream, or events).
+ * lps_reconstruct_frame and lps_iterate return LPS_ERR_STATE for a plan that holds a slab. */
+int lps_slab_reduction_size(const lps_plan* plan, size_t* sum_floats, size_t* max_floats);
+/* Step (0) on the slab; needs lps_set_coils, lps_set_mask and lps_set_data. */
+int lps_slab_begin(lps_plan* plan, float* rec);
+/* Iteration k (1, 2, ... in order, at most max_iters) from the reduced record; leaves the
+ * slab's share of iteration k in rec. Stops doing work once the tol rule has stopped the frame
+ * (every slab takes the same decision from the same reduced record). */
+int lps_slab_iterate(lps_plan* plan, float* rec, int k);
+/* After the last iteration and its reduction: statistics of the frame (support_count is the
+ * slab's own), outputs settled for lps_get_recon / lps_get_state / lps_get_support, and for a
+ * recursive plan the prior of the next frame installed. Synchronises the plan's stream. */
+int lps_slab_end(lps_plan* plan, const float* rec, lps_stats* stats);
 
 /* Adjoint operator E^H without any device allocation. The paper has no counterpart: this
  * entry point exists for callers that cannot allocate device memory when they need the

@@ -344,12 +344,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
   if (stats_on && (tid >> 5) == sw) {
     const int lane = tid & 31;
     const float4* dc4 = reinterpret_cast<const float4*>(a.dc_part);
-    for (int i0 = 0; i0 < a.g.nx; i0 += 256) {
+    for (int i0 = 0; i0 < a.ndc; i0 += 256) {
       float4 q[8];
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
         const int i = i0 + lane + 32 * u;
-        q[u] = i < a.g.nx ? dc4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
+        q[u] = i < a.ndc ? dc4[i] : make_float4(0.f, 0.f, 0.f, 0.f);
       }
 #pragma unroll
       for (int u = 0; u < 8; ++u) {

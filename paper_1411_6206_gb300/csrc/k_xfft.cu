@@ -12,10 +12,13 @@ namespace lps {
 
 constexpr int kLines = 16;
 
+// A plan that holds a slab of the volume (planes x0 .. x0+nx-1 of nxt) transforms whole
+// readouts of nxt samples; the inverse keeps its own planes, the forward takes the planes it
+// does not hold as zero (its output is the slab's share of E x, which the slabs add up).
 __global__ void __launch_bounds__(kThreads) k_xfft(const XfftArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const Geom& g = a.g;
-  const int nx = g.nx, nxp = nx + 1;
+  const int nx = g.nxt, nxp = nx + 1, x0 = g.x0, nxl = g.nx;
   float2* bufA = reinterpret_cast<float2*>(smem);
   float2* bufB = bufA + kLines * nxp;
   float2* tw = bufB + kLines * nxp;
@@ -36,8 +39,9 @@ __global__ void __launch_bounds__(kThreads) k_xfft(const XfftArgs a) {
   } else {
     for (int e = tid; e < tot; e += kThreads) {
       const int x = e / kLines, l = e - (e / kLines) * kLines;
-      bufA[l * nxp + x] = (l < nl) ? a.in[((long long)x * g.ncoil + c) * g.mpad + l0 + l]
-                                   : make_float2(0.f, 0.f);
+      const int xl = x - x0;
+      bufA[l * nxp + x] = (l < nl && xl >= 0 && xl < nxl) ? a.in[((long long)xl * g.ncoil + c) * g.mpad + l0 + l]
+                                                          : make_float2(0.f, 0.f);
     }
   }
   __syncthreads();
@@ -46,9 +50,9 @@ __global__ void __launch_bounds__(kThreads) k_xfft(const XfftArgs a) {
   fft_run(&s, &d, g.px, kLines, 1, nxp, tw, a.inverse != 0);
   const float sc = g.scale_x;
   if (a.inverse) {
-    for (int e = tid; e < tot; e += kThreads) {
-      const int x = e / kLines, l = e - (e / kLines) * kLines;
-      if (l < nl) a.out[((long long)x * g.ncoil + c) * g.mpad + l0 + l] = cscale(s[l * nxp + x], sc);
+    for (int e = tid; e < kLines * nxl; e += kThreads) {
+      const int xl = e / kLines, l = e - (e / kLines) * kLines;
+      if (l < nl) a.out[((long long)xl * g.ncoil + c) * g.mpad + l0 + l] = cscale(s[l * nxp + x0 + xl], sc);
     }
   } else {
     float2* dst = a.out + ((long long)c * m + l0) * nx;
@@ -60,7 +64,7 @@ __global__ void __launch_bounds__(kThreads) k_xfft(const XfftArgs a) {
 }
 
 size_t xfft_smem_bytes(const Geom& g) {
-  return (size_t)(2 * kLines * (g.nx + 1) + g.nx) * sizeof(float2);
+  return (size_t)(2 * kLines * (g.nxt + 1) + g.nxt) * sizeof(float2);
 }
 
 // Grid: (ceil(nlines_cap / kLines), ncoil); CTAs past the current line count exit.

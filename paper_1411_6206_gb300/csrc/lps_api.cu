@@ -30,6 +30,70 @@ void set_err(const char* fmt, ...) {
 
 }  // namespace lps
 
+namespace lps {
+
+// The slab's share of the reduction record of x-slab sharding, summed in a fixed order: the
+// Gram partials (entry by entry over the partials), the data-consistency statistics and the
+// sparse step's (a warp each, lanes then shuffles), and max |T(X_0)| from the control block.
+__global__ void __launch_bounds__(256) k_slab_pack(const float2* __restrict__ gram_part, int nparts, int nc,
+                                                   const float* __restrict__ dc_part, int ndc,
+                                                   const float* __restrict__ lrs_part, int nlrs,
+                                                   const DevCtrl* __restrict__ ctrl, float* __restrict__ rec) {
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  float2* G = reinterpret_cast<float2*>(rec + kSlabRecHead);
+  const int nn = nc * nc;
+  for (int e = tid; e < nn; e += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int q = 0; q < nparts; ++q) acc = cadd(acc, gram_part[(long long)q * nn + e]);
+    G[e] = acc;
+  }
+  if (w == 0) {
+    float r2 = 0.f, d2 = 0.f, o2 = 0.f;
+    for (int i = lane; i < ndc; i += 32) {
+      const float4 q = reinterpret_cast<const float4*>(dc_part)[i];
+      r2 += q.x;
+      d2 += q.y;
+      o2 += q.z;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      r2 += __shfl_xor_sync(0xffffffffu, r2, o);
+      d2 += __shfl_xor_sync(0xffffffffu, d2, o);
+      o2 += __shfl_xor_sync(0xffffffffu, o2, o);
+    }
+    if (lane == 0) {
+      rec[0] = r2;
+      rec[1] = d2;
+      rec[2] = o2;
+      rec[3] = 0.f;
+    }
+  } else if (w == 1) {
+    float l1 = 0.f, cnt = 0.f;
+    for (int i = lane; i < nlrs; i += 32) {
+      l1 += lrs_part[2 * i];
+      cnt += lrs_part[2 * i + 1];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      l1 += __shfl_xor_sync(0xffffffffu, l1, o);
+      cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    }
+    if (lane == 0) {
+      rec[4] = l1;
+      rec[5] = cnt;
+      rec[6] = rec[7] = 0.f;
+    }
+  } else if (tid == 64) {
+    rec[kSlabRecHead + 2 * nn] = __uint_as_float(ctrl->haar_max_bits);
+  }
+}
+
+cudaError_t launch_slab_pack(const float2* gram_part, int nparts, int nc, const float* dc_part, int ndc,
+                             const float* lrs_part, int nlrs, const DevCtrl* ctrl, float* rec, cudaStream_t st) {
+  k_slab_pack<<<1, 256, 0, st>>>(gram_part, nparts, nc, dc_part, ndc, lrs_part, nlrs, ctrl, rec);
+  return cudaGetLastError();
+}
+
+}  // namespace lps
+
 namespace {
 
 bool make_fft_plan(int n, FftPlan& p) {
@@ -135,7 +199,7 @@ size_t arena_size(const Geom& g, int max_iters) {
   s += r((size_t)gram_part_capacity(g) * g.nc * g.nc * sizeof(float2));   // gram partials
   s += 4 * r((size_t)g.nc * g.nc * sizeof(float2));      // W, V, float64 mode: Gram, refined V
   s += r((size_t)g.nc * g.nc * sizeof(double2)) + r((size_t)g.nc * sizeof(double));   // A, eigenvalues
-  s += r((size_t)g.nx * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
+  s += r((size_t)g.nxt * sizeof(float2)) + r((size_t)g.ny * sizeof(float2)) + r((size_t)g.nz * sizeof(float2));
   s += r((size_t)g.plane * sizeof(int));                  // line table
   s += r((size_t)g.nx * 4 * sizeof(float)) + 2 * r((size_t)g.ntiles * 2 * sizeof(float));   // statistic partials
   s += 2 * r((size_t)g.nc * sizeof(double));
@@ -177,8 +241,15 @@ int validate(const lps_params* p, Geom* gout) {
     set_err("nz = %d exceeds LPS_MAX_NC = %d", p->nz, LPS_MAX_NC);
     return LPS_ERR_UNSUPPORTED;
   }
+  // x-slab of a larger volume: nx_total = 0 means the whole volume
+  const int nxt = p->nx_total ? p->nx_total : p->nx;
+  ARG(p->nx_total == 0 || (p->nx_total >= p->nx && p->nx_total <= 1024 && p->nx_total % 8 == 0),
+      "nx_total must be 0 or a multiple of 8 in nx..1024");
+  ARG(p->x0 >= 0 && p->x0 % 8 == 0 && p->x0 + p->nx <= nxt, "x0 must be a multiple of 8 with x0 + nx <= nx_total");
   Geom g{};
   g.nx = p->nx;
+  g.nxt = nxt;
+  g.x0 = p->x0;
   g.ny = p->ny;
   g.nz = p->nz;
   g.ncoil = p->ncoil;
@@ -191,8 +262,8 @@ int validate(const lps_params* p, Geom* gout) {
   g.ntiles = (p->nx / 8) * (p->ny / 8);
   g.N = (long long)p->nx * p->ny * p->nz;
   g.scale_yz = (float)(1.0 / std::sqrt((double)p->ny * (p->fft_z ? p->nz : 1)));
-  g.scale_x = (float)(1.0 / std::sqrt((double)p->nx));
-  if (!make_fft_plan(p->ny, g.py) || !make_fft_plan(p->nz, g.pz) || !make_fft_plan(p->nx, g.px)) {
+  g.scale_x = (float)(1.0 / std::sqrt((double)nxt));
+  if (!make_fft_plan(p->ny, g.py) || !make_fft_plan(p->nz, g.pz) || !make_fft_plan(nxt, g.px)) {
     set_err("FFT lengths need prime factors <= 64 and at most %d passes", kMaxPasses);
     return LPS_ERR_UNSUPPORTED;
   }
@@ -283,7 +354,7 @@ int ensure_lines(lps_plan* P, int m) {
   const size_t hyb = (size_t)P->g.nx * P->g.ncoil * cap + 4;
   int rc;
   if ((rc = dalloc(P, &P->dhyb, hyb))) return rc;
-  if ((rc = dalloc(P, &P->kstage, (size_t)P->g.ncoil * cap * P->g.nx + 4))) return rc;
+  if ((rc = dalloc(P, &P->kstage, (size_t)P->g.ncoil * cap * P->g.nxt + 4))) return rc;
   if ((rc = dalloc(P, &P->hscratch, hyb))) return rc;
   P->m_cap = cap;
   P->g.mpad = cap;
@@ -389,8 +460,18 @@ EigArgs eig_args(lps_plan* P, int iter, int finalize, int i) {
   e.gram_part = P->gram_part;
   e.nparts = gram_parts(P->g, P->p.precision);
   e.dc_part = P->dc_part;
+  e.ndc = P->g.nx;
   e.lrs_part = (i & 1) ? P->lrs_part2 : P->lrs_part;
   e.lrs_parts = lrs_blocks(P->g);
+  if (P->slab_rec) {
+    // x-slab sharding: the Gram and the statistics come reduced over all slabs in one record
+    e.gram_part = reinterpret_cast<const float2*>(P->slab_rec + kSlabRecHead);
+    e.nparts = 1;
+    e.dc_part = P->slab_rec;
+    e.ndc = 1;
+    e.lrs_part = P->slab_rec + 4;
+    e.lrs_parts = 1;
+  }
   e.W = P->W;
   e.V = P->V;
   e.sigma_prev = P->sigma_prev;
@@ -695,7 +776,7 @@ int lps_estimate_device_bytes(const lps_params* p, size_t* bytes) {
   if (p->precision != LPS_FP32) b += N * 8;    // reprojection output
   b += (size_t)g.ncoil * N * 8;                // coils
   if (p->coil_format == LPS_COILS_FP16) b += (size_t)g.ncoil * N * 4;   // half-precision copy
-  b += 3 * ((size_t)g.nx * g.ncoil * m + 4) * 8;   // hybrid data, k-space staging, scratch
+  b += 2 * ((size_t)g.nx * g.ncoil * m + 4) * 8 + ((size_t)g.nxt * g.ncoil * m + 4) * 8;   // hybrid, scratch, staging
   b += (size_t)gram_part_capacity(g) * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
   b += (size_t)g.nx * 4 + (size_t)g.ntiles * 16 + 2 * N / 8;
   b += (size_t)(p->max_iters + 2) * sizeof(IterRec) + 4096;
@@ -742,7 +823,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
   if ((rc = aalloc(P, &P->dc_part, (size_t)g.nx * 4))) return fail(rc);
   if ((rc = aalloc(P, &P->lrs_part, (size_t)g.ntiles * 2))) return fail(rc);
   if ((rc = aalloc(P, &P->lrs_part2, (size_t)g.ntiles * 2))) return fail(rc);
-  if ((rc = aalloc(P, &P->tw_x, (size_t)g.nx))) return fail(rc);
+  if ((rc = aalloc(P, &P->tw_x, (size_t)g.nxt))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_y, (size_t)g.ny))) return fail(rc);
   if ((rc = aalloc(P, &P->tw_z, (size_t)g.nz))) return fail(rc);
   if ((rc = aalloc(P, &P->lines, (size_t)g.plane))) return fail(rc);
@@ -776,7 +857,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
     CK(cudaMemcpy(d, t.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
     return LPS_OK;
   };
-  if ((rc = up(P->tw_x, g.nx)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.nz))) return fail(rc);
+  if ((rc = up(P->tw_x, g.nxt)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.nz))) return fail(rc);
   if (cudaMemset(P->persist, 0, sizeof(DevPersist)) != cudaSuccess ||
       cudaMemset(P->ctrl, 0, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMemset(P->dc_part, 0, g.nx * 4 * sizeof(float)) != cudaSuccess ||
@@ -862,7 +943,7 @@ int lps_set_data(lps_plan* P, const void* kdata, int nlines) {
   ARG(nlines == P->nlines, "nlines %d does not match the mask (%d lines)", nlines, P->nlines);
   const void* src = kdata;
   if (!is_device_ptr(kdata)) {
-    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * nlines * P->g.nx * sizeof(float2),
+    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * nlines * P->g.nxt * sizeof(float2),
                        cudaMemcpyDefault, P->st));
     src = P->kstage;
   }
@@ -902,6 +983,10 @@ int lps_clear_prior(lps_plan* P) {
 int lps_iterate(lps_plan* P, int n_iters, lps_stats* stats) {
   int rc = need_ready(P);
   if (rc) return rc;
+  if (P->g.nxt != P->g.nx) {
+    set_err("a plan that holds a slab of the volume iterates through lps_slab_begin/iterate/end");
+    return LPS_ERR_STATE;
+  }
   const int done = P->state_ready ? P->iters_done : 0;
   ARG(n_iters >= 0 && done + n_iters <= P->p.max_iters, "n_iters out of range (done %d, max_iters %d)", done,
       P->p.max_iters);
@@ -924,6 +1009,10 @@ int lps_reconstruct_frame(lps_plan* P, void* out_recon, void* out_L, void* out_S
                           double* out_sigma, lps_stats* stats) {
   int rc = need_ready(P);
   if (rc) return rc;
+  if (P->g.nxt != P->g.nx) {
+    set_err("a plan that holds a slab of the volume reconstructs through lps_slab_begin/iterate/end");
+    return LPS_ERR_STATE;
+  }
   if ((rc = build_graph(P))) return rc;
   if (P->hp.skip) {   // left over from a batch in which this plan sat out a step
     P->hp.skip = 0;
@@ -1114,7 +1203,7 @@ int lps_forward(lps_plan* P, const void* image, void* kdata) {
   x.inverse = 0;
   LK(launch_xfft(x, P->st));
   if (!dev) {
-    CK(cudaMemcpyAsync(kdata, P->kstage, (size_t)P->g.ncoil * P->nlines * P->g.nx * sizeof(float2),
+    CK(cudaMemcpyAsync(kdata, P->kstage, (size_t)P->g.ncoil * P->nlines * P->g.nxt * sizeof(float2),
                        cudaMemcpyDefault, P->st));
     CK(cudaStreamSynchronize(P->st));
   }
@@ -1129,7 +1218,7 @@ int lps_adjoint(lps_plan* P, const void* kdata, void* image) {
   }
   const float2* src = (const float2*)kdata;
   if (!is_device_ptr(kdata)) {
-    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * P->nlines * P->g.nx * sizeof(float2),
+    CK(cudaMemcpyAsync(P->kstage, kdata, (size_t)P->g.ncoil * P->nlines * P->g.nxt * sizeof(float2),
                        cudaMemcpyDefault, P->st));
     src = P->kstage;
   }
@@ -1184,6 +1273,76 @@ int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm
   }
   P->state_ready = false;
   return LPS_OK;
+}
+
+int lps_slab_reduction_size(const lps_plan* P, size_t* sum_floats, size_t* max_floats) {
+  ARG(P != nullptr && sum_floats != nullptr && max_floats != nullptr, "NULL argument");
+  *sum_floats = slab_sum_floats(P->g.nc);
+  *max_floats = 1;
+  return LPS_OK;
+}
+
+int lps_slab_begin(lps_plan* P, float* rec) {
+  int rc = need_ready(P);
+  if (rc) return rc;
+  ARG(rec != nullptr && is_device_ptr(rec), "rec must be a device buffer");
+  P->slab_rec = nullptr;
+  if ((rc = enqueue_init(P, P->st))) return rc;
+  LK(launch_slab_pack(P->gram_part, gram_parts(P->g, P->p.precision), P->g.nc, P->dc_part, P->g.nx, P->lrs_part,
+                      lrs_blocks(P->g), P->ctrl, rec, P->st));
+  P->iters_done = 0;
+  P->state_ready = true;
+  P->slab_open = true;
+  return LPS_OK;
+}
+
+int lps_slab_iterate(lps_plan* P, float* rec, int k) {
+  ARG(P != nullptr && rec != nullptr, "NULL argument");
+  if (!P->slab_open) {
+    set_err("lps_slab_begin must precede lps_slab_iterate");
+    return LPS_ERR_STATE;
+  }
+  ARG(k == P->iters_done + 1 && k <= P->p.max_iters, "iteration %d out of order (done %d, max_iters %d)", k,
+      P->iters_done, P->p.max_iters);
+  if (k == 1) {
+    // the maximum over the slabs of |T(X_0)| fixes lambda_S at the first iteration
+    CK(cudaMemcpyAsync(&P->ctrl->haar_max_bits, rec + slab_sum_floats(P->g.nc), sizeof(float),
+                       cudaMemcpyDeviceToDevice, P->st));
+  }
+  P->slab_rec = rec;
+  const int i = k - 1;
+  int rc = enqueue_iter(P, k, i, P->st, P->side);
+  P->slab_rec = nullptr;
+  if (rc) return rc;
+  // the sparse step of iteration k wrote its partials to buffer (i + 1) & 1
+  LK(launch_slab_pack(P->gram_part, gram_parts(P->g, P->p.precision), P->g.nc, P->dc_part, P->g.nx,
+                      (i & 1) ? P->lrs_part : P->lrs_part2, lrs_blocks(P->g), P->ctrl, rec, P->st));
+  P->iters_done = k;
+  return LPS_OK;
+}
+
+int lps_slab_end(lps_plan* P, const float* rec, lps_stats* stats) {
+  ARG(P != nullptr && rec != nullptr, "NULL argument");
+  if (!P->slab_open || P->iters_done < 1) {
+    set_err("lps_slab_end needs lps_slab_begin and at least one lps_slab_iterate");
+    return LPS_ERR_STATE;
+  }
+  const int K = P->iters_done;
+  P->slab_rec = rec;
+  int rc = enqueue_finalize(P, K, K, P->st);
+  P->slab_rec = nullptr;
+  if (rc) return rc;
+  if ((rc = enqueue_settle(P, 1, P->st))) return rc;
+  if (P->p.recursive) {
+    const size_t w = support_words(P->g);
+    CK(cudaMemcpyAsync(P->sup_prior, P->sup_out, w * sizeof(uint32_t), cudaMemcpyDeviceToDevice, P->st));
+    CK(cudaMemcpyAsync(P->sigma_prev, P->sigma_out, P->g.nc * sizeof(double), cudaMemcpyDeviceToDevice, P->st));
+    CK(cudaMemsetAsync(&P->persist->has_sup, 1, 2 * sizeof(int), P->st));
+    P->hp.has_sup = 1;
+    P->hp.has_sigma = 1;
+  }
+  P->slab_open = false;
+  return read_stats(P, stats);
 }
 
 // Checkpoint layout: header, prior support words, prior sigma, L, S, X, lambdas.

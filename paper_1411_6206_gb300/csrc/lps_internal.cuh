@@ -63,7 +63,8 @@ inline double iter_objective(const IterRec& r, float lambda_L, float lambda_S) {
 }
 
 struct Geom {
-  int nx, ny, nz, ncoil;
+  int nx, ny, nz, ncoil;    // nx: the x-planes this plan holds (a slab of nxt planes)
+  int nxt, x0;              // x extent of the whole volume (readout length) and the slab's first plane
   int nc;                   // Casorati columns (= nz)
   int plane;                // ny*nz, elements of one x-plane
   int nyp;                  // padded row stride of the FFT buffers (odd)
@@ -74,7 +75,7 @@ struct Geom {
   int ntiles;               // (nx/8)*(ny/8)
   long long N;              // nx*ny*nz
   float scale_yz;           // 1/sqrt(ny*nz) (fft_z) or 1/sqrt(ny)
-  float scale_x;            // 1/sqrt(nx)
+  float scale_x;            // 1/sqrt(nxt)
   FftPlan py, pz, px;
   int dc_generic;           // 1: always the runtime-sized data-consistency kernel (autotuner)
   int dc_direct;            // runtime-sized kernel reads coil maps from global memory (no staging)
@@ -119,7 +120,8 @@ struct XfftArgs {
   float2* out;
   const float2* tw_x;
   const DevPersist* persist;
-  int inverse;              // 1: k-space [c][l][kx] -> hybrid [x][c][l]; 0: the reverse
+  int inverse;              // 1: k-space [c][l][kx] -> hybrid [x][c][l] (the plan's planes x0 .. x0+nx-1);
+                            // 0: the reverse (planes outside the slab count as zero)
 };
 
 // ---- support-aware sparse step (step 3), one CTA per group of 8x8 tiles ------------
@@ -143,7 +145,8 @@ struct EigArgs {
   Geom g;
   const float2* gram_part;  // [nparts][nc][nc]
   int nparts;
-  const float* dc_part;     // [nx][4]
+  const float* dc_part;     // [ndc][4]
+  int ndc;                  // data-consistency statistic partials (nx; 1 for a reduced slab record)
   const float* lrs_part;    // [lrs_parts][2]
   int lrs_parts;            // CTAs of the sparse-step kernel
   float2* W;                // [nc][nc]

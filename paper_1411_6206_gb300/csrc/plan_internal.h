@@ -93,6 +93,10 @@ struct lps_plan {
   cudaGraphExec_t gexec = nullptr;
   bool graph_valid = false;
   unsigned graph_gen = 0;              // incremented at every capture
+  // x-slab sharding: the reduced record the eigen kernel reads (device, caller-owned) while
+  // lps_slab_iterate / lps_slab_end enqueue work; nullptr otherwise
+  const float* slab_rec = nullptr;
+  bool slab_open = false;
   // profiling: event pairs around every kernel of the frame graph, by kernel class
   bool profiling = false;
   std::vector<cudaEvent_t> ev;      // 2 per recorded launch
@@ -101,6 +105,14 @@ struct lps_plan {
 };
 
 namespace lps {
+
+// Reduction record of x-slab sharding (floats): [0..3] data-consistency statistic sums,
+// [4..5] sparse-step sums, [6..7] zero, [8 .. 8 + 2 nc^2) the Gram (complex, row-major) -- the
+// part the slabs add up -- then one float, max |T(X_0)|, that they take the maximum of.
+constexpr int kSlabRecHead = 8;
+inline size_t slab_sum_floats(int nc) { return (size_t)kSlabRecHead + 2 * (size_t)nc * nc; }
+cudaError_t launch_slab_pack(const float2* gram_part, int nparts, int nc, const float* dc_part, int ndc,
+                             const float* lrs_part, int nlrs, const DevCtrl* ctrl, float* rec, cudaStream_t st);
 
 // Helpers of lps_api.cu used by the other host translation units.
 int plan_build_graph(lps_plan* P);        // capture + instantiate the per-frame graph if stale

@@ -44,7 +44,8 @@ class Params(C.Structure):
                 ("lambda_L_rel", C.c_double), ("lambda_S_rel", C.c_double),
                 ("lambda_p", C.c_double), ("rank_tau", C.c_double), ("tol", C.c_double),
                 ("precision", C.c_int), ("eig_precision", C.c_int), ("support_rule", C.c_int),
-                ("recursive", C.c_int), ("coil_format", C.c_int), ("reserved", C.c_int * 7)]
+                ("recursive", C.c_int), ("coil_format", C.c_int), ("nx_total", C.c_int), ("x0", C.c_int),
+                ("reserved", C.c_int * 5)]
 
 
 class Stats(C.Structure):
@@ -127,6 +128,10 @@ _SIGS = {
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
+    "lps_slab_reduction_size": ([_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
+    "lps_slab_begin": ([_VP, _VP], C.c_int),
+    "lps_slab_iterate": ([_VP, _VP, C.c_int], C.c_int),
+    "lps_slab_end": ([_VP, _VP, C.POINTER(Stats)], C.c_int),
     "lps_adjoint_noalloc": ([C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, _VP, _VP, _VP, C.c_int, _VP, _VP],
                             C.c_int),
     "lps_get_recon": ([_VP, _VP], C.c_int),
@@ -358,6 +363,27 @@ def adjoint_noalloc(nx: int, ny: int, nz: int, ncoil: int, mask, coils, kdata, n
     for callers that cannot allocate device memory at the point of use."""
     _check(load().lps_adjoint_noalloc(nx, ny, nz, ncoil, fft_z, ptr(mask), ptr(coils), ptr(kdata), nlines,
                                       ptr(image), _stream(stream)), "adjoint_noalloc")
+
+
+def slab_reduction_size(plan: int):
+    """(sum_floats, max_floats) of the reduction record of an x-slab plan."""
+    a, b = C.c_size_t(), C.c_size_t()
+    _check(load().lps_slab_reduction_size(plan, C.byref(a), C.byref(b)), "slab_reduction_size")
+    return a.value, b.value
+
+
+def slab_begin(plan: int, rec):
+    _check(load().lps_slab_begin(plan, ptr(rec)), "slab_begin")
+
+
+def slab_iterate(plan: int, rec, k: int):
+    _check(load().lps_slab_iterate(plan, ptr(rec), k), "slab_iterate")
+
+
+def slab_end(plan: int, rec) -> "Stats":
+    st = Stats()
+    _check(load().lps_slab_end(plan, ptr(rec), C.byref(st)), "slab_end")
+    return st
 
 
 def get_recon(plan: int, out):
