@@ -123,6 +123,17 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     }
   };
   if (early) prologue_loads();
+  // Coil maps are set before any frame work: the column of this thread for the group's first
+  // coil is loaded now; inside the loop the next coil's column is loaded one coil ahead, so
+  // that its latency passes during the row phase of the current coil.
+  float2 cn[kNZ];
+  auto load_col = [&](int c) {
+    const float2* Cc = a.coils + (long long)c * g.N + xoff + gt;
+    const __half2* Ch = HALF ? a.coils_h + (long long)c * g.N + xoff + gt : nullptr;
+#pragma unroll
+    for (int z = 0; z < kNZ; ++z) cn[z] = HALF ? __half22float2(__ldg(Ch + z * xy)) : __ldg(Cc + z * xy);
+  };
+  if (grp < g.ncoil) load_col(grp);
   pdl_trigger();
   pdl_wait();   // W and the control block (without W also L, S and X) come from earlier work
   const int conv = a.ctrl ? a.ctrl->converged : 0;
@@ -206,7 +217,8 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     // column phase: v[z] = sc C_c Z at (z, y = gt), transform along z
     const bool first = c == grp;
 #pragma unroll
-    for (int z = 0; z < kNZ; ++z) v[z] = cscale(cmul(coil(z), zs[z * kRS + gt]), sc);
+    for (int z = 0; z < kNZ; ++z) v[z] = cscale(cmul(cn[z], zs[z * kRS + gt]), sc);
+    if (c + G < ncoil) load_col(c + G);
     if (FFTZ) dft16(v, false);
 #pragma unroll
     for (int k = 0; k < kNZ; ++k) B[k * kRS + gt] = v[k];

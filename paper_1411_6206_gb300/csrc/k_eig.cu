@@ -126,7 +126,7 @@ __device__ __forceinline__ void jsync(int nthr) { asm volatile("bar.sync 1, %0;"
 // CTA have no task and wait at the CTA barrier that follows.
 template <int NCT>
 __device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n_rt, float eps, float floor_,
-                      int max_sweeps, int* flags) {
+                      int max_sweeps, float start, int* flags) {
   const int n = NCT ? NCT : n_rt;
   const int nthr = jacobi_threads(n);
   using C = float2;
@@ -161,19 +161,20 @@ __device__ int jacobi(float2*& A, float2*& An, float2*& V, float2*& Vn, int n_rt
   const int np2 = next_pos(p2, np), nq2 = next_pos(q2, np);
   int sweep = 0;
   for (;;) {
-    // converged when no off-diagonal entry exceeds twice its rotation threshold (a sweep still
-    // rotates every pair above the threshold itself): the residual stays at the rounding level
-    // of the float32 Gram, and sweeps that would only move rounding noise are not started
+    // converged when no off-diagonal entry exceeds `start` times its rotation threshold (a
+    // sweep still rotates every pair above the threshold itself), so that sweeps that would only
+    // move rounding noise are not started
     if (tid == 0) flags[sweep & 1] = 0;
     jsync(nthr);
     for (int t = tid; t < n * n; t += nthr) {
       const int p = t / n, q = t - (t / n) * n;
       if (p < q) {
-        // the rotation test of rot_params at twice the thresholds (no rotation parameters)
+        // the rotation test of rot_params at `start` times the thresholds (no rotation
+        // parameters)
         const float app = A[p * kLd + p].x, aqq = A[q * kLd + q].x;
         const float2 apq = A[p * kLd + q];
         const float g2 = apq.x * apq.x + apq.y * apq.y;
-        const float lim = fmaxf(2.f * eps * fmaxf(fabsf(app), fabsf(aqq)), 2.f * floor_);
+        const float lim = fmaxf(start * eps * fmaxf(fabsf(app), fabsf(aqq)), start * floor_);
         if (g2 > lim * lim) flags[sweep & 1] = 1;
       }
     }
@@ -495,7 +496,12 @@ __global__ void __launch_bounds__(kEigThreads, 1) k_eig(const EigArgs a) {
     float2* Vf = sh.V;
     float2* Vfn = sh.V1;
     if (tid < jacobi_threads(n)) {
-      sweeps = jacobi<NCT>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, sh.flags);
+      // a new sweep starts above 8x the rotation threshold (64u of the larger diagonal entry or
+      // 8u of the trace), still below the float32 Gram's own accumulation error (about
+      // u sqrt(rows) of the trace); before the float64 refinement (part 1) at 2x, which leaves
+      // the refinement pairs coupled well below its 1e-3 gap limit
+      sweeps = jacobi<NCT>(Af, Afn, Vf, Vfn, n, 4.8e-7f, 6.0e-8f * trace + 1e-30f, 12, a.part == 1 ? 2.f : 8.f,
+                           sh.flags);
       if (tid == 0) {
         // own fields: other Jacobi threads may still read flags[] in their last convergence test
         sh.jac_sweeps = sweeps;
