@@ -181,6 +181,14 @@ int lps_set_data(lps_plan* plan, const void* kdata, int nlines);
 int lps_set_prior(lps_plan* plan, const uint32_t* support, const double* sigma_prev);
 int lps_clear_prior(lps_plan* plan);
 
+/* Sliding temporal window (layout LPS_LAYOUT_FRAMES): when the next call reconstructs the
+ * window advanced by `shift` frames, the support installed as the prior (the recursion of
+ * Sec. 3) must follow its frames. Moves the prior support `shift` Casorati columns towards
+ * column 0 (the first `shift` columns are dropped) and repeats the last remaining column in the
+ * `shift` freed ones (the newest frame's prior is the support of the frame before it). The
+ * prior singular values are kept. 1 <= shift < nz; enqueued on the plan's stream. */
+int lps_shift_prior_columns(lps_plan* plan, int shift);
+
 /* Run n iterations of Algorithm 1 on the resident state, starting with step (0) if the
  * state was reset by lps_set_data. Stops early on the tol rule (stats->iters tells). */
 int lps_iterate(lps_plan* plan, int n_iters, lps_stats* stats /* nullable */);

@@ -972,6 +972,23 @@ int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev
   return upload_persist(P);
 }
 
+int lps_shift_prior_columns(lps_plan* P, int shift) {
+  ARG(P != nullptr, "plan is NULL");
+  ARG(shift >= 1 && shift < P->g.nz, "shift must be in 1..nz-1");
+  // support words of one Casorati column (the coefficients of one slice or frame are
+  // contiguous: the column index is the outermost of the tile-major numbering)
+  const size_t wpc = (size_t)P->g.nx * P->g.ny / 32;
+  const size_t keep = (size_t)(P->g.nz - shift) * wpc;
+  // through the second support buffer, free between frames (the ranges overlap)
+  CK(cudaMemcpyAsync(P->sup_out2, P->sup_prior + shift * wpc, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
+                     P->st));
+  CK(cudaMemcpyAsync(P->sup_prior, P->sup_out2, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice, P->st));
+  for (int z = P->g.nz - shift; z < P->g.nz; ++z)
+    CK(cudaMemcpyAsync(P->sup_prior + z * wpc, P->sup_out2 + keep - wpc, wpc * sizeof(uint32_t),
+                       cudaMemcpyDeviceToDevice, P->st));
+  return LPS_OK;
+}
+
 int lps_clear_prior(lps_plan* P) {
   ARG(P != nullptr, "plan is NULL");
   P->hp.v_valid = 0;

@@ -128,6 +128,7 @@ _SIGS = {
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
+    "lps_shift_prior_columns": ([_VP, C.c_int], C.c_int),
     "lps_slab_reduction_size": ([_VP, C.POINTER(C.c_size_t), C.POINTER(C.c_size_t)], C.c_int),
     "lps_slab_begin": ([_VP, _VP], C.c_int),
     "lps_slab_iterate": ([_VP, _VP, C.c_int], C.c_int),
@@ -363,6 +364,10 @@ def adjoint_noalloc(nx: int, ny: int, nz: int, ncoil: int, mask, coils, kdata, n
     for callers that cannot allocate device memory at the point of use."""
     _check(load().lps_adjoint_noalloc(nx, ny, nz, ncoil, fft_z, ptr(mask), ptr(coils), ptr(kdata), nlines,
                                       ptr(image), _stream(stream)), "adjoint_noalloc")
+
+
+def shift_prior_columns(plan: int, shift: int = 1):
+    _check(load().lps_shift_prior_columns(plan, shift), "shift_prior_columns")
 
 
 def slab_reduction_size(plan: int):
