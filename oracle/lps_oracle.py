@@ -13,7 +13,8 @@ fusion or algebraic shortcut beyond what the definition states:
               (z, x, y) (or over (x, y) per slice), M the Cartesian line mask.
               Implemented with scipy.fft.fftn(norm="ortho") on the full grid.
   T, T^{-1}   the sparsifying transform of Sec. 2 ("Wavelets"; Sec. 4 "Wavelet domain"):
-              orthonormal 2D Haar, Mallat pyramid, J levels, per slice, explicit filter bank.
+              orthonormal 2D Haar, Mallat pyramid, J levels, per slice, explicit filter bank;
+              T3 the 3D variant (the same per slice, then J levels of the 1D Haar along z).
   soft        the soft-threshold operator of Sec. 2 (x/|x| max(|x|-lambda, 0), complex x).
   svt         singular-value soft-thresholding, Algorithm 1 step (1), via numpy.linalg.svd
               of the Casorati matrix (no Gram-matrix route).
@@ -163,6 +164,34 @@ def Tinv(c: np.ndarray, J: int = 3) -> np.ndarray:
     return np.stack([ihaar2(c[z], J) for z in range(c.shape[0])])
 
 
+def T3(x: np.ndarray, J: int = 3) -> np.ndarray:
+    """3D orthonormal Haar (the tensor-product variant): the per-slice 2D transform T, then J
+    levels of the 1D Haar along z over the whole nz in Mallat order (at each level the leading
+    approximation block is split into low and high halves). nz must be a multiple of 2^J."""
+    out = np.array(T(x, J), dtype=np.complex128, copy=True)
+    hz = out.shape[0]
+    for _ in range(J):
+        lo, hi = _haar_split(out[:hz], 0)
+        out[:hz // 2] = lo
+        out[hz // 2:hz] = hi
+        hz //= 2
+    return out
+
+
+def T3inv(c: np.ndarray, J: int = 3) -> np.ndarray:
+    out = np.array(c, dtype=np.complex128, copy=True)
+    hz = out.shape[0] >> (J - 1)
+    for _ in range(J):
+        out[:hz] = _haar_merge(out[:hz // 2], out[hz // 2:hz], 0)
+        hz *= 2
+    return Tinv(out, J)
+
+
+def sparsifying(p):
+    """The transform pair of step (3): T (2D per slice, the default) or T3 (3D)."""
+    return (T3, T3inv) if p.wavelet_dims == 3 else (T, Tinv)
+
+
 # ----------------------------------------------------------------------------------------
 # Pointwise and singular-value operators
 # ----------------------------------------------------------------------------------------
@@ -242,6 +271,7 @@ class Params:
     tol: float = 0.0
     fft_z: int = 1
     support_rule: str = "threshold"   # or "nonzero"
+    wavelet_dims: int = 2             # 2: per-slice 2D Haar (R6); 3: 3D tensor-product Haar
 
 
 @dataclasses.dataclass
@@ -271,7 +301,8 @@ class Prior:
 
 def initial_lambdas(X0: np.ndarray, p: Params):
     s = np.linalg.svd(casorati(X0), compute_uv=False)
-    return p.lambda_L_rel * s[0], p.lambda_S_rel * np.max(np.abs(T(X0, p.wavelet_levels)))
+    Tf, _ = sparsifying(p)
+    return p.lambda_L_rel * s[0], p.lambda_S_rel * np.max(np.abs(Tf(X0, p.wavelet_levels)))
 
 
 def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
@@ -282,6 +313,7 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
     prior  None (t = 1, plain L+S) or Prior(support, sigma) of frame t-1
     state  optional (X, S, L_prev, lambda_L, lambda_S) to start from instead of step (0)."""
     J = p.wavelet_levels
+    Tf, Tfinv = sparsifying(p)
     K = p.max_iters if iters is None else iters
     if state is None:
         X = EH(d, coils, mask, p.fft_z)               # (0) X_0 = A^{-1}(y)
@@ -310,9 +342,9 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
         Lm, s, s2 = svt(casorati(X - S), lamL, p.lambda_p, sig_prev, p.rank_tau)
         L = uncasorati(Lm, shape)
         # (3) sparsity off the prior support
-        c = T(X - Lp, J)
+        c = Tf(X - Lp, J)
         c2 = support_shrink(c, lamS, keep)
-        S = Tinv(c2, J)
+        S = Tfinv(c2, J)
         # (4) data consistency
         R = E(L + S, coils, mask, p.fft_z) - d
         X = L + S - EH(R, coils, mask, p.fft_z)
@@ -340,7 +372,7 @@ def objective(L, S, d, coils, mask, lamL, lamS, keep, p: Params) -> float:
     the Lagrangian form of Eq. (3) without the sigma-closeness constraint (lambda_p = 0)."""
     R = E(L + S, coils, mask, p.fft_z) - d
     nuc = np.linalg.svd(casorati(L), compute_uv=False).sum()
-    c = T(S, p.wavelet_levels)
+    c = sparsifying(p)[0](S, p.wavelet_levels)
     off = np.ones(c.shape, bool) if keep is None else ~keep
     return 0.5 * float(np.vdot(R, R).real) + lamL * nuc + lamS * float(np.abs(c[off]).sum())
 

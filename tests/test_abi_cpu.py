@@ -114,6 +114,29 @@ def test_abi_coefficient_order_is_blockwise_mallat(J):
                         assert np.abs(got - ref).max() < 1e-12
 
 
+@pytest.mark.parametrize("J", [1, 2, 3])
+def test_abi_order_3d_is_blockwise_mallat(J):
+    """With the 3D transform the ABI coefficient of slice z = bz 2^J + w, tile (tx, ty), (u, v)
+    is coefficient (w, u', v') of the aligned 2^J x 2^J x 2^J block's own 3D transform."""
+    rng = np.random.default_rng(3)
+    nz, nx, ny = 16, 16, 8
+    x = rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny))
+    c = O.T3(x, J)
+    zz, ii, jj = abi_to_mallat(nz, nx, ny, J, 3)
+    assert len(set(zip(zz, ii, jj))) == nz * nx * ny
+    vals = c[zz, ii, jj].reshape(nz, nx // 8, ny // 8, 8, 8)
+    B = 1 << J
+    for bz in range(nz // B):
+        for tx in range(nx // 8):
+            for ty in range(ny // 8):
+                for su in range(8 // B):
+                    for sv in range(8 // B):
+                        x0, y0 = tx * 8 + su * B, ty * 8 + sv * B
+                        ref = O.T3(x[bz * B:(bz + 1) * B, x0:x0 + B, y0:y0 + B], J)
+                        got = vals[bz * B:(bz + 1) * B, tx, ty, su * B:(su + 1) * B, sv * B:(sv + 1) * B]
+                        assert np.abs(got - ref).max() < 1e-12
+
+
 def test_bitmap_pack_roundtrip():
     rng = np.random.default_rng(1)
     sup = rng.random((3, 16, 8)) < 0.3

@@ -140,6 +140,86 @@ def test_haar_constant_block_single_coefficient():
     assert abs(c[0, 1, 0] - 8 * (2 - 1j)) < 1e-12
 
 
+def haar1_basis(n, J):
+    """Analytic orthonormal 1D Haar functions (Mallat positions): level-j details are
+    +-1 / sqrt(2^j) on aligned blocks of 2^j (first half +, second half -), the level-J
+    approximation 1 / sqrt(2^J) on aligned blocks of 2^J."""
+    basis = {}
+    for j in range(1, J + 1):
+        b = 2 ** j
+        for k in range(n // b):
+            f = np.zeros(n)
+            f[k * b: k * b + b // 2] = 1 / np.sqrt(b)
+            f[k * b + b // 2: k * b + b] = -1 / np.sqrt(b)
+            basis[n // b + k] = f
+            if j == J:
+                a = np.zeros(n)
+                a[k * b: k * b + b] = 1 / np.sqrt(b)
+                basis[k] = a
+    return basis
+
+
+@pytest.mark.parametrize("nz,nx,ny,J", [(8, 8, 8, 3), (16, 8, 16, 3), (4, 8, 8, 2), (2, 8, 4, 1)])
+def test_haar3_equals_analytic_basis(nz, nx, ny, J):
+    """The 3D variant is the tensor product of the 1D Haar along z with the 2D pyramid: its
+    coefficient (k, i, j) is <f_k (x) g_ij, x> for the analytic functions f (1D) and g (2D)."""
+    x = crandn(nz, nx, ny)
+    c = O.T3(x, J)
+    fz = haar1_basis(nz, J)
+    g2 = haar_basis(nx, ny, J)
+    assert len(fz) == nz and len(g2) == nx * ny
+    for k, f in fz.items():
+        for (i, j), g in g2.items():
+            assert abs(c[k, i, j] - (f[:, None, None] * g[None] * x).sum()) < 1e-12
+
+
+def test_haar3_orthonormal_and_invertible():
+    x = crandn(16, 16, 24)
+    c = O.T3(x, 3)
+    assert abs(np.linalg.norm(c) - np.linalg.norm(x)) < 1e-12 * np.linalg.norm(x)
+    assert np.abs(O.T3inv(c, 3) - x).max() < 1e-12
+    # not the per-slice transform: the z pass moves energy between slices
+    assert np.abs(c - O.T(x, 3)).max() > 0.1
+
+
+def test_haar3_constant_cube_single_coefficient():
+    """A constant a on the aligned 8 x 8 x 8 cube (z, x, y) in [8, 16) x [0, 8) x [8, 16)
+    has one 3D coefficient, a sqrt(512), at the approximation position (1, 0, 1); the 2D
+    transform gives eight coefficients 8a instead (one per slice)."""
+    a = 0.5 + 1.5j
+    x = np.zeros((16, 16, 16), complex)
+    x[8:16, 0:8, 8:16] = a
+    c = O.T3(x, 3)
+    assert np.argwhere(np.abs(c) > 1e-12).tolist() == [[1, 0, 1]]
+    assert abs(c[1, 0, 1] - a * np.sqrt(512)) < 1e-12
+    assert (np.abs(O.T(x, 3)) > 1e-12).sum() == 8
+
+
+def test_initial_lambdas_and_sparse_step_use_the_3d_transform():
+    """With wavelet_dims = 3, lambda_S = rel_S max|T3(X_0)| and step (3) shrinks the 3D
+    coefficients. X_0 = the constant cube a on 8 x 8 x 8 (full mask, unit coil, so E^H E = I):
+    sigma_1 = |a| sqrt(512) (eight equal Casorati columns of norm 8|a|), max|T3 X_0| =
+    |a| sqrt(512). One iteration from the state (X = cube, S = 0, L_prev = 0) with lambda_S = l
+    gives S = (1 - l / (|a| sqrt(512))) X; the per-slice transform would give (1 - l / (8|a|)) X."""
+    a = 2.0 - 1.0j
+    nz, nx, ny = 8, 8, 8
+    x = np.full((nz, nx, ny), a)
+    coils = np.ones((1, nz, nx, ny), complex)
+    mask = np.ones((nz, ny), np.uint8)
+    d = O.E(x, coils, mask)
+    p3 = O.Params(lambda_L_rel=0.01, lambda_S_rel=0.005, max_iters=1, wavelet_dims=3)
+    lL, lS = O.initial_lambdas(x, p3)
+    assert abs(lL - 0.01 * abs(a) * np.sqrt(512)) < 1e-12
+    assert abs(lS - 0.005 * abs(a) * np.sqrt(512)) < 1e-12
+    lam = 4.0
+    zero = np.zeros_like(x)
+    r3 = O.priori_ls(d, coils, mask, p3, iters=1, state=(x, zero, zero, 0.0, lam))
+    assert np.abs(r3.S - (1 - lam / (abs(a) * np.sqrt(512))) * x).max() < 1e-12
+    p2 = O.Params(lambda_L_rel=0.01, lambda_S_rel=0.005, max_iters=1)
+    r2 = O.priori_ls(d, coils, mask, p2, iters=1, state=(x, zero, zero, 0.0, lam))
+    assert np.abs(r2.S - (1 - lam / (8 * abs(a))) * x).max() < 1e-12
+
+
 # ---------------------------------------------------------------- soft threshold
 
 def read_golden(name):
