@@ -892,9 +892,10 @@ def run_precision(args):
     return out, job
 
 
-def run_coils_fp16(args):
-    """The cardiac-shaped sequence with the coil maps stored in half precision (LPS_COILS_FP16):
-    frames/s and the data-consistency kernel's time per launch against float32 maps."""
+def plan_variants(variants, kernel):
+    """The cardiac-shaped sequence on plans that differ in lps_params fields only: frames/s
+    (median of 3 sequences, L2 flushed before each) and the time per launch of one kernel
+    class (a profiling pass), per variant."""
     import torch
     from paper_1411_6206_gb300 import lps, phantom as P
     w = P.CARDIAC
@@ -906,8 +907,8 @@ def run_coils_fp16(args):
     out = {}
     recon = torch.empty((T, w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
-    for name, fmt in (("fp32", lps.COILS_FP32), ("fp16", lps.COILS_FP16)):
-        pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1, coil_format=fmt)
+    for name, kw in variants:
+        pl = lps.Plan(w.nx, w.ny, w.nz, w.ncoil, stream=st, max_iters=w.iters, recursive=1, **kw)
         pl.set_coils(coils)
 
         def seq():
@@ -931,12 +932,34 @@ def run_coils_fp16(args):
         lps.set_profiling(pl.handle, True)
         seq()
         st.synchronize()
-        kt = lps.get_kernel_times(pl.handle).as_dict()["data_consistency"]
+        kt = lps.get_kernel_times(pl.handle).as_dict()[kernel]
+        words = np.empty(pl.support_words(), np.uint32)
+        lps.get_support(pl.handle, words, None)
         pl.close()
         out[name] = {"frames_per_s": round(T / (float(np.median(ms)) / 1e3), 2),
-                     "dc_us_per_launch": round(1e3 * kt["ms"] / max(1, kt["launches"]), 2)}
+                     kernel + "_us_per_launch": round(1e3 * kt["ms"] / max(1, kt["launches"]), 2),
+                     "support_fraction_last_frame": round(
+                         float(np.unpackbits(words.view(np.uint8)).sum()) / (32 * words.size), 4)}
+    return out
+
+
+def run_coils_fp16(args):
+    """The cardiac-shaped sequence with the coil maps stored in half precision (LPS_COILS_FP16):
+    frames/s and the data-consistency kernel's time per launch against float32 maps."""
+    from paper_1411_6206_gb300 import lps
+    out = plan_variants((("fp32", dict(coil_format=lps.COILS_FP32)), ("fp16", dict(coil_format=lps.COILS_FP16))),
+                        "data_consistency")
     out["how"] = ("same inputs, float32 maps given to both plans (the fp16 plan rounds them); the effect of the "
                   "rounding on the reconstruction is measured by tests/test_gpu_coils_fp16.py")
+    return out
+
+
+def run_haar3(args):
+    """The cardiac-shaped sequence with the 3D Haar (wavelet_dims = 3) against the per-slice 2D
+    Haar: frames/s, the sparse-step kernel's time per launch and the support fraction."""
+    out = plan_variants((("haar2d", dict(wavelet_dims=2)), ("haar3d", dict(wavelet_dims=3))), "sparse_step")
+    out["how"] = ("same inputs and iteration count; the 3D variant adds the z pass through shared memory "
+                  "to the sparse-step kernel")
     return out
 
 
@@ -1074,6 +1097,7 @@ def main():
             out["fig3"] = run_fig3(args)
         if ws == 1 and not args.no_small:
             out["coils_fp16"] = run_coils_fp16(args)
+            out["haar3d"] = run_haar3(args)
             out["window"] = run_window(args)
         if ws == 1 and not args.no_cpu_baseline:
             cb, nr = cpu_baseline(args, w)

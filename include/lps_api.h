@@ -41,8 +41,11 @@
  *     array, in which every aligned B x B sub-block holds that block's own Mallat layout
  *     (approximation at the block origin; the level-j details at offsets B/2^j along v
  *     (x-low, y-high), along u (x-high, y-low) and both). For J = 3 a tile is one block.
- *     Bit i of a bitmap is bit (i & 31) of 32-bit word i >> 5; lps_support_words() gives the
- *     word count (nx*ny*nz/32).
+ *     With the 3D Haar (wavelet_dims = 3) the same numbering
+ *     holds, slice z = bz * B + w standing for 1D position w, in Mallat order inside the
+ *     block (approximation at w = 0, the level-j details at B/2^j .. B/2^(j-1) - 1), of the
+ *     aligned block bz of B slices. Bit i of a bitmap is bit (i & 31) of 32-bit word i >> 5;
+ *     lps_support_words() gives the word count (nx*ny*nz/32).
  *   - Work is issued on the plan's CUDA stream. Only calls that return host-visible results
  *     (stats, host outputs, mask upload) synchronise it.
  */
@@ -125,7 +128,10 @@ typedef struct lps_params {
   int nx_total;            /* 0: the plan holds the whole volume; else the x extent of the
                               volume of which it holds planes x0 .. x0+nx-1 (lps_slab_*)     */
   int x0;                  /* first plane of the slab (multiple of 8)                       */
-  int reserved[5];         /* must be zero                                                  */
+  int wavelet_dims;        /* sparsifying transform T: 2 (0 reads as 2) the per-slice 2D Haar;
+                              3 the 3D Haar, the 2D pyramid times the J-level 1D Haar along z
+                              (nz a multiple of 2^J; the support numbering below)            */
+  int reserved[4];         /* must be zero                                                  */
 } lps_params;
 
 typedef struct lps_stats {

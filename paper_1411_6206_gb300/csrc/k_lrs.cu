@@ -9,9 +9,16 @@
 // (l1 off the support) and the support count are reduced per CTA in a fixed order.
 //
 // Wavelet coefficient layout: within a tile the 8 x 8 coefficient array holds, for every
-// aligned 2^J x 2^J sub-block, that sub-block's own Mallat layout. Thread t owns tile row
-// (u, v) = ((t&63)>>3, t&7) of the slices z = (t>>6) + 4q, so a warp covers 32 consecutive
-// coefficients of one slice and one ballot gives one 32-bit word of the bitmap.
+// aligned 2^J x 2^J sub-block, that sub-block's own Mallat layout. Eight consecutive lanes
+// hold the 64 coefficients of one (tile, slice), so four lanes give one 32-bit word of the
+// bitmap.
+//
+// The 3D variant (Z3) is the tensor product of that 2D pyramid with the J-level 1D Haar along
+// z on aligned blocks of 2^J slices: after the in-plane analysis every thread stores its row
+// in shared memory, each thread then transforms the z columns of a (tile, z block, u, v) set,
+// and the rows come back for the shrink; the synthesis runs the same passes in reverse. The
+// slice z = 2^J bz + w of the bitmap then holds the coefficients of 1D position w (Mallat
+// order inside the block) of z block bz.
 #include "lps_internal.cuh"
 
 #include <algorithm>
@@ -104,11 +111,88 @@ __device__ __forceinline__ void haar_inv(float2 (&r)[8], int u, int lane) {
   haar_inv_level<J, 1>(r, u, lane);
 }
 
-template <int J>
+// z pass of the 3D variant. zb holds one row of 8 complex per thread, row r at zb + 8r with
+// element v at position v ^ ((r >> 1) & 7): the row stores of a half-warp (16 rows, one
+// element each) and the column reads (consecutive (u, v)) hit 32 distinct banks.
+__device__ __forceinline__ int zslot(int row, int v) { return row * 8 + (v ^ ((row >> 1) & 7)); }
+
+__device__ __forceinline__ void zrow_store(float2* zb, int row, const float2 (&r)[8]) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) zb[zslot(row, v)] = r[v];
+}
+__device__ __forceinline__ void zrow_load(const float2* zb, int row, float2 (&r)[8]) {
+#pragma unroll
+  for (int v = 0; v < 8; ++v) r[v] = zb[zslot(row, v)];
+}
+
+// J-level 1D Haar along z (forward or inverse, Mallat order inside each aligned block of
+// B = 2^J slices) on the columns (tile, z block, u, v) of zb; the columns are spread over the
+// CTA's threads. Returns max |c| of the forward coefficients this thread produced (MAXC).
+template <int J, bool INV, bool MAXC>
+__device__ __forceinline__ float zpass(float2* zb, int nc, int tpc, int tid, int nthr) {
+  constexpr int B = 1 << J;
+  constexpr float r2 = 0.70710678118654752f;
+  const int nzb = nc / B;
+  const int ncol = tpc * nzb * 64;
+  float mx = 0.f;
+  for (int col = tid; col < ncol; col += nthr) {
+    const int uv = col & 63, rest = col >> 6;
+    const int tl = rest / nzb, bz = rest - tl * nzb;
+    const int row0 = (tl * nc + bz * B) * 8 + (uv >> 3), v = uv & 7;
+    float2 f[B];
+#pragma unroll
+    for (int w = 0; w < B; ++w) f[w] = zb[zslot(row0 + 8 * w, v)];
+    if constexpr (!INV) {
+#pragma unroll
+      for (int l = 1; l <= J; ++l) {
+        const int A = B >> (l - 1), H = A / 2;
+        float2 t[B];
+#pragma unroll
+        for (int q = 0; q < B / 2; ++q) {
+          if (q < H) {
+            t[q] = cscale(cadd(f[2 * q], f[2 * q + 1]), r2);
+            t[q + H] = cscale(csub(f[2 * q], f[2 * q + 1]), r2);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+          if (q < A) f[q] = t[q];
+      }
+      if constexpr (MAXC) {
+#pragma unroll
+        for (int w = 0; w < B; ++w) mx = fmaxf(mx, sqrtf(cabs2(f[w])));
+      }
+    } else {
+#pragma unroll
+      for (int l = J; l >= 1; --l) {
+        const int A = B >> (l - 1), H = A / 2;
+        float2 t[B];
+#pragma unroll
+        for (int q = 0; q < B / 2; ++q) {
+          if (q < H) {
+            t[2 * q] = cscale(cadd(f[q], f[q + H]), r2);
+            t[2 * q + 1] = cscale(csub(f[q], f[q + H]), r2);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < B; ++q)
+          if (q < A) f[q] = t[q];
+      }
+    }
+    if constexpr (!MAXC) {
+#pragma unroll
+      for (int w = 0; w < B; ++w) zb[zslot(row0 + 8 * w, v)] = f[w];
+    }
+  }
+  return mx;
+}
+
+template <int J, bool Z3>
 __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem[];
   float* red = reinterpret_cast<float*>(smem);
+  float2* zb = reinterpret_cast<float2*>(smem + 32 * sizeof(float));   // Z3: one row per thread
   const int nc = g.nc;
   const int tpc = g.lrs_tpc > 0 ? g.lrs_tpc : 32 / nc;   // tiles per CTA
 
@@ -162,8 +246,14 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   if (maxonly) {
     haar_fwd<J>(Xr, u, lane);
     float mx = 0.f;
+    if constexpr (Z3) {
+      zrow_store(zb, tid, Xr);
+      __syncthreads();
+      mx = zpass<J, false, true>(zb, nc, tpc, tid, blockDim.x);
+    } else {
 #pragma unroll
-    for (int v = 0; v < 8; ++v) mx = fmaxf(mx, sqrtf(cabs2(Xr[v])));
+      for (int v = 0; v < 8; ++v) mx = fmaxf(mx, sqrtf(cabs2(Xr[v])));
+    }
     mx = block_max(mx, red);
     if (tid == 0) atomicMax(&a.ctrl->haar_max_bits, __float_as_uint(mx));
     return;
@@ -175,6 +265,13 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
 #pragma unroll
   for (int v = 0; v < 8; ++v) D[v] = csub(Xr[v], Lp[v]);
   haar_fwd<J>(D, u, lane);
+  if constexpr (Z3) {
+    zrow_store(zb, tid, D);
+    __syncthreads();
+    zpass<J, false, false>(zb, nc, tpc, tid, blockDim.x);
+    __syncthreads();
+    zrow_load(zb, tid, D);
+  }
   const unsigned keepbits = has_sup ? (prior_word >> ((u & 3) * 8)) & 0xffu : 0u;
   float l1 = 0.f;
   unsigned sbits = 0;
@@ -199,6 +296,13 @@ __global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
   if (act && (u & 3) == 0 && a.sup_out) a.sup_out[wbase + (u >> 2)] = word;
   const float cnt = (act && (u & 3) == 0) ? (float)__popc(word) : 0.f;
   if (!act) l1 = 0.f;
+  if constexpr (Z3) {
+    zrow_store(zb, tid, D);   // the same slots this thread loaded: no barrier needed before
+    __syncthreads();
+    zpass<J, true, false>(zb, nc, tpc, tid, blockDim.x);
+    __syncthreads();
+    zrow_load(zb, tid, D);
+  }
   haar_inv<J>(D, u, lane);
   if (act) {
     float4* sd = reinterpret_cast<float4*>(a.S + rowoff);
@@ -289,26 +393,33 @@ int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : 32 / g.nc; }
 // Haar shuffles need full warps; lanes beyond the tiles are inactive).
 int lrs_threads(const Geom& g) { return (8 * g.nc * lrs_tpc(g) + 31) / 32 * 32; }
 
-static size_t lrs_smem(const Geom&) { return 32 * sizeof(float); }
+static size_t lrs_smem(const Geom& g) {
+  return 32 * sizeof(float) + (g.wz ? (size_t)lrs_threads(g) * 8 * sizeof(float2) : 0);
+}
 
 int lrs_blocks(const Geom& g) { return (g.ntiles + lrs_tpc(g) - 1) / lrs_tpc(g); }
 
-template <int J>
+template <int J, bool Z3>
 static cudaError_t launch_lrs_j(const LrsArgs& a, cudaStream_t st) {
   const size_t smem = lrs_smem(a.g);
   if (smem > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(k_lrs<J>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(k_lrs<J, Z3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
   }
-  cudaError_t e = launch_pdl(k_lrs<J>, dim3(lrs_blocks(a.g)), dim3(lrs_threads(a.g)), smem, st, a);
+  cudaError_t e = launch_pdl(k_lrs<J, Z3>, dim3(lrs_blocks(a.g)), dim3(lrs_threads(a.g)), smem, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
-  switch (a.g.J) {
-    case 1: return launch_lrs_j<1>(a, st);
-    case 2: return launch_lrs_j<2>(a, st);
-    default: return launch_lrs_j<3>(a, st);
+  // the 3D variant needs whole z blocks (validated with the plan's parameters)
+  if (a.g.wz && a.g.nc % (1 << a.g.J) != 0) return cudaErrorInvalidValue;
+  switch (a.g.J * 2 + (a.g.wz ? 1 : 0)) {
+    case 2: return launch_lrs_j<1, false>(a, st);
+    case 3: return launch_lrs_j<1, true>(a, st);
+    case 4: return launch_lrs_j<2, false>(a, st);
+    case 5: return launch_lrs_j<2, true>(a, st);
+    case 7: return launch_lrs_j<3, true>(a, st);
+    default: return launch_lrs_j<3, false>(a, st);
   }
 }
 

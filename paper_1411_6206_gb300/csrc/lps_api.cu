@@ -224,6 +224,9 @@ int validate(const lps_params* p, Geom* gout) {
     return LPS_ERR_UNSUPPORTED;
   }
   ARG(p->wavelet_levels >= 1 && p->wavelet_levels <= 3, "wavelet_levels must be 1..3");
+  ARG(p->wavelet_dims == 0 || p->wavelet_dims == 2 || p->wavelet_dims == 3, "wavelet_dims must be 2 or 3");
+  ARG(p->wavelet_dims != 3 || p->nz % (1 << p->wavelet_levels) == 0,
+      "the 3D Haar needs nz a multiple of 2^wavelet_levels");
   ARG(p->max_iters >= 1 && p->max_iters <= 4096, "max_iters must be 1..4096");
   ARG(std::isfinite(p->lambda_L_rel) && p->lambda_L_rel >= 0, "lambda_L_rel must be finite, >= 0");
   ARG(std::isfinite(p->lambda_S_rel) && p->lambda_S_rel >= 0, "lambda_S_rel must be finite, >= 0");
@@ -259,6 +262,7 @@ int validate(const lps_params* p, Geom* gout) {
   g.planeP = p->nz * g.nyp + ((p->nz * g.nyp) & 1);
   g.fft_z = p->fft_z;
   g.J = p->wavelet_levels;
+  g.wz = p->wavelet_dims == 3 ? 1 : 0;
   g.ntiles = (p->nx / 8) * (p->ny / 8);
   g.N = (long long)p->nx * p->ny * p->nz;
   g.scale_yz = (float)(1.0 / std::sqrt((double)p->ny * (p->fft_z ? p->nz : 1)));
@@ -746,6 +750,7 @@ int lps_params_init(lps_params* p) {
   p->layout = LPS_LAYOUT_SLICES;
   p->fft_z = 1;
   p->wavelet_levels = 3;
+  p->wavelet_dims = 2;
   p->max_iters = 50;
   p->lambda_L_rel = 0.01;
   p->lambda_S_rel = 0.005;
@@ -975,6 +980,7 @@ int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev
 int lps_shift_prior_columns(lps_plan* P, int shift) {
   ARG(P != nullptr, "plan is NULL");
   ARG(shift >= 1 && shift < P->g.nz, "shift must be in 1..nz-1");
+  ARG(!P->g.wz, "the 3D Haar mixes the columns of a z block: its support has no per-column shift");
   // support words of one Casorati column (the coefficients of one slice or frame are
   // contiguous: the column index is the outermost of the tile-major numbering)
   const size_t wpc = (size_t)P->g.nx * P->g.ny / 32;
@@ -1365,7 +1371,7 @@ int lps_slab_end(lps_plan* P, const float* rec, lps_stats* stats) {
 // Checkpoint layout: header, prior support words, prior sigma, L, S, X, lambdas.
 struct CkptHeader {
   uint32_t magic, version;
-  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done, v_valid, pad;
+  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done, v_valid, wz;
   double lambda_L, lambda_S;
 };
 
@@ -1384,7 +1390,7 @@ int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
   CK(cudaMemcpyAsync(&dp, P->persist, sizeof(DevPersist), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
   CkptHeader h{0x4c50531a, 2, P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.J, dp.has_sup,
-               dp.has_sigma, P->iters_done, dp.v_valid, 0, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
+               dp.has_sigma, P->iters_done, dp.v_valid, P->g.wz, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
   unsigned char* o = (unsigned char*)buf;
   std::memcpy(o, &h, sizeof(h));
   o += sizeof(h);
@@ -1412,7 +1418,8 @@ int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   ARG(h.magic == 0x4c50531a && h.version == 2, "not a checkpoint of this library");
-  ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J, "checkpoint shape mismatch");
+  ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J && h.wz == P->g.wz,
+      "checkpoint shape mismatch");
   const unsigned char* i = (const unsigned char*)buf + sizeof(h);
   CK(cudaStreamSynchronize(P->st));
   CK(cudaMemcpy(P->sup_prior, i, w * 4, cudaMemcpyHostToDevice));

@@ -72,6 +72,7 @@ struct Geom {
   int mpad;                 // row stride (elements) of the hybrid data per (x, coil)
   int fft_z;                // 3D (1) or per-slice 2D (0) encode
   int J;                    // Haar levels
+  int wz;                   // 1: 3D Haar (the 2D pyramid times the 1D Haar along z), 0: per slice
   int ntiles;               // (nx/8)*(ny/8)
   long long N;              // nx*ny*nz
   float scale_yz;           // 1/sqrt(ny*nz) (fft_z) or 1/sqrt(ny)

@@ -37,7 +37,7 @@ def test_library_exports_every_declared_symbol(lps):
 
 def test_params_defaults_and_status_strings(lps):
     p = lps.params_init()
-    assert p.max_iters == 50 and p.wavelet_levels == 3 and p.fft_z == 1
+    assert p.max_iters == 50 and p.wavelet_levels == 3 and p.fft_z == 1 and p.wavelet_dims == 2
     assert abs(p.lambda_L_rel - 0.01) < 1e-15 and abs(p.lambda_S_rel - 0.005) < 1e-15
     assert lps.status_string(0) == "LPS_OK"
     assert lps.status_string(-1) == "LPS_ERR_INVALID_ARG"
@@ -48,6 +48,7 @@ def test_params_defaults_and_status_strings(lps):
     (dict(nx=12), -1), (dict(ny=0), -1), (dict(ncoil=0), -1), (dict(wavelet_levels=4), -1),
     (dict(lambda_p=1.5), -1), (dict(layout=2), -1), (dict(layout=1), -8), (dict(precision=3), -1),
     (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1), (dict(coil_format=2), -1),
+    (dict(wavelet_dims=1), -1), (dict(wavelet_dims=3, nz=12), -1), (dict(wavelet_dims=3, nz=6, wavelet_levels=2), -1),
 ])
 def test_plan_create_rejects_bad_params(lps, bad, code):
     kw = dict(nx=32, ny=32, nz=8, ncoil=2)
