@@ -38,6 +38,8 @@ in the design document of this repository):
   R7 singular values are matched to sigma_prev by rank (both descending); directions with
      sigma_i <= tau * sigma_1 are dropped after step (2) (rank guard).
   R8 soft(0, lambda) = 0; |x| = lambda gives 0.
+  R9 the 3D variant of T (wavelet_dims = 3) is the tensor product of the 2D pyramid of R6
+     with the J-level 1D Haar along z; nz a multiple of 2^J.
 """
 from __future__ import annotations
 
