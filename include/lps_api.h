@@ -251,9 +251,10 @@ int lps_get_recon(lps_plan* plan, void* out);
  * Not in the paper (it fixes no launch shapes): times, on the plan's resident coils, mask and
  * data, the candidate shapes of the two per-iteration kernels whose shape is a free choice,
  * and installs the fastest in the plan (its frame graph is captured again):
- *  - data consistency: the compile-time plane kernel where one exists, else/and the
- *    runtime-sized kernel with each candidate ordering of the FFT radix passes along y and z,
- *    coil planes staged in shared memory or read from global memory;
+ *  - data consistency: the compile-time plane kernel where one exists, the register-transform
+ *    coil loop where the plane has one, and the runtime-sized kernel with each candidate
+ *    ordering of the FFT radix passes along y and z, coil planes staged in shared memory or
+ *    read from global memory;
  *  - sparse update: 8x8 in-plane tiles per CTA.
  * Results are cached per geometry (nx, ny, nz, ncoil, fft_z, precision) for the process.
  * Requires lps_set_coils, lps_set_mask and lps_set_data; synchronises the plan's stream; the
@@ -263,7 +264,10 @@ typedef struct lps_tune_result {
                               coil planes staged in shared memory, 2: the same reading coil
                               maps from global memory (half the shared memory); 128 x 16
                               planes also: 3: register-transform kernel, 4 coil groups (the
-                              default there), 4: the same with 8 coil groups                */
+                              default there), 4: the same with 8 coil groups; planes of
+                              ny = 16 Q (Q = 4..10) by nz in {8, 10, ..., 16, 20, 24, 28, 32}:
+                              5: the runtime-sized kernel's update with its coil loop on
+                              register transforms (the default there)                      */
   int radix_y[8];          /* FFT passes along y of the runtime-sized kernel (0-terminated) */
   int radix_z[8];          /* FFT passes along z                                            */
   int lrs_tiles;           /* 8x8 tiles per CTA of the sparse-step kernel                   */
@@ -275,7 +279,8 @@ int lps_autotune(lps_plan* plan, lps_tune_result* out);
 int lps_autotune_clear_cache(void);
 /* Install a launch shape (for instance one measured by lps_autotune in an earlier process):
  * dc_variant, radix_y / radix_z (variants 1 and 2; their products must be ny and nz) and
- * lrs_tiles are used, the other fields ignored. Variants 3 and 4 need a 128 x 16 plane. Synchronises the plan's stream; the frame
+ * lrs_tiles are used, the other fields ignored. Variants 3 and 4 need a 128 x 16 plane,
+ * variant 5 a plane listed beside it. Synchronises the plan's stream; the frame
  * graph is captured again at the next frame. */
 int lps_apply_tune(lps_plan* plan, const lps_tune_result* tune);
 

@@ -281,6 +281,8 @@ int validate(const lps_params* p, Geom* gout) {
   // 128 x 16 planes: the update runs on the register-transform kernel (four coil groups; their
   // sums in shared memory when there are more than four coils)
   if (g.ny == 128 && g.nz == 16) g.dc_reg_groups = g.ncoil > 4 ? 104 : 4;
+  // planes of ny = 16 Q by even nz <= 32: the update's coil loop on register transforms
+  g.dc_rt = dc_rt_geometry(g) ? 1 : 0;
   if (dc_ept(g) < 0 || dc_smem_bytes(g) > 227 * 1024) {
     set_err("x-plane of %d x %d does not fit one CTA", p->ny, p->nz);
     return LPS_ERR_UNSUPPORTED;

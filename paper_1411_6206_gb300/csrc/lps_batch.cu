@@ -124,6 +124,7 @@ void install(lps_plan* P, const TuneEntry& t) {
   P->g.dc_generic = runtime;
   P->g.dc_direct = t.res.dc_variant == 2;
   P->g.dc_reg_groups = reg_groups_of(t.res.dc_variant, P->g.ncoil);
+  P->g.dc_rt = t.res.dc_variant == 5;
   if (runtime) {
     P->g.py = t.py;
     P->g.pz = t.pz;
@@ -248,11 +249,28 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
     return time_launches(P, e0, e1, 5, [&] { return launch_dc(a, kDcUpdate, P->st); }, us);
   };
   // data-consistency kernel: the compile-time plane kernel, the register-transform kernel in
-  // both group counts where the plane has one, then the runtime-sized candidates
+  // both group counts where the plane has one, the register-transform coil loop of k_dc, then
+  // the runtime-sized candidates
+  if (dc_rt_geometry(g0) && !P->coils_h) {
+    Geom g = g0;
+    g.dc_generic = 0;
+    g.dc_reg_groups = 0;
+    g.dc_rt = 1;
+    if (dc_rt_applies(g)) {
+      double us;
+      if ((rc = dc_time(g, &us))) goto done;
+      ++count;
+      if (us < best.res.dc_us) {
+        best.res.dc_variant = 5;
+        best.res.dc_us = us;
+      }
+    }
+  }
   if (dc_has_fixed(g0)) {
     for (int variant : {0, 3, 4}) {
       Geom g = g0;
       g.dc_generic = 0;
+      g.dc_rt = 0;
       g.dc_reg_groups = reg_groups_of(variant, g.ncoil);
       if (variant != 0 && !dc_reg_applies(g)) continue;
       double us;
@@ -274,6 +292,7 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
           g.dc_generic = 1;
           g.dc_direct = direct;
           g.dc_reg_groups = 0;
+          g.dc_rt = 0;
           g.py = py;
           g.pz = pz;
           double us;
@@ -336,11 +355,13 @@ done:
 
 int lps_apply_tune(lps_plan* P, const lps_tune_result* t) {
   ARG(P != nullptr && t != nullptr, "NULL argument");
-  ARG(t->dc_variant >= 0 && t->dc_variant <= 4, "dc_variant must be 0..4");
+  ARG(t->dc_variant >= 0 && t->dc_variant <= 5, "dc_variant must be 0..5");
   ARG(t->lrs_tiles >= 1 && t->lrs_tiles <= 32 / P->g.nc, "lrs_tiles must be in 1..32/nz");
   TuneEntry e{};
   e.res = *t;
-  if (t->dc_variant == 0 || t->dc_variant >= 3) {
+  if (t->dc_variant == 5) {
+    ARG(dc_rt_geometry(P->g), "no register-transform coil loop for this plane size");
+  } else if (t->dc_variant == 0 || t->dc_variant >= 3) {
     Geom g = P->g;
     g.dc_generic = 0;
     g.dc_reg_groups = reg_groups_of(t->dc_variant, g.ncoil);

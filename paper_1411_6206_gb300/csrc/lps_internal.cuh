@@ -82,6 +82,8 @@ struct Geom {
   int dc_direct;            // runtime-sized kernel reads coil maps from global memory (no staging)
   int lrs_tpc;              // 8x8 tiles per CTA of the sparse-step kernel (0: 32 / nc)
   int dc_reg_groups;        // register-transform DC kernel (128 x 16 planes): coil groups, 0 = off
+  int dc_rt;                // update on k_dc's register-transform coil loop where the plane has one
+  int dc_rt_dsm;            // that loop stages each coil's samples in shared memory (set at launch)
 };
 
 // ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
@@ -214,6 +216,8 @@ int lrs_tpc(const Geom& g);
 int lrs_threads(const Geom& g);
 bool dc_has_fixed(const Geom& g);
 bool dc_reg_applies(const Geom& g);
+bool dc_rt_geometry(const Geom& g);   // a register-transform instantiation exists for the plane
+bool dc_rt_applies(const Geom& g);
 cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);

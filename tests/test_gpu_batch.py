@@ -161,9 +161,10 @@ def test_installed_launch_shapes_keep_parity(L, variant, ry, rz):
 @pytest.mark.parametrize("size", [(144, 28, 13), (160, 14, 16)])
 def test_mix_member_full_size_matches_oracle(L, size):
     """Two members of the serving mix at full size (in-plane 144 = 16 * 9 and 160 = 32 * 5,
-    13 and 16 coils, first frame at 50% of the lines, 50 iterations), through the runtime-sized
-    kernel with the launch shape the autotuner picks, against the oracle: NRMSE <= 1e-3 and
-    support bits equal except within the tie band of lambda_S."""
+    13 and 16 coils, first frame at 50% of the lines, 50 iterations), with the data-consistency
+    kernel the autotuner picks (register-transform coil loop or runtime-sized Stockham passes),
+    against the oracle: NRMSE <= 1e-3 and support bits equal except within the tie band of
+    lambda_S."""
     import os
     import scipy.fft as sfft
     from paper_1411_6206_gb300 import phantom as P
@@ -179,7 +180,7 @@ def test_mix_member_full_size_matches_oracle(L, size):
     pl.set_mask(mask)
     pl.set_data(dev(d))
     r = pl.autotune()
-    assert r.dc_variant in (1, 2)          # no compile-time plane kernel for this size
+    assert r.dc_variant in (1, 2, 5)       # no compile-time plane kernel for this size
     recon = torch.empty((w.nz, w.nx, w.ny), dtype=torch.complex64, device="cuda")
     sup = np.empty(pl.support_words(), np.uint32)
     st = pl.reconstruct_frame(recon=recon, support=sup)
