@@ -3,6 +3,8 @@
 // k_dc_rt_nz*.cu).
 #include "k_dc.cuh"
 
+#include <algorithm>
+
 namespace lps {
 
 int dc_ept(const Geom& g) { return dc_ept_of(g.plane); }
@@ -47,11 +49,10 @@ cudaError_t launch_dc_fixed(const DcArgs& a, int mode, cudaStream_t st);
 
 // Shared memory of the register-transform update: the direct kernel's layout with the W
 // region replaced by the larger of itself and the transform loop's region.
-static size_t dc_rt_smem_bytes(const Geom& g, bool stage_d) {
+static size_t dc_rt_smem_bytes(const Geom& g, int dsm_slots) {
   Geom gd = g;
   gd.dc_direct = 1;
-  return dc_smem_bytes(gd) - (size_t)g.nz * g.nz * sizeof(float2) +
-         rt_region_bytes(g.nz, g.ny, stage_d ? g.mpad : 0);
+  return dc_smem_bytes(gd) - (size_t)g.nz * g.nz * sizeof(float2) + rt_region_bytes(g.nz, g.ny, dsm_slots);
 }
 
 bool dc_rt_geometry(const Geom& g) {
@@ -64,17 +65,19 @@ bool dc_rt_geometry(const Geom& g) {
 }
 
 bool dc_rt_applies(const Geom& g) {
-  return g.dc_rt && !g.dc_generic && dc_rt_geometry(g) && dc_rt_smem_bytes(g, false) <= 227 * 1024;
+  return g.dc_rt && !g.dc_generic && dc_rt_geometry(g) && dc_rt_smem_bytes(g, 0) <= 227 * 1024;
 }
 
 // cudaErrorNotSupported where the plane has no register-transform instantiation (or the plan
 // keeps half-precision coil maps, which the runtime-sized kernel reads).
 static cudaError_t launch_dc_rt(const DcArgs& a, cudaStream_t st) {
   if (!dc_rt_applies(a.g) || a.coils_h) return cudaErrorNotSupported;
-  // the samples of a coil go to shared memory where they fit, else are read from L2
+  // slots for a coil's samples in shared memory: the line capacity, or what is left of the
+  // 227 KB (a frame with more lines reads them from L2)
   DcArgs b = a;
-  b.g.dc_rt_dsm = dc_rt_smem_bytes(a.g, true) <= 227 * 1024 ? 1 : 0;
-  const size_t smem = dc_rt_smem_bytes(b.g, b.g.dc_rt_dsm != 0);
+  const size_t fixed = dc_rt_smem_bytes(a.g, 0);
+  b.g.dc_rt_dsm = (int)std::min<size_t>((size_t)a.g.mpad, (227 * 1024 - fixed) / sizeof(float2)) & ~1;
+  const size_t smem = dc_rt_smem_bytes(b.g, b.g.dc_rt_dsm);
 #define LPS_RT_DISPATCH(NZ) \
   case NZ: return launch_dc_rt_nz<NZ>(b, smem, st);
   switch (a.g.nz) {

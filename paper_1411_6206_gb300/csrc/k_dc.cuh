@@ -98,7 +98,7 @@ __device__ __forceinline__ void xlane_inv(float2 (&v)[Q], int l, float2 w16, flo
 // region (which it reuses): frequency rows, two coil-map stages, the samples, the mask
 // bitmap and its prefix counts.
 __host__ __device__ constexpr int rt_ps(int Q) { return 16 * (Q | 1); }
-// mpad: the samples' staging slots (0 when d' is read from global memory).
+// mpad: the samples' staging slots (complex elements).
 __host__ __device__ inline size_t rt_region_bytes(int nz, int ny, int mpad) {
   const int Q = ny / 16, WB = (ny + 31) / 32;
   const size_t sf = (size_t)nz * rt_ps(Q) > (size_t)nz * nz ? (size_t)nz * rt_ps(Q) : (size_t)nz * nz;
@@ -118,8 +118,10 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
   float2* stg0 = Sf + SF;
   float2* stg1 = stg0 + NZ * NY;
   float2* dsm = stg1 + NZ * NY;
-  const bool stage_d = g.dc_rt_dsm != 0;   // samples staged in shared memory (when they fit)
-  unsigned* rbits = reinterpret_cast<unsigned*>(dsm + (stage_d ? g.mpad : 0));
+  // the coil's samples are staged in shared memory when the frame's lines fit the slots the
+  // launch provided, else read from L2
+  const bool stage_d = m <= g.dc_rt_dsm;
+  unsigned* rbits = reinterpret_cast<unsigned*>(dsm + g.dc_rt_dsm);
   int* rpre = reinterpret_cast<int*>(rbits + NZ * WB);
   const int tid = threadIdx.x, l = tid & 15;
   const int nyp = g.nyp;
@@ -192,7 +194,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     cp_async_commit();
     cp_async_wait<2>();   // this thread's map elements of coil c
     // row phase, forward
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < RT; ++r) {
       const int t = tid + r * kThreads;
       if (t < NT) {
@@ -241,7 +243,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     }
     __syncthreads();
     // row phase, inverse, and the conjugate-coil sum
-#pragma unroll
+#pragma unroll 1
     for (int r = 0; r < RT; ++r) {
       const int t = tid + r * kThreads;
       if (t < NT) {

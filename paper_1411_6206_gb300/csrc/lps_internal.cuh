@@ -83,7 +83,7 @@ struct Geom {
   int lrs_tpc;              // 8x8 tiles per CTA of the sparse-step kernel (0: 32 / nc)
   int dc_reg_groups;        // register-transform DC kernel (128 x 16 planes): coil groups, 0 = off
   int dc_rt;                // update on k_dc's register-transform coil loop where the plane has one
-  int dc_rt_dsm;            // that loop stages each coil's samples in shared memory (set at launch)
+  int dc_rt_dsm;            // that loop's shared-memory slots for a coil's samples (set at launch)
 };
 
 // ---- data-consistency / adjoint / forward kernel (one CTA per x-plane) -------------
