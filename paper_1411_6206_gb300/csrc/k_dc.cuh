@@ -94,6 +94,10 @@ __device__ __forceinline__ void xlane_inv(float2 (&v)[Q], int l, float2 w16, flo
   }
 }
 
+// Threads of a k_dc CTA: 512 for the register-transform loop of planes with nz >= 20 (one row
+// task per thread, a thread pair per z column), else kThreads.
+__host__ __device__ constexpr int dc_threads(int rtz, int rtq) { return (rtq > 0 && rtz >= 20) ? 512 : kThreads; }
+
 // Shared memory of the register-transform loop, from the start of the iteration-form W
 // region (which it reuses): frequency rows, two coil-map stages, the samples, the mask
 // bitmap and its prefix counts.
@@ -105,12 +109,38 @@ __host__ __device__ inline size_t rt_region_bytes(int nz, int ny, int mpad) {
   return (sf + 2 * (size_t)nz * ny + (size_t)mpad) * sizeof(float2) + 2 * (size_t)nz * WB * sizeof(int);
 }
 
-template <int NZ, int Q>
+// One z column split over a thread pair (h = 0, 1): thread h holds the samples z = 2m + h,
+// transforms them (H = NZ/2 points), and one radix-2 step across the pair leaves it holding
+// kz = k + h H. The inverse mirrors it (thread h ends with z = 2m + h again).
+template <int NZ, bool INV>
+__device__ __forceinline__ void zpair_dft(float2 (&v)[NZ / 2], int h) {
+  constexpr int H = NZ / 2;
+  if constexpr (!INV) {
+    dftr::dft<H, false>(v);
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 o = h ? dftr::rot<NZ, false>(v[k], k) : v[k];
+      const float2 p = shfl_xor2(o, 1);
+      v[k] = h ? csub(p, o) : cadd(o, p);
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < H; ++k) {
+      const float2 p = shfl_xor2(v[k], 1);
+      v[k] = h ? dftr::rot<NZ, true>(csub(p, v[k]), k) : cadd(v[k], p);
+    }
+    dftr::dft<H, true>(v);
+  }
+}
+
+template <int NZ, int Q, int NTH>
 __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __restrict__ zbuf,
                                              float2* __restrict__ abuf, const float2* __restrict__ twy,
                                              float2* region, int x, int m) {
   constexpr int L = 16, QP = Q | 1, PS = L * QP, NY = L * Q, WB = (NY + 31) / 32;
-  constexpr int NT = NZ * L, RT = (NT + kThreads - 1) / kThreads;
+  constexpr int NT = NZ * L, RT = (NT + NTH - 1) / NTH;
+  constexpr bool PAIR = NZ >= 20;   // z columns on thread pairs
+  static_assert(!PAIR || (NZ % 2 == 0 && 2 * NY <= NTH), "thread pairs per column");
   static_assert(NT % 32 == 0, "whole warps of row tasks");
   constexpr int SF = NZ * PS > NZ * NZ ? NZ * PS : NZ * NZ;
   const Geom& g = a.g;
@@ -130,9 +160,9 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
 
   // mask bitmap: bit ky of word (kz, ky / 32); rpre = line number of the word's first bit
   // (lines are numbered in raster order of (kz, ky))
-  for (int i = tid; i < NZ * WB; i += kThreads) rbits[i] = 0u;
+  for (int i = tid; i < NZ * WB; i += NTH) rbits[i] = 0u;
   __syncthreads();
-  for (int i = tid; i < m; i += kThreads) {
+  for (int i = tid; i < m; i += NTH) {
     const int p = a.lines[i];
     const int kz = p / nyp, ky = p - (p / nyp) * nyp;
     atomicOr(&rbits[kz * WB + (ky >> 5)], 1u << (ky & 31));
@@ -172,7 +202,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     const float2* base = a.coils + (long long)c * g.N + (long long)x * NY;
 #pragma unroll
     for (int r = 0; r < RT; ++r) {
-      const int t = tid + r * kThreads;
+      const int t = tid + r * NTH;
       if (t < NT) {
         const int z = t >> 4;
 #pragma unroll
@@ -187,7 +217,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     const float2* stg = (c & 1) ? stg1 : stg0;
     const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
     if (stage_d)
-      for (int i = tid; i < m; i += kThreads) cp_async8(dsm + i, dh + i);
+      for (int i = tid; i < m; i += NTH) cp_async8(dsm + i, dh + i);
     const float2* dsrc = stage_d ? dsm : dh;
     cp_async_commit();
     if (c + 1 < g.ncoil) issue_stage(c + 1, (c & 1) ? stg0 : stg1);
@@ -196,7 +226,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     // row phase, forward
 #pragma unroll 1
     for (int r = 0; r < RT; ++r) {
-      const int t = tid + r * kThreads;
+      const int t = tid + r * NTH;
       if (t < NT) {
         const int z = t >> 4;
         float2 v[Q];
@@ -216,36 +246,67 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
     cp_async_wait<1>();   // the samples of coil c (this thread's share)
     __syncthreads();
     // column phase: z transform, residual on the sampled lines, inverse z transform
-    for (int ky = tid; ky < NY; ky += kThreads) {
+    if constexpr (!PAIR) {
+      for (int ky = tid; ky < NY; ky += NTH) {
+        const int k2 = ky / Q, k1 = ky - k2 * Q;
+        const int off = (int)(__brev((unsigned)k2) >> 28) * QP + k1;
+        float2 v[NZ];
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) v[z] = Sf[z * PS + off];
+        if (g.fft_z) dftr::dft<NZ, false>(v);
+        const int wi = ky >> 5;
+        const unsigned bit = ky & 31, below = (1u << bit) - 1u;
+#pragma unroll
+        for (int kz = 0; kz < NZ; ++kz) {
+          const unsigned bits = rbits[kz * WB + wi];
+          if ((bits >> bit) & 1u) {
+            const int line = rpre[kz * WB + wi] + __popc(bits & below);
+            const float2 r = csub(v[kz], dsrc[line]);
+            resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
+            v[kz] = r;
+          } else {
+            v[kz] = make_float2(0.f, 0.f);
+          }
+        }
+        if (g.fft_z) dftr::dft<NZ, true>(v);
+#pragma unroll
+        for (int z = 0; z < NZ; ++z) Sf[z * PS + off] = v[z];
+      }
+    } else if (tid < 2 * NY) {   // whole warps (2 NY = 32 Q)
+      constexpr int H = NZ / 2;
+      const int ky = tid >> 1, h = tid & 1;
       const int k2 = ky / Q, k1 = ky - k2 * Q;
       const int off = (int)(__brev((unsigned)k2) >> 28) * QP + k1;
-      float2 v[NZ];
+      float2 v[H];
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) v[z] = Sf[z * PS + off];
-      if (g.fft_z) dftr::dft<NZ, false>(v);
+      for (int m2 = 0; m2 < H; ++m2) v[m2] = Sf[(2 * m2 + h) * PS + off];
+      const bool fz = g.fft_z != 0;
+      if (fz) zpair_dft<NZ, false>(v, h);
       const int wi = ky >> 5;
       const unsigned bit = ky & 31, below = (1u << bit) - 1u;
 #pragma unroll
-      for (int kz = 0; kz < NZ; ++kz) {
+      for (int k = 0; k < H; ++k) {
+        // frequency kz = k + h H after the transform; slice 2k + h without it
+        const int kz = fz ? k + h * H : 2 * k + h;
         const unsigned bits = rbits[kz * WB + wi];
         if ((bits >> bit) & 1u) {
           const int line = rpre[kz * WB + wi] + __popc(bits & below);
-          const float2 r = csub(v[kz], dsrc[line]);
+          const float2 r = csub(v[k], dsrc[line]);
           resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
-          v[kz] = r;
+          v[k] = r;
         } else {
-          v[kz] = make_float2(0.f, 0.f);
+          v[k] = make_float2(0.f, 0.f);
         }
       }
-      if (g.fft_z) dftr::dft<NZ, true>(v);
+      if (fz) zpair_dft<NZ, true>(v, h);
 #pragma unroll
-      for (int z = 0; z < NZ; ++z) Sf[z * PS + off] = v[z];
+      for (int m2 = 0; m2 < H; ++m2) Sf[(2 * m2 + h) * PS + off] = v[m2];
     }
     __syncthreads();
     // row phase, inverse, and the conjugate-coil sum
 #pragma unroll 1
     for (int r = 0; r < RT; ++r) {
-      const int t = tid + r * kThreads;
+      const int t = tid + r * NTH;
       if (t < NT) {
         const int z = t >> 4;
         float2 v[Q];
@@ -278,7 +339,8 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
 // RTZ, RTQ > 0: the coil loop of the update runs on register transforms (dc_rt_coils) for
 // planes of ny = 16 RTQ by nz = RTZ.
 template <int EPT, int MODE, bool STAGE, bool HALF, int RTZ = 0, int RTQ = 0>
-__global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(const DcArgs a) {
+__global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1 : 2) k_dc(const DcArgs a) {
+  constexpr int NTH = dc_threads(RTZ, RTQ);
   static_assert(!(HALF && (STAGE || MODE != kDcUpdate)), "half-precision coil maps: direct update only");
   static_assert(RTQ == 0 || (MODE == kDcUpdate && !STAGE && !HALF), "register transforms: direct float32 update only");
   const Geom& g = a.g;
@@ -304,8 +366,8 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
   const int m = a.persist->nlines;
   int* errp = a.ctrl ? &a.ctrl->err : nullptr;
 
-  for (int i = tid; i < ny; i += kThreads) twy[i] = a.tw_y[i];
-  for (int i = tid; i < nz; i += kThreads) twz[i] = a.tw_z[i];
+  for (int i = tid; i < ny; i += NTH) twy[i] = a.tw_y[i];
+  for (int i = tid; i < nz; i += NTH) twz[i] = a.tw_z[i];
   if (STAGE && tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -329,7 +391,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
     }
   }
 
-  // Element ownership for the elementwise phases: e = tid + k*kThreads.
+  // Element ownership for the elementwise phases: e = tid + k*NTH.
   float2 Zr[EPT];
   float2 acc[EPT];
   int pe[EPT];    // padded offset z*nyp + y
@@ -342,7 +404,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
   float2 Dz[EPT];
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int e = tid + k * kThreads;
+    const int e = tid + k * NTH;
     acc[k] = make_float2(0.f, 0.f);
     Zr[k] = Dz[k] = make_float2(0.f, 0.f);
     pe[k] = -1;
@@ -369,10 +431,10 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
   if (iter_form && a.W) {
     // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns,
     // one pixel column and 4 output slices per task, into bufB.
-    for (int i = tid; i < nz * nz; i += kThreads) wsh[i] = a.W[i];
+    for (int i = tid; i < nz * nz; i += NTH) wsh[i] = a.W[i];
     __syncthreads();
     const int nzb = (nz + 3) / 4;
-    for (int task = tid; task < ny * nzb; task += kThreads) {
+    for (int task = tid; task < ny * nzb; task += NTH) {
       const int y = task % ny, zb = (task / ny) * 4;
       float2 o[4];
 #pragma unroll
@@ -398,7 +460,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
       if (pe[k] < 0) continue;
-      const int e = tid + k * kThreads;
+      const int e = tid + k * NTH;
       const int z = e / ny, y = e - (e / ny) * ny;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
       const float2 Lk = a.W ? bufB[pe[k]] : a.Lpre[gi];
@@ -421,11 +483,11 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
         bufB[pe[k]] = make_float2(0.f, 0.f);
       }
     __syncthreads();
-    resid = dc_rt_coils<RTZ, RTQ>(a, bufA, bufB, twy, wsh, x, m);
+    resid = dc_rt_coils<RTZ, RTQ, NTH>(a, bufA, bufB, twy, wsh, x, m);
     __syncthreads();
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      const int e = tid + k * kThreads;
+      const int e = tid + k * NTH;
       const int z = e / ny, y = e - (e / ny) * ny;
       const bool in = e < plane;
       pe[k] = in ? z * nyp + y : -1;
@@ -455,7 +517,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
       // P = scale * C_c * Z, then the forward transform over y (rows) and z (columns).
 #pragma unroll
       for (int k = 0; k < EPT; ++k) {
-        const int e = tid + k * kThreads;
+        const int e = tid + k * NTH;
         if (e < plane) src[pe[k]] = cscale(cmul(STAGE ? coil[e] : gc(k), Zr[k]), sc);
       }
       __syncthreads();
@@ -463,7 +525,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
       if (g.fft_z) fft_run(&src, &dst, g.pz, ny, nyp, 1, twz, false);
       if (MODE == kDcForward) {
         float2* ho = a.hyb_out + ((long long)x * g.ncoil + c) * g.mpad;
-        for (int l = tid; l < m; l += kThreads) ho[l] = src[a.lines[l]];
+        for (int l = tid; l < m; l += NTH) ho[l] = src[a.lines[l]];
         __syncthreads();
         if (STAGE && tid == 0 && c + 2 < g.ncoil) {
           fence_proxy_async();
@@ -478,7 +540,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
     for (int k = 0; k < EPT; ++k)
       if (pe[k] >= 0) dst[pe[k]] = make_float2(0.f, 0.f);
     __syncthreads();
-    for (int l = tid; l < m; l += kThreads) {
+    for (int l = tid; l < m; l += NTH) {
       const int p = a.lines[l];
       float2 r;
       if (MODE == kDcAdjoint) {
@@ -499,7 +561,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
     fft_run(&src, &dst, g.py, nz, 1, nyp, twy, true);
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
-      const int e = tid + k * kThreads;
+      const int e = tid + k * NTH;
       if (e < plane) {
         const float2 r = src[pe[k]];
         const float2 cc = STAGE ? coil[e] : gc(k);
@@ -521,7 +583,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
   // X = Z - E^H(E Z - d)  (update) or X_0 = E^H d (adjoint); then M = X - S into bufA.
 #pragma unroll
   for (int k = 0; k < EPT; ++k) {
-    const int e = tid + k * kThreads;
+    const int e = tid + k * NTH;
     if (e < plane) {
       const int z = e / ny, y = e - (e / ny) * ny;
       const long long gi = (long long)z * xy + (long long)x * ny + y;
@@ -545,7 +607,7 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
     // Plane share of G = M^H M: G[i][j] = sum_y conj(M[i][y]) M[j][y], columns i, j = slices.
     const int nc = g.nc;
     float2* gp = a.gram_part + (long long)x * nc * nc;
-    for (int t = tid; t < nc * nc; t += kThreads) {
+    for (int t = tid; t < nc * nc; t += NTH) {
       const int i = t / nc, j = t - (t / nc) * nc;
       if (i > j) continue;
       const float2* ri = bufA + i * nyp;
@@ -571,14 +633,14 @@ __global__ void __launch_bounds__(kThreads, (STAGE || RTZ >= 20) ? 1 : 2) k_dc(c
 
 // Elements per thread of the runtime-sized kernel's elementwise phases, rounded up to the
 // compiled values (1, 2, 4, 8, 16, 24; -1: plane too large).
-__host__ __device__ constexpr int dc_ept_of(int plane) {
-  return (plane + kThreads - 1) / kThreads <= 1   ? 1
-         : (plane + kThreads - 1) / kThreads <= 2 ? 2
-         : (plane + kThreads - 1) / kThreads <= 4 ? 4
-         : (plane + kThreads - 1) / kThreads <= 8 ? 8
-         : (plane + kThreads - 1) / kThreads <= 16 ? 16
-         : (plane + kThreads - 1) / kThreads <= 24 ? 24
-                                                  : -1;
+__host__ __device__ constexpr int dc_ept_of(int plane, int nth = kThreads) {
+  return (plane + nth - 1) / nth <= 1   ? 1
+         : (plane + nth - 1) / nth <= 2 ? 2
+         : (plane + nth - 1) / nth <= 4 ? 4
+         : (plane + nth - 1) / nth <= 8 ? 8
+         : (plane + nth - 1) / nth <= 16 ? 16
+         : (plane + nth - 1) / nth <= 24 ? 24
+                                        : -1;
 }
 
 template <int EPT, int MODE, bool STAGE, bool HALF, int RTZ = 0, int RTQ = 0>
@@ -590,7 +652,8 @@ static cudaError_t launch_dc_t(const DcArgs& a, size_t smem, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  cudaError_t e = launch_pdl(k_dc<EPT, MODE, STAGE, HALF, RTZ, RTQ>, dim3(a.g.nx), dim3(kThreads), smem, st, a);
+  cudaError_t e = launch_pdl(k_dc<EPT, MODE, STAGE, HALF, RTZ, RTQ>, dim3(a.g.nx), dim3(dc_threads(RTZ, RTQ)), smem,
+                             st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -599,7 +662,7 @@ template <int NZ>
 cudaError_t launch_dc_rt_nz(const DcArgs& a, size_t smem, cudaStream_t st) {
 #define LPS_RT_CASE(Q)                                                                     \
   case Q:                                                                                  \
-    return launch_dc_t<dc_ept_of(16 * Q * NZ), kDcUpdate, false, false, NZ, Q>(a, smem, st);
+    return launch_dc_t<dc_ept_of(16 * Q * NZ, dc_threads(NZ, Q)), kDcUpdate, false, false, NZ, Q>(a, smem, st);
   switch (a.g.ny / 16) {
     LPS_RT_CASE(4)
     LPS_RT_CASE(5)
