@@ -651,6 +651,11 @@ def run_served(args):
     res = {mode: serve_once(lps, ws_, inputs, trace, mode == "plain", 0) for mode in ("served", "plain")}
     out = dict(res["served"])
     out["plain"] = res["plain"]
+    # the same offered load over twice the arrival window: with capacity above the load the
+    # latency percentiles stay put instead of growing with the queue
+    long_s = 2.0 * args.serve_seconds
+    out["long_window"] = dict(serve_once(lps, ws_, inputs, serve_trace(len(ws_), rate, long_s, seed=9), False, 0),
+                              window_s=long_s)
     out.update({"sessions": len(ws_), "arrival_rate_per_session": rate, "offered_frames_per_s": rate * len(ws_),
                 "window_s": args.serve_seconds, "hbm_budget_bytes": 150 * 10 ** 9,
                 "sizes": [f"{w.nx}x{w.ny}x{w.nz}x{w.ncoil}c" for w in ws_],

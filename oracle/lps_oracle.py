@@ -24,7 +24,9 @@ fusion or algebraic shortcut beyond what the definition states:
 
 Readings of passages that are silent, ambiguous or garbled (each is listed with its reason
 in the design document of this repository):
-  R1 Casorati columns are the nz slices of one volume (Sec. 2): M in C^{(nx ny) x nz}.
+  R1 Casorati columns are the nz slices of one volume (Sec. 2): M in C^{(nx ny) x nz}; the
+     "frames" layout takes columns of frame_slices consecutive slices (3D frame volumes, each
+     with its own 3D encode and mask) instead.
   R2 lambda_L = lambda_L_rel * sigma_max(X_0), lambda_S = lambda_S_rel * max|T(X_0)|,
      fixed once per frame (the paper gives no values; lambda_T in the input list of
      Algorithm 1 is read as lambda_L).
@@ -65,18 +67,32 @@ def _axes(fft_z: int):
     return (0, 1, 2) if fft_z else (1, 2)
 
 
-def E(x: np.ndarray, coils: np.ndarray, mask: np.ndarray, fft_z: int = 1) -> np.ndarray:
+def _fft(a: np.ndarray, fft_z: int, zblock: Optional[int], inverse: bool) -> np.ndarray:
+    """Orthonormal DFT over (z, x, y) of an image [nz][nx][ny]: over all nz slices (fft_z = 1),
+    per slice (fft_z = 0), or over each aligned block of `zblock` slices separately (the 3D
+    encode of every frame volume when the Casorati columns are volumes of zblock slices)."""
+    f = sfft.ifftn if inverse else sfft.fftn
+    if zblock is None or zblock == a.shape[0]:
+        return f(a, axes=_axes(fft_z), norm="ortho")
+    nz, nx, ny = a.shape
+    blocks = a.reshape(nz // zblock, zblock, nx, ny)
+    return f(blocks, axes=(1, 2, 3), norm="ortho").reshape(nz, nx, ny)
+
+
+def E(x: np.ndarray, coils: np.ndarray, mask: np.ndarray, fft_z: int = 1,
+      zblock: Optional[int] = None) -> np.ndarray:
     """d = M F (C x): image [nz][nx][ny] -> samples [ncoil][m][nx] (Sec. 2, acquisition)."""
     kz, ky = line_index(mask)
     ncoil = coils.shape[0]
     out = np.empty((ncoil, kz.size, x.shape[1]), np.complex128)
     for c in range(ncoil):
-        K = sfft.fftn(coils[c] * x, axes=_axes(fft_z), norm="ortho")
+        K = _fft(coils[c] * x, fft_z, zblock, False)
         out[c] = K[kz, :, ky]
     return out
 
 
-def EH(d: np.ndarray, coils: np.ndarray, mask: np.ndarray, fft_z: int = 1) -> np.ndarray:
+def EH(d: np.ndarray, coils: np.ndarray, mask: np.ndarray, fft_z: int = 1,
+       zblock: Optional[int] = None) -> np.ndarray:
     """x = sum_c conj(C_c) F^H M^T d_c: samples [ncoil][m][nx] -> image [nz][nx][ny]."""
     kz, ky = line_index(mask)
     ncoil, nz, nx, ny = coils.shape
@@ -84,7 +100,7 @@ def EH(d: np.ndarray, coils: np.ndarray, mask: np.ndarray, fft_z: int = 1) -> np
     for c in range(ncoil):
         K = np.zeros((nz, nx, ny), np.complex128)
         K[kz, :, ky] = d[c]
-        x += np.conj(coils[c]) * sfft.ifftn(K, axes=_axes(fft_z), norm="ortho")
+        x += np.conj(coils[c]) * _fft(K, fft_z, zblock, True)
     return x
 
 
@@ -206,28 +222,29 @@ def soft(x: np.ndarray, lam: float) -> np.ndarray:
     return x * scale
 
 
-def casorati(x: np.ndarray) -> np.ndarray:
-    """[nz][nx][ny] -> Casorati matrix [(nx ny)][nz], one column per slice (R1)."""
+def casorati(x: np.ndarray, cs: int = 1) -> np.ndarray:
+    """[nz][nx][ny] -> Casorati matrix [(cs nx ny)][nz / cs]: one column per slice (R1), or,
+    with cs > 1, per volume of cs consecutive slices (the "frames" layout of 3D frames)."""
     nz = x.shape[0]
-    return x.reshape(nz, -1).T
+    return x.reshape(nz // cs, -1).T
 
 
 def uncasorati(m: np.ndarray, shape) -> np.ndarray:
     return m.T.reshape(shape)
 
 
-def casorati_gram(X: np.ndarray, S: Optional[np.ndarray] = None) -> np.ndarray:
+def casorati_gram(X: np.ndarray, S: Optional[np.ndarray] = None, cs: int = 1) -> np.ndarray:
     """G = M^H M of the Casorati matrix M = casorati(X - S): the small Hermitian matrix
     whose eigenpairs are the squared singular values and right singular vectors that the
     singular-value thresholding of step (1) (Sec. 3) acts on. Plain definition, FP64."""
-    M = casorati(X if S is None else X - S).astype(np.complex128)
+    M = casorati(X if S is None else X - S, cs).astype(np.complex128)
     return M.conj().T @ M
 
 
-def reproject(X: np.ndarray, S: Optional[np.ndarray], W: np.ndarray) -> np.ndarray:
+def reproject(X: np.ndarray, S: Optional[np.ndarray], W: np.ndarray, cs: int = 1) -> np.ndarray:
     """L = uncasorati((X - S) W): with W = V diag(sigma''/sigma) V^H this is the low-rank
     term U diag(sigma'') V^H of steps (1)-(2) (Sec. 3). Plain definition, FP64."""
-    M = casorati(X if S is None else X - S).astype(np.complex128)
+    M = casorati(X if S is None else X - S, cs).astype(np.complex128)
     return uncasorati(M @ np.asarray(W, np.complex128), X.shape)
 
 
@@ -274,6 +291,7 @@ class Params:
     fft_z: int = 1
     support_rule: str = "threshold"   # or "nonzero"
     wavelet_dims: int = 2             # 2: per-slice 2D Haar (R6); 3: 3D tensor-product Haar
+    frame_slices: int = 1             # slices per Casorati column (> 1: columns are 3D frames)
 
 
 @dataclasses.dataclass
@@ -301,8 +319,16 @@ class Prior:
     sigma: Optional[np.ndarray] = None     # sigma'' of the previous frame, rank order
 
 
+def zblock_of(p: Params) -> Optional[int]:
+    """Slices per z transform of E: each frame volume alone when the columns are 3D frames
+    (its slices with the 3D encode, one at a time without it), else the fft_z default."""
+    if p.frame_slices > 1:
+        return p.frame_slices if p.fft_z else 1
+    return None
+
+
 def initial_lambdas(X0: np.ndarray, p: Params):
-    s = np.linalg.svd(casorati(X0), compute_uv=False)
+    s = np.linalg.svd(casorati(X0, p.frame_slices), compute_uv=False)
     Tf, _ = sparsifying(p)
     return p.lambda_L_rel * s[0], p.lambda_S_rel * np.max(np.abs(Tf(X0, p.wavelet_levels)))
 
@@ -317,8 +343,9 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
     J = p.wavelet_levels
     Tf, Tfinv = sparsifying(p)
     K = p.max_iters if iters is None else iters
+    zb, cs = zblock_of(p), p.frame_slices
     if state is None:
-        X = EH(d, coils, mask, p.fft_z)               # (0) X_0 = A^{-1}(y)
+        X = EH(d, coils, mask, p.fft_z, zb)           # (0) X_0 = A^{-1}(y)
         S = np.zeros_like(X)                          #     S_0 = 0
         Lp = X.copy()                                 #     L_0 := X_0 (R3)
         lamL, lamS = initial_lambdas(X, p)            # R2
@@ -335,21 +362,21 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
     c = np.zeros_like(X)
     it = 0
     L = Lp
-    s2 = np.zeros(shape[0])
-    s = np.zeros(shape[0])
+    s2 = np.zeros(shape[0] // cs)
+    s = np.zeros(shape[0] // cs)
     for it in range(1, K + 1):
         Z_old = Lp + S
         # (1) singular-value soft-thresholding of X_{it-1} - S_{it-1}
         # (2) prior pull of the singular values towards those of L^(t-1)
-        Lm, s, s2 = svt(casorati(X - S), lamL, p.lambda_p, sig_prev, p.rank_tau)
+        Lm, s, s2 = svt(casorati(X - S, cs), lamL, p.lambda_p, sig_prev, p.rank_tau)
         L = uncasorati(Lm, shape)
         # (3) sparsity off the prior support
         c = Tf(X - Lp, J)
         c2 = support_shrink(c, lamS, keep)
         S = Tfinv(c2, J)
         # (4) data consistency
-        R = E(L + S, coils, mask, p.fft_z) - d
-        X = L + S - EH(R, coils, mask, p.fft_z)
+        R = E(L + S, coils, mask, p.fft_z, zb) - d
+        X = L + S - EH(R, coils, mask, p.fft_z, zb)
         Lp = L
         resid2 = float(np.vdot(R, R).real)
         off = np.ones(c.shape, bool) if keep is None else ~keep
@@ -372,8 +399,8 @@ def priori_ls(d, coils, mask, p: Params, prior: Optional[Prior] = None,
 def objective(L, S, d, coils, mask, lamL, lamS, keep, p: Params) -> float:
     """F(L, S) = 1/2 ||E(L + S) - d||^2 + lamL ||L||_* + lamS ||T(S)|_{off prior}||_1,
     the Lagrangian form of Eq. (3) without the sigma-closeness constraint (lambda_p = 0)."""
-    R = E(L + S, coils, mask, p.fft_z) - d
-    nuc = np.linalg.svd(casorati(L), compute_uv=False).sum()
+    R = E(L + S, coils, mask, p.fft_z, zblock_of(p)) - d
+    nuc = np.linalg.svd(casorati(L, p.frame_slices), compute_uv=False).sum()
     c = sparsifying(p)[0](S, p.wavelet_levels)
     off = np.ones(c.shape, bool) if keep is None else ~keep
     return 0.5 * float(np.vdot(R, R).real) + lamL * nuc + lamS * float(np.abs(c[off]).sum())

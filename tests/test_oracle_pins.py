@@ -84,6 +84,83 @@ def test_line_order_is_raster():
     assert list(zip(kz, ky)) == [(0, 3), (1, 0), (2, 1)]
 
 
+# ---------------------------------------------------------------- 3D frames as Casorati columns
+
+def brute_E_blocks(x, coils, mask, zb):
+    """d[c][l][kx] for line l = (z, ky), z = b zb + kz: the DFT of frame volume b alone,
+    sum over its zb slices, x and y of C x exp(-2 pi i (kx x/nx + ky y/ny + kz s/zb)) / sqrt(zb nx ny)."""
+    ncoil, nz, nx, ny = coils.shape
+    lines = np.argwhere(mask)
+    out = np.zeros((ncoil, len(lines), nx), complex)
+    ss, xx, yy = np.meshgrid(np.arange(zb), np.arange(nx), np.arange(ny), indexing="ij")
+    for c in range(ncoil):
+        img = coils[c] * x
+        for l, (z, ky) in enumerate(lines):
+            b, kz = divmod(z, zb)
+            vol = img[b * zb:(b + 1) * zb]
+            for kx in range(nx):
+                ph = np.exp(-2j * np.pi * (kx * xx / nx + ky * yy / ny + kz * ss / zb))
+                out[c, l, kx] = (vol * ph).sum() / np.sqrt(zb * nx * ny)
+    return out
+
+
+@pytest.mark.parametrize("zb", [2, 3])
+def test_E_frame_volumes_match_brute_force(zb):
+    nz, nx, ny, nc = 2 * zb, 4, 4, 2
+    coils = crandn(nc, nz, nx, ny)
+    mask = rand_mask(ny, nz, 0.5)
+    x = crandn(nz, nx, ny)
+    got = O.E(x, coils, mask, 1, zb)
+    assert np.abs(got - brute_E_blocks(x, coils, mask, zb)).max() < 1e-12
+    # adjoint identity of the frame-volume encode
+    y = crandn(nc, int(mask.sum()), nx)
+    lhs = np.vdot(got, y)
+    rhs = np.vdot(x, O.EH(y, coils, mask, 1, zb))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs)
+    # one block is the whole-volume encode, a block of one slice the per-slice encode
+    assert np.abs(O.E(x, coils, mask, 1, nz) - O.E(x, coils, mask, 1)).max() < 1e-12
+    assert np.abs(O.E(x, coils, mask, 1, 1) - O.E(x, coils, mask, 0)).max() < 1e-12
+
+
+def test_volume_columns_gram_and_rank_one_closed_form():
+    """Columns of cs slices: the Gram is the sum, over the slice position s inside a column, of
+    the slice Gram's entries (i cs + s, j cs + s); a separable sequence x[t cs + s] = v[t] u[s]
+    (one volume u scaled per frame) is a rank-1 Casorati with sigma_1 = ||u|| ||v||, which
+    initial_lambdas returns times lambda_L_rel."""
+    cs, T, nx, ny = 3, 4, 8, 8
+    X = crandn(cs * T, nx, ny)
+    G1 = O.casorati_gram(X)
+    G = O.casorati_gram(X, None, cs)
+    want = np.array([[sum(G1[i * cs + s, j * cs + s] for s in range(cs)) for j in range(T)] for i in range(T)])
+    assert np.abs(G - want).max() < 1e-10
+    u = crandn(cs, nx, ny)
+    v = np.array([1.0, -2.0j, 0.5, 3.0 + 1.0j])
+    x = np.concatenate([v[t] * u for t in range(T)])
+    sv = np.linalg.svd(O.casorati(x, cs), compute_uv=False)
+    assert abs(sv[0] - np.linalg.norm(u) * np.linalg.norm(v)) < 1e-10 * sv[0] and sv[1] < 1e-10 * sv[0]
+    p = O.Params(lambda_L_rel=0.01, frame_slices=cs)
+    assert abs(O.initial_lambdas(x, p)[0] - 0.01 * np.linalg.norm(u) * np.linalg.norm(v)) < 1e-12 * sv[0]
+    # the slice columns of the same sequence are not rank 1 (u varies over its slices)
+    assert np.linalg.svd(O.casorati(x), compute_uv=False)[1] > 1e-3
+
+
+@pytest.mark.parametrize("fft_z", [1, 0])
+def test_frame_volumes_exact_recovery_full_mask_zero_thresholds(fft_z):
+    cs, T, nx, ny = 2, 3, 8, 8
+    nz = cs * T
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny))
+    coils = P.coil_maps(nx, ny, nz, 2, seed=5)
+    mask = np.ones((nz, ny), np.uint8)
+    p = O.Params(lambda_L_rel=0.0, lambda_S_rel=0.0, lambda_p=0.0, rank_tau=0.0, max_iters=3,
+                 fft_z=fft_z, frame_slices=cs)
+    # data from the brute-force per-frame DFT (3D encode) or the per-slice encode
+    d = brute_E_blocks(x, coils, mask, cs) if fft_z else O.E(x, coils, mask, 0)
+    r = O.priori_ls(d, coils, mask, p)
+    assert O.nrmse(r.recon, x) < 1e-12
+    assert r.sigma.shape == (T,)
+
+
 # ---------------------------------------------------------------- Haar transform
 
 def haar_basis(nx, ny, J):
