@@ -72,11 +72,14 @@ extern "C" {
 
 /* ---- options ---------------------------------------------------------------------- */
 #define LPS_LAYOUT_SLICES      0  /* Casorati columns = the nz slices of a volume (Sec. 2) */
-/* Casorati columns = the frames of a 2D + time segment (nx x ny images): nz counts the
- * frames, mask row z holds frame z's ky lines and every frame is encoded by its own 2D DFT
- * (fft_z must be 0; frames that are 3D volumes return LPS_ERR_UNSUPPORTED). Coil maps are
- * given per frame ([c][frame][x][y]). With the recursion, the prior of a segment comes from
- * the previous segment of the session. */
+/* Casorati columns = the frames of a segment. 2D frames (frame_slices 1, nx x ny images): nz
+ * counts the frames, mask row z holds frame z's ky lines and every frame is encoded by its own
+ * 2D DFT (fft_z must be 0). 3D frames (frame_slices = s > 1): nz = frames * s slices, frame t
+ * being slices t s .. t s + s - 1 (one Casorati column of s nx ny voxels); mask rows t s + kz
+ * hold frame t's (kz, ky) lines and each frame volume is encoded by its own 3D DFT over its s
+ * slices (fft_z = 1) or per slice (fft_z = 0). Coil maps are given per frame
+ * ([c][slice][x][y] over all nz slices); sigma arrays have one entry per column. With the
+ * recursion, the prior of a segment comes from the previous segment of the session. */
 #define LPS_LAYOUT_FRAMES      1
 
 #define LPS_FP32               0  /* every stage in float32 (Gram and reprojection on FMA) */
@@ -131,7 +134,11 @@ typedef struct lps_params {
   int wavelet_dims;        /* sparsifying transform T: 2 (0 reads as 2) the per-slice 2D Haar;
                               3 the 3D Haar, the 2D pyramid times the J-level 1D Haar along z
                               (nz a multiple of 2^J; the support numbering below)            */
-  int reserved[4];         /* must be zero                                                  */
+  int frame_slices;        /* LPS_LAYOUT_FRAMES: slices per frame (0 reads as 1). 1: 2D frames
+                              (fft_z = 0); > 1: 3D frames, nz / frame_slices columns each a
+                              volume of frame_slices slices with its own 3D encode (fft_z = 1)
+                              or per-slice encode (fft_z = 0); float32 path, whole volumes   */
+  int reserved[3];         /* must be zero                                                  */
 } lps_params;
 
 typedef struct lps_stats {
@@ -192,7 +199,8 @@ int lps_clear_prior(lps_plan* plan);
  * Sec. 3) must follow its frames. Moves the prior support `shift` Casorati columns towards
  * column 0 (the first `shift` columns are dropped) and repeats the last remaining column in the
  * `shift` freed ones (the newest frame's prior is the support of the frame before it). The
- * prior singular values are kept. 1 <= shift < nz; enqueued on the plan's stream. */
+ * prior singular values are kept. 1 <= shift < columns (nz / frame_slices); enqueued on
+ * the plan's stream. */
 int lps_shift_prior_columns(lps_plan* plan, int shift);
 
 /* Run n iterations of Algorithm 1 on the resident state, starting with step (0) if the

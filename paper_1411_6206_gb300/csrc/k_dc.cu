@@ -57,7 +57,7 @@ static size_t dc_rt_smem_bytes(const Geom& g, int dsm_slots) {
 
 bool dc_rt_geometry(const Geom& g) {
   const int q = g.ny / 16;
-  if (g.ny % 16 != 0 || q < 4 || q > 10 || dc_has_fixed(g)) return false;
+  if (g.cs != 1 || g.ny % 16 != 0 || q < 4 || q > 10 || dc_has_fixed(g)) return false;
   switch (g.nz) {
     case 8: case 10: case 12: case 14: case 16: case 20: case 24: case 28: case 32: return true;
     default: return false;

@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   int* errp = a.ctrl ? &a.ctrl->err : nullptr;
 
   for (int i = tid; i < ny; i += NTH) twy[i] = a.tw_y[i];
-  for (int i = tid; i < nz; i += NTH) twz[i] = a.tw_z[i];
+  for (int i = tid; i < g.zn; i += NTH) twz[i] = a.tw_z[i];
   if (STAGE && tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
@@ -431,20 +431,22 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   if (iter_form && a.W) {
     // Steps (1)-(2) completed here: L_k = (X_{k-1} - S_{k-1}) W over the plane's columns,
     // one pixel column and 4 output slices per task, into bufB.
-    for (int i = tid; i < nz * nz; i += NTH) wsh[i] = a.W[i];
+    // Casorati column i is slices i cs .. i cs + cs - 1: L[j cs + s] = sum_i M[i cs + s] W[i][j]
+    const int nc = g.nc, cs = g.cs;
+    for (int i = tid; i < nc * nc; i += NTH) wsh[i] = a.W[i];
     __syncthreads();
-    const int nzb = (nz + 3) / 4;
-    for (int task = tid; task < ny * nzb; task += NTH) {
-      const int y = task % ny, zb = (task / ny) * 4;
+    const int ncb = (nc + 3) / 4;
+    for (int task = tid; task < ny * cs * ncb; task += NTH) {
+      const int y = task % ny, r = task / ny, s = r % cs, jb = (r / cs) * 4;
       float2 o[4];
 #pragma unroll
       for (int j = 0; j < 4; ++j) o[j] = make_float2(0.f, 0.f);
-      for (int i = 0; i < nz; ++i) {
-        const float2 mv = bufA[i * nyp + y];
+      for (int i = 0; i < nc; ++i) {
+        const float2 mv = bufA[(i * cs + s) * nyp + y];
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
-          if (zb + j < nz) {
-            const float2 w = wsh[i * nz + zb + j];
+          if (jb + j < nc) {
+            const float2 w = wsh[i * nc + jb + j];
             o[j].x = fmaf(mv.x, w.x, fmaf(-mv.y, w.y, o[j].x));
             o[j].y = fmaf(mv.x, w.y, fmaf(mv.y, w.x, o[j].y));
           }
@@ -452,7 +454,7 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
       }
 #pragma unroll
       for (int j = 0; j < 4; ++j)
-        if (zb + j < nz) bufB[(zb + j) * nyp + y] = o[j];
+        if (jb + j < nc) bufB[((jb + j) * cs + s) * nyp + y] = o[j];
     }
     __syncthreads();
   }
@@ -522,7 +524,7 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
       }
       __syncthreads();
       fft_run(&src, &dst, g.py, nz, 1, nyp, twy, false);
-      if (g.fft_z) fft_run(&src, &dst, g.pz, ny, nyp, 1, twz, false);
+      if (g.fft_z) fft_run(&src, &dst, g.pz, ny, nyp, 1, twz, false, nz / g.zn, g.zn * nyp);
       if (MODE == kDcForward) {
         float2* ho = a.hyb_out + ((long long)x * g.ncoil + c) * g.mpad;
         for (int l = tid; l < m; l += NTH) ho[l] = src[a.lines[l]];
@@ -557,7 +559,7 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
       src = dst;
       dst = t;
     }
-    if (g.fft_z) fft_run(&src, &dst, g.pz, ny, nyp, 1, twz, true);
+    if (g.fft_z) fft_run(&src, &dst, g.pz, ny, nyp, 1, twz, true, nz / g.zn, g.zn * nyp);
     fft_run(&src, &dst, g.py, nz, 1, nyp, twy, true);
 #pragma unroll
     for (int k = 0; k < EPT; ++k) {
@@ -604,19 +606,22 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   }
   __syncthreads();
   if (a.gram_part) {
-    // Plane share of G = M^H M: G[i][j] = sum_y conj(M[i][y]) M[j][y], columns i, j = slices.
-    const int nc = g.nc;
+    // Plane share of G = M^H M: G[i][j] = sum over the column's slices s and y of
+    // conj(M[i cs + s][y]) M[j cs + s][y] (columns i, j; cs = 1: the slices).
+    const int nc = g.nc, cs = g.cs;
     float2* gp = a.gram_part + (long long)x * nc * nc;
     for (int t = tid; t < nc * nc; t += NTH) {
       const int i = t / nc, j = t - (t / nc) * nc;
       if (i > j) continue;
-      const float2* ri = bufA + i * nyp;
-      const float2* rj = bufA + j * nyp;
       float sr = 0.f, si = 0.f;
-      for (int y = 0; y < ny; ++y) {
-        const float2 u = ri[y], v = rj[y];
-        sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
-        si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
+      for (int s = 0; s < cs; ++s) {
+        const float2* ri = bufA + (i * cs + s) * nyp;
+        const float2* rj = bufA + (j * cs + s) * nyp;
+        for (int y = 0; y < ny; ++y) {
+          const float2 u = ri[y], v = rj[y];
+          sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
+          si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
+        }
       }
       gp[i * nc + j] = make_float2(sr, si);
       if (i != j) gp[j * nc + i] = make_float2(sr, -si);

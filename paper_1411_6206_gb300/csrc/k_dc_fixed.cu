@@ -483,7 +483,7 @@ static cudaError_t launch_fixed_mode(const DcArgs& a, int mode, cudaStream_t st)
 }
 
 static bool has_fixed(const Geom& g) {
-  if (g.dc_generic || g.nx % kGramCluster != 0) return false;   // the grid is made of whole clusters (nx % 8 == 0 anyway)
+  if (g.dc_generic || g.cs != 1 || g.nx % kGramCluster != 0) return false;   // whole clusters (nx % 8 == 0 anyway)
   return (g.ny == 128 && g.nz == 16) || (g.ny == 192 && g.nz == 32) || (g.ny == 32 && g.nz == 8);
 }
 

@@ -408,7 +408,7 @@ cudaError_t launch_reg(const DcArgs& a, cudaStream_t st) {
 // cudaErrorNotSupported. It writes the same Gram partial count as the staged-coil kernel
 // (nx / 4, one per 4-plane cluster).
 bool dc_reg_applies(const Geom& g) {
-  return !g.dc_generic && g.ny == kNY && g.nz == kNZ && g.nx % kRegCluster == 0 && g.dc_reg_groups > 0;
+  return !g.dc_generic && g.cs == 1 && g.ny == kNY && g.nz == kNZ && g.nx % kRegCluster == 0 && g.dc_reg_groups > 0;
 }
 
 cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st) {

@@ -188,13 +188,13 @@ __device__ __forceinline__ float zpass(float2* zb, int nc, int tpc, int tid, int
 }
 
 template <int J, bool Z3>
-__global__ void __launch_bounds__(kThreads) k_lrs(const LrsArgs a) {
+__global__ void __launch_bounds__(1024) k_lrs(const LrsArgs a) {
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem[];
   float* red = reinterpret_cast<float*>(smem);
   float2* zb = reinterpret_cast<float2*>(smem + 32 * sizeof(float));   // Z3: one row per thread
-  const int nc = g.nc;
-  const int tpc = g.lrs_tpc > 0 ? g.lrs_tpc : 32 / nc;   // tiles per CTA
+  const int nc = g.nz;   // slices per tile (every slice of the volume)
+  const int tpc = g.lrs_tpc > 0 ? g.lrs_tpc : (32 / nc > 0 ? 32 / nc : 1);   // tiles per CTA
 
   const int tid = threadIdx.x, lane = tid & 31;
   const int u = tid & 7, grp = tid >> 3;
@@ -338,16 +338,18 @@ __global__ void __launch_bounds__(kThreads) k_gram_plane(const float2* X, const 
     }
     __syncthreads();
     const bool first = x == (int)blockIdx.x * q;
-    // each thread owns its entries across the planes, so the running sums need no barrier
+    // each thread owns its entries across the planes, so the running sums need no barrier;
+    // column i holds slices i cs .. i cs + cs - 1
     for (int t = threadIdx.x; t < nc * nc; t += kThreads) {
       const int i = t / nc, j = t - (t / nc) * nc;
       if (i > j) continue;
       float sr = 0.f, si = 0.f;
-      for (int y = 0; y < ny; ++y) {
-        const float2 u = M[i * nyp + y], v = M[j * nyp + y];
-        sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
-        si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
-      }
+      for (int s = 0; s < g.cs; ++s)
+        for (int y = 0; y < ny; ++y) {
+          const float2 u = M[(i * g.cs + s) * nyp + y], v = M[(j * g.cs + s) * nyp + y];
+          sr = fmaf(u.x, v.x, fmaf(u.y, v.y, sr));
+          si = fmaf(u.x, v.y, fmaf(-u.y, v.x, si));
+        }
       if (!first) {
         const float2 o = gp[i * nc + j];
         sr += o.x;
@@ -387,11 +389,11 @@ cudaError_t launch_combine(const float2* L, const float2* S, float2* out, long l
   return cudaGetLastError();
 }
 
-int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : 32 / g.nc; }
+int lrs_tpc(const Geom& g) { return g.lrs_tpc > 0 ? g.lrs_tpc : std::max(1, 32 / g.nz); }
 
 // Threads of one sparse-step CTA: 8 per (tile, slice), rounded up to whole warps (the
 // Haar shuffles need full warps; lanes beyond the tiles are inactive).
-int lrs_threads(const Geom& g) { return (8 * g.nc * lrs_tpc(g) + 31) / 32 * 32; }
+int lrs_threads(const Geom& g) { return (8 * g.nz * lrs_tpc(g) + 31) / 32 * 32; }
 
 static size_t lrs_smem(const Geom& g) {
   return 32 * sizeof(float) + (g.wz ? (size_t)lrs_threads(g) * 8 * sizeof(float2) : 0);
@@ -412,7 +414,8 @@ static cudaError_t launch_lrs_j(const LrsArgs& a, cudaStream_t st) {
 
 cudaError_t launch_lrs(const LrsArgs& a, cudaStream_t st) {
   // the 3D variant needs whole z blocks (validated with the plan's parameters)
-  if (a.g.wz && a.g.nc % (1 << a.g.J) != 0) return cudaErrorInvalidValue;
+  if (a.g.wz && a.g.nz % (1 << a.g.J) != 0) return cudaErrorInvalidValue;
+  if (lrs_threads(a.g) > 1024) return cudaErrorInvalidValue;
   switch (a.g.J * 2 + (a.g.wz ? 1 : 0)) {
     case 2: return launch_lrs_j<1, false>(a, st);
     case 3: return launch_lrs_j<1, true>(a, st);
@@ -468,7 +471,7 @@ cudaError_t launch_gram_sum(const float2* part, int nparts, int nc, float2* G, c
 // form of the reprojection that k_lrs fuses with the sparse step).
 __global__ void k_reproj_f32(const float2* __restrict__ X, const float2* __restrict__ S,
                              const float2* __restrict__ W, float2* __restrict__ L, Geom g) {
-  const long long nr = (long long)g.nx * g.ny;
+  const long long nr = g.N / g.nc;   // rows of the Casorati matrix (voxels of a column)
   const int nc = g.nc;
   for (long long r = blockIdx.x * (long long)blockDim.x + threadIdx.x; r < nr; r += (long long)gridDim.x * blockDim.x) {
     float2 m[kMaxNc];
@@ -492,7 +495,7 @@ __global__ void k_reproj_f32(const float2* __restrict__ X, const float2* __restr
 
 cudaError_t launch_reproj_f32(const float2* X, const float2* S, const float2* W, float2* L, const Geom& g,
                               cudaStream_t st) {
-  const long long nr = (long long)g.nx * g.ny;
+  const long long nr = g.N / g.nc;
   const int blocks = (int)std::min<long long>((nr + 127) / 128, 152LL * 8);
   k_reproj_f32<<<blocks, 128, 0, st>>>(X, S, W, L, g);
   return cudaGetLastError();

@@ -217,16 +217,26 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->ncoil >= 1 && p->ncoil <= 64, "ncoil must be in 1..64");
   ARG(p->layout == LPS_LAYOUT_SLICES || p->layout == LPS_LAYOUT_FRAMES, "layout must be SLICES or FRAMES");
   ARG(p->fft_z == 0 || p->fft_z == 1, "fft_z must be 0 or 1");
-  if (p->layout == LPS_LAYOUT_FRAMES && p->fft_z != 0) {
-    // a column is one 2D frame with its own ky lines: the per-slice 2D encode; frames that are
-    // 3D volumes (a 3D encode per column) are not implemented
-    set_err("LPS_LAYOUT_FRAMES takes 2D frames (fft_z = 0)");
+  // Casorati columns: the slices (layout "slices"), or frames of frame_slices slices each
+  const int fs = p->frame_slices ? p->frame_slices : 1;
+  ARG(fs >= 1 && fs <= 128, "frame_slices must be 0..128");
+  ARG(p->layout == LPS_LAYOUT_FRAMES || fs == 1, "frame_slices applies to LPS_LAYOUT_FRAMES");
+  ARG(p->nz % fs == 0, "nz must be a multiple of frame_slices");
+  if (p->layout == LPS_LAYOUT_FRAMES && fs == 1 && p->fft_z != 0) {
+    // a column is one 2D frame with its own ky lines: the per-slice 2D encode
+    set_err("LPS_LAYOUT_FRAMES with 2D frames (frame_slices 1) takes fft_z = 0");
+    return LPS_ERR_UNSUPPORTED;
+  }
+  if (fs > 1 && (p->precision != LPS_FP32 || p->nx_total != 0)) {
+    set_err("3D frames (frame_slices > 1) run the float32 path on whole volumes");
     return LPS_ERR_UNSUPPORTED;
   }
   ARG(p->wavelet_levels >= 1 && p->wavelet_levels <= 3, "wavelet_levels must be 1..3");
   ARG(p->wavelet_dims == 0 || p->wavelet_dims == 2 || p->wavelet_dims == 3, "wavelet_dims must be 2 or 3");
   ARG(p->wavelet_dims != 3 || p->nz % (1 << p->wavelet_levels) == 0,
       "the 3D Haar needs nz a multiple of 2^wavelet_levels");
+  ARG(p->wavelet_dims != 3 || fs == 1 || fs % (1 << p->wavelet_levels) == 0,
+      "the 3D Haar of 3D frames needs frame_slices a multiple of 2^wavelet_levels");
   ARG(p->max_iters >= 1 && p->max_iters <= 4096, "max_iters must be 1..4096");
   ARG(std::isfinite(p->lambda_L_rel) && p->lambda_L_rel >= 0, "lambda_L_rel must be finite, >= 0");
   ARG(std::isfinite(p->lambda_S_rel) && p->lambda_S_rel >= 0, "lambda_S_rel must be finite, >= 0");
@@ -240,8 +250,9 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->recursive == 0 || p->recursive == 1, "recursive must be 0 or 1");
   ARG(p->coil_format == LPS_COILS_FP32 || p->coil_format == LPS_COILS_FP16,
       "coil_format must be LPS_COILS_FP32 or LPS_COILS_FP16");
-  if (p->nz > LPS_MAX_NC) {
-    set_err("nz = %d exceeds LPS_MAX_NC = %d", p->nz, LPS_MAX_NC);
+  if (p->nz / fs > LPS_MAX_NC || p->nz > 128) {
+    set_err("%d Casorati columns of %d slices: at most LPS_MAX_NC = %d columns and 128 slices", p->nz / fs, fs,
+            LPS_MAX_NC);
     return LPS_ERR_UNSUPPORTED;
   }
   // x-slab of a larger volume: nx_total = 0 means the whole volume
@@ -256,7 +267,9 @@ int validate(const lps_params* p, Geom* gout) {
   g.ny = p->ny;
   g.nz = p->nz;
   g.ncoil = p->ncoil;
-  g.nc = p->nz;
+  g.cs = fs;
+  g.nc = p->nz / fs;
+  g.zn = (fs > 1 && p->fft_z) ? fs : p->nz;
   g.plane = p->ny * p->nz;
   g.nyp = p->ny + 1;
   g.planeP = p->nz * g.nyp + ((p->nz * g.nyp) & 1);
@@ -265,9 +278,9 @@ int validate(const lps_params* p, Geom* gout) {
   g.wz = p->wavelet_dims == 3 ? 1 : 0;
   g.ntiles = (p->nx / 8) * (p->ny / 8);
   g.N = (long long)p->nx * p->ny * p->nz;
-  g.scale_yz = (float)(1.0 / std::sqrt((double)p->ny * (p->fft_z ? p->nz : 1)));
+  g.scale_yz = (float)(1.0 / std::sqrt((double)p->ny * (p->fft_z ? g.zn : 1)));
   g.scale_x = (float)(1.0 / std::sqrt((double)nxt));
-  if (!make_fft_plan(p->ny, g.py) || !make_fft_plan(p->nz, g.pz) || !make_fft_plan(nxt, g.px)) {
+  if (!make_fft_plan(p->ny, g.py) || !make_fft_plan(g.zn, g.pz) || !make_fft_plan(nxt, g.px)) {
     set_err("FFT lengths need prime factors <= 64 and at most %d passes", kMaxPasses);
     return LPS_ERR_UNSUPPORTED;
   }
@@ -864,7 +877,7 @@ int lps_plan_create(const lps_params* p, void* stream, lps_plan** out) {
     CK(cudaMemcpy(d, t.data(), n * sizeof(float2), cudaMemcpyHostToDevice));
     return LPS_OK;
   };
-  if ((rc = up(P->tw_x, g.nxt)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.nz))) return fail(rc);
+  if ((rc = up(P->tw_x, g.nxt)) || (rc = up(P->tw_y, g.ny)) || (rc = up(P->tw_z, g.zn))) return fail(rc);
   if (cudaMemset(P->persist, 0, sizeof(DevPersist)) != cudaSuccess ||
       cudaMemset(P->ctrl, 0, sizeof(DevCtrl)) != cudaSuccess ||
       cudaMemset(P->dc_part, 0, g.nx * 4 * sizeof(float)) != cudaSuccess ||
@@ -981,17 +994,17 @@ int lps_set_prior(lps_plan* P, const uint32_t* support, const double* sigma_prev
 
 int lps_shift_prior_columns(lps_plan* P, int shift) {
   ARG(P != nullptr, "plan is NULL");
-  ARG(shift >= 1 && shift < P->g.nz, "shift must be in 1..nz-1");
+  ARG(shift >= 1 && shift < P->g.nc, "shift must be in 1..columns-1");
   ARG(!P->g.wz, "the 3D Haar mixes the columns of a z block: its support has no per-column shift");
   // support words of one Casorati column (the coefficients of one slice or frame are
   // contiguous: the column index is the outermost of the tile-major numbering)
-  const size_t wpc = (size_t)P->g.nx * P->g.ny / 32;
-  const size_t keep = (size_t)(P->g.nz - shift) * wpc;
+  const size_t wpc = (size_t)P->g.cs * P->g.nx * P->g.ny / 32;
+  const size_t keep = (size_t)(P->g.nc - shift) * wpc;
   // through the second support buffer, free between frames (the ranges overlap)
   CK(cudaMemcpyAsync(P->sup_out2, P->sup_prior + shift * wpc, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice,
                      P->st));
   CK(cudaMemcpyAsync(P->sup_prior, P->sup_out2, keep * sizeof(uint32_t), cudaMemcpyDeviceToDevice, P->st));
-  for (int z = P->g.nz - shift; z < P->g.nz; ++z)
+  for (int z = P->g.nc - shift; z < P->g.nc; ++z)
     CK(cudaMemcpyAsync(P->sup_prior + z * wpc, P->sup_out2 + keep - wpc, wpc * sizeof(uint32_t),
                        cudaMemcpyDeviceToDevice, P->st));
   return LPS_OK;
@@ -1373,7 +1386,7 @@ int lps_slab_end(lps_plan* P, const float* rec, lps_stats* stats) {
 // Checkpoint layout: header, prior support words, prior sigma, L, S, X, lambdas.
 struct CkptHeader {
   uint32_t magic, version;
-  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done, v_valid, wz;
+  int nx, ny, nz, ncoil, J, has_sup, has_sigma, iters_done, v_valid, wz;   // wz + 256 * slices per column
   double lambda_L, lambda_S;
 };
 
@@ -1392,7 +1405,7 @@ int lps_session_export(lps_plan* P, void* buf, size_t* bytes) {
   CK(cudaMemcpyAsync(&dp, P->persist, sizeof(DevPersist), cudaMemcpyDeviceToHost, P->st));
   CK(cudaStreamSynchronize(P->st));
   CkptHeader h{0x4c50531a, 2, P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.J, dp.has_sup,
-               dp.has_sigma, P->iters_done, dp.v_valid, P->g.wz, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
+               dp.has_sigma, P->iters_done, dp.v_valid, P->g.wz + 256 * P->g.cs, P->h_ctrl->lambda_L, P->h_ctrl->lambda_S};
   unsigned char* o = (unsigned char*)buf;
   std::memcpy(o, &h, sizeof(h));
   o += sizeof(h);
@@ -1420,7 +1433,7 @@ int lps_session_import(lps_plan* P, const void* buf, size_t bytes) {
   CkptHeader h;
   std::memcpy(&h, buf, sizeof(h));
   ARG(h.magic == 0x4c50531a && h.version == 2, "not a checkpoint of this library");
-  ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J && h.wz == P->g.wz,
+  ARG(h.nx == P->g.nx && h.ny == P->g.ny && h.nz == P->g.nz && h.J == P->g.J && h.wz == P->g.wz + 256 * P->g.cs,
       "checkpoint shape mismatch");
   const unsigned char* i = (const unsigned char*)buf + sizeof(h);
   CK(cudaStreamSynchronize(P->st));

@@ -211,7 +211,7 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
   ARG(P != nullptr, "plan is NULL");
   int rc = plan_need_ready(P);
   if (rc) return rc;
-  const TuneKey key{P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.fft_z, P->p.precision};
+  const TuneKey key{P->g.nx, P->g.ny, P->g.nz, P->g.ncoil, P->g.fft_z + 2 * P->g.cs, P->p.precision};
   {
     std::lock_guard<std::mutex> lock(g_tune_mutex);
     auto it = g_tune_cache.find(key);
@@ -284,7 +284,7 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
   }
   {
     const std::vector<FftPlan> cy = fft_candidates(g0.ny, 6);
-    const std::vector<FftPlan> cz = fft_candidates(g0.nz, 4);
+    const std::vector<FftPlan> cz = fft_candidates(g0.zn, 4);
     for (int direct = 0; direct < 2; ++direct)
       for (const FftPlan& py : cy)
         for (const FftPlan& pz : cz) {
@@ -308,7 +308,7 @@ int lps_autotune(lps_plan* P, lps_tune_result* out) {
   }
   // low-rank / sparse kernel: 8x8 tiles per CTA
   {
-    const int tmax = 32 / g0.nc;
+    const int tmax = std::max(1, 32 / g0.nz);
     int last = -1;
     for (int t : {tmax, tmax / 2, tmax / 4, 1}) {
       if (t < 1 || t == last) continue;
@@ -356,7 +356,7 @@ done:
 int lps_apply_tune(lps_plan* P, const lps_tune_result* t) {
   ARG(P != nullptr && t != nullptr, "NULL argument");
   ARG(t->dc_variant >= 0 && t->dc_variant <= 5, "dc_variant must be 0..5");
-  ARG(t->lrs_tiles >= 1 && t->lrs_tiles <= 32 / P->g.nc, "lrs_tiles must be in 1..32/nz");
+  ARG(t->lrs_tiles >= 1 && t->lrs_tiles <= std::max(1, 32 / P->g.nz), "lrs_tiles must be in 1..max(1, 32/nz)");
   TuneEntry e{};
   e.res = *t;
   if (t->dc_variant == 5) {
@@ -380,7 +380,7 @@ int lps_apply_tune(lps_plan* P, const lps_tune_result* t) {
       return f.np > 0 && prod == n;
     };
     ARG(plan_of(t->radix_y, P->g.ny, e.py), "radix_y does not factor ny");
-    ARG(plan_of(t->radix_z, P->g.nz, e.pz), "radix_z does not factor nz");
+    ARG(plan_of(t->radix_z, P->g.zn, e.pz), "radix_z does not factor the z transform length");
   }
   ARG(cudaStreamSynchronize(P->st) == cudaSuccess, "stream error");
   install(P, e);

@@ -65,12 +65,14 @@ inline double iter_objective(const IterRec& r, float lambda_L, float lambda_S) {
 struct Geom {
   int nx, ny, nz, ncoil;    // nx: the x-planes this plan holds (a slab of nxt planes)
   int nxt, x0;              // x extent of the whole volume (readout length) and the slab's first plane
-  int nc;                   // Casorati columns (= nz)
+  int nc;                   // Casorati columns (nz / cs)
   int plane;                // ny*nz, elements of one x-plane
   int nyp;                  // padded row stride of the FFT buffers (odd)
   int planeP;               // nz*nyp rounded up to even
   int mpad;                 // row stride (elements) of the hybrid data per (x, coil)
   int fft_z;                // 3D (1) or per-slice 2D (0) encode
+  int cs;                   // slices per Casorati column (> 1: columns are 3D frame volumes)
+  int zn;                   // length of each z transform (nz, or cs for 3D frames)
   int J;                    // Haar levels
   int wz;                   // 1: 3D Haar (the 2D pyramid times the 1D Haar along z), 0: per slice
   int ntiles;               // (nx/8)*(ny/8)
@@ -477,17 +479,20 @@ __device__ __forceinline__ unsigned fdiv(unsigned t, FastDiv f) {
 template <int R>
 __device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2* __restrict__ out, int n,
                                            int Ns, int nb, int es, int bs, const float2* __restrict__ tw,
-                                           bool inv) {
+                                           bool inv, int nb2, int bs2) {
   const int nbf = n / R;
-  const int total = nb * nbf;
+  const int total = nb * nb2 * nbf;
   const int tws = n / (Ns * R);
-  const FastDiv fnb = make_fdiv((unsigned)nb), fns = make_fdiv((unsigned)Ns);
+  const FastDiv fnb = make_fdiv((unsigned)(nb * nb2)), fns = make_fdiv((unsigned)Ns), fb1 = make_fdiv((unsigned)nb);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int j = (int)fdiv((unsigned)t, fnb);
-    const int b = t - j * nb;
+    const int bb = t - j * (nb * nb2);
+    const int b2 = (int)fdiv((unsigned)bb, fb1);
+    const int b = bb - b2 * nb;
     const int jq = (int)fdiv((unsigned)j, fns);
     const int k = j - jq * Ns;
-    const float2* src = in + b * bs;
+    const int boff = b * bs + b2 * bs2;
+    const float2* src = in + boff;
     float2 v[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[(j + r * nbf) * es];
@@ -501,7 +506,7 @@ __device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2
     }
     dft_reg<R>(v, inv, tw, n);
     const int idxD = jq * Ns * R + k;
-    float2* dst = out + b * bs;
+    float2* dst = out + boff;
 #pragma unroll
     for (int r = 0; r < R; ++r) dst[(idxD + r * Ns) * es] = v[r];
   }
@@ -510,20 +515,24 @@ __device__ __forceinline__ void fft_pass_r(const float2* __restrict__ in, float2
 // Pass with a radix that has no register specialisation: one thread per output element.
 __device__ __forceinline__ void fft_pass_any(const float2* __restrict__ in, float2* __restrict__ out, int n,
                                              int Ns, int R, int nb, int es, int bs,
-                                             const float2* __restrict__ tw, bool inv) {
+                                             const float2* __restrict__ tw, bool inv, int nb2, int bs2) {
   const int nbf = n / R;
-  const int total = nb * n;
+  const int total = nb * nb2 * n;
   const int tws = n / (Ns * R);
   const int st = n / R;
-  const FastDiv fnb = make_fdiv((unsigned)nb), fnbf = make_fdiv((unsigned)nbf), fns = make_fdiv((unsigned)Ns);
+  const FastDiv fnb = make_fdiv((unsigned)(nb * nb2)), fnbf = make_fdiv((unsigned)nbf), fns = make_fdiv((unsigned)Ns),
+                fb1 = make_fdiv((unsigned)nb);
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int rest = (int)fdiv((unsigned)t, fnb);
-    const int b = t - rest * nb;
+    const int bb = t - rest * (nb * nb2);
+    const int b2 = (int)fdiv((unsigned)bb, fb1);
+    const int b = bb - b2 * nb;
     const int s = (int)fdiv((unsigned)rest, fnbf);
     const int j = rest - s * nbf;
     const int jq = (int)fdiv((unsigned)j, fns);
     const int k = j - jq * Ns;
-    const float2* src = in + b * bs;
+    const int boff = b * bs + b2 * bs2;
+    const float2* src = in + boff;
     float2 acc = make_float2(0.f, 0.f);
     for (int r = 0; r < R; ++r) {
       float2 v = src[(j + r * nbf) * es];
@@ -536,32 +545,33 @@ __device__ __forceinline__ void fft_pass_any(const float2* __restrict__ in, floa
       acc = cadd(acc, cmul(cmul(v, w), u));
     }
     const int idxD = jq * Ns * R + k;
-    out[b * bs + (idxD + s * Ns) * es] = acc;
+    out[boff + (idxD + s * Ns) * es] = acc;
   }
 }
 
 __device__ __forceinline__ void fft_pass(const float2* in, float2* out, int n, int Ns, int R, int nb, int es,
-                                         int bs, const float2* tw, bool inv) {
+                                         int bs, const float2* tw, bool inv, int nb2, int bs2) {
   switch (R) {
-    case 2: fft_pass_r<2>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 3: fft_pass_r<3>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 4: fft_pass_r<4>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 5: fft_pass_r<5>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 7: fft_pass_r<7>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 8: fft_pass_r<8>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    case 16: fft_pass_r<16>(in, out, n, Ns, nb, es, bs, tw, inv); break;
-    default: fft_pass_any(in, out, n, Ns, R, nb, es, bs, tw, inv); break;
+    case 2: fft_pass_r<2>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 3: fft_pass_r<3>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 4: fft_pass_r<4>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 5: fft_pass_r<5>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 7: fft_pass_r<7>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 8: fft_pass_r<8>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    case 16: fft_pass_r<16>(in, out, n, Ns, nb, es, bs, tw, inv, nb2, bs2); break;
+    default: fft_pass_any(in, out, n, Ns, R, nb, es, bs, tw, inv, nb2, bs2); break;
   }
 }
 
 // Full transform: passes ping-pong between *src and *dst (swapped after each pass); on
-// return *src holds the result. A __syncthreads() follows every pass.
+// return *src holds the result. A __syncthreads() follows every pass. Transforms are indexed
+// by (b < nb, b2 < nb2) at b bs + b2 bs2 (nb2 > 1: blocks of slices transformed separately).
 __device__ __forceinline__ void fft_run(float2** src, float2** dst, const FftPlan& p, int nb, int es, int bs,
-                                        const float2* tw, bool inv) {
+                                        const float2* tw, bool inv, int nb2 = 1, int bs2 = 0) {
   int Ns = 1;
   for (int i = 0; i < p.np; ++i) {
     const int R = p.r[i];
-    fft_pass(*src, *dst, p.n, Ns, R, nb, es, bs, tw, inv);
+    fft_pass(*src, *dst, p.n, Ns, R, nb, es, bs, tw, inv, nb2, bs2);
     __syncthreads();
     float2* t = *src;
     *src = *dst;

@@ -45,7 +45,7 @@ class Params(C.Structure):
                 ("lambda_p", C.c_double), ("rank_tau", C.c_double), ("tol", C.c_double),
                 ("precision", C.c_int), ("eig_precision", C.c_int), ("support_rule", C.c_int),
                 ("recursive", C.c_int), ("coil_format", C.c_int), ("nx_total", C.c_int), ("x0", C.c_int),
-                ("wavelet_dims", C.c_int), ("reserved", C.c_int * 4)]
+                ("wavelet_dims", C.c_int), ("frame_slices", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class Stats(C.Structure):

@@ -49,6 +49,8 @@ def test_params_defaults_and_status_strings(lps):
     (dict(lambda_p=1.5), -1), (dict(layout=2), -1), (dict(layout=1), -8), (dict(precision=3), -1),
     (dict(nz=40), -8), (dict(ny=8 * 67), -8), (dict(max_iters=0), -1), (dict(coil_format=2), -1),
     (dict(wavelet_dims=1), -1), (dict(wavelet_dims=3, nz=12), -1), (dict(wavelet_dims=3, nz=6, wavelet_levels=2), -1),
+    (dict(frame_slices=2), -1), (dict(layout=1, frame_slices=3), -1), (dict(layout=1, frame_slices=2, precision=1), -8),
+    (dict(layout=1, frame_slices=2, nx_total=64), -8),
 ])
 def test_plan_create_rejects_bad_params(lps, bad, code):
     kw = dict(nx=32, ny=32, nz=8, ncoil=2)
