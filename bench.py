@@ -502,6 +502,11 @@ def cpu_parity(small_job, prec_job):
                 r = O.priori_ls(small_job["data"][t].astype(np.complex128), C, small_job["masks"][t], p, prior)
                 errs.append(round(O.nrmse(small_job["recon"][t], r.recon), 8))
             out["small"] = errs
+            f3 = small_job.get("frames3d")
+            if f3 is not None:
+                r = O.priori_ls(f3["data"].astype(np.complex128), f3["coils"].astype(np.complex128), f3["mask"],
+                                O.Params(max_iters=w.iters, frame_slices=f3["fs"]))
+                out["small_frames3d"] = round(O.nrmse(f3["recon"], r.recon), 8)
         if prec_job is not None:
             w = prec_job["w"]
             t0 = time.perf_counter()
@@ -809,6 +814,35 @@ def run_small(args):
            "repeats": len(ms),
            "how": "CUDA events around the 8-frame sequence (median of 10, after 3 warm-up runs); the run "
                   "is launch- and latency-bound, so no roofline fraction is reported"}
+    # the same 8 frames as one Casorati of volume columns (voxels x frames, layout "frames" with
+    # 3D frames): one reconstruction of the segment from all frames' lines
+    nzs = T * w.nz
+    pf = lps.Plan(w.nx, w.ny, nzs, w.ncoil, stream=st, max_iters=w.iters, layout=lps.LAYOUT_FRAMES,
+                  frame_slices=w.nz)
+    pf.set_coils(torch.cat([coils] * T, dim=1).contiguous())
+    mseg = np.ascontiguousarray(np.concatenate(masks, axis=0))
+    pf.set_mask(mseg)
+    dseg = torch.cat(list(kd), dim=1).contiguous()
+    pf.set_data(dseg)
+    seg = torch.empty((nzs, w.nx, w.ny), dtype=torch.complex64, device=dev)
+    for _ in range(3):
+        pf.reconstruct_frame(recon=seg, stats=False)
+    ms3 = []
+    for _ in range(10):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        pf.set_data(dseg)
+        pf.reconstruct_frame(recon=seg, stats=False)
+        e1.record(st)
+        st.synchronize()
+        ms3.append(e0.elapsed_time(e1))
+    pf.close()
+    med3 = float(np.median(ms3))
+    res["frames3d"] = {"workload": f"{T} frames of {w.nx}x{w.ny}x{w.nz} as the Casorati columns "
+                                   f"({w.nx * w.ny * w.nz} voxels x {T}), {w.iters} iterations",
+                       "us_per_segment": round(1e3 * med3, 1), "frames_per_s": round(T / (med3 / 1e3), 1)}
+    job["frames3d"] = {"coils": torch.cat([coils] * T, dim=1).cpu().numpy(), "mask": mseg,
+                       "data": dseg.cpu().numpy(), "recon": seg.cpu().numpy(), "fs": w.nz}
     return res, job
 
 
@@ -1113,6 +1147,8 @@ def main():
             par = cpu_parity(small_job, prec_job)
             if "small" in par:
                 out["small"]["nrmse_vs_oracle"] = par["small"]
+            if "small_frames3d" in par:
+                out["small"]["frames3d"]["nrmse_vs_oracle"] = par["small_frames3d"]
             if "precision" in par:
                 for k, v in par["precision"].items():
                     out["precision"][k]["nrmse_frame1_vs_oracle"] = v
