@@ -666,8 +666,8 @@ cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
   }
 }
 
-// float64 Rayleigh-Ritz refinement of the float32 eigendecomposition (LPS_EIG_FP64), one warp
-// per eigenvector j, in two kernels (the second needs every column of A):
+// float64 Rayleigh-Ritz refinement of the float32 eigendecomposition (LPS_EIG_FP64), one CTA of
+// four warps per eigenvector j, in two kernels (the second needs the diagonal of A):
 //   k_ritz64_a: A[:, j] = V^H (G v_j)
 //   k_ritz64_b: lambda_j = A_jj + sum_i |A_ij|^2 / (A_jj - A_ii) and
 //               v'_j = v_j + sum_i v_i A_ij / (A_jj - A_ii), normalised,
@@ -676,42 +676,67 @@ cudaError_t launch_eig(const EigArgs& a, cudaStream_t st) {
 // 1e-3 of their gap, where the corrected vectors stay orthonormal to ~1e-6; inside a cluster of
 // close eigenvalues (the noise floor) any rotation of the vectors is an eigenbasis to the
 // cluster's width, so the float32 vectors, orthonormal to float32 rounding, are kept there.
-__global__ void __launch_bounds__(32) k_ritz64_a(const RitzArgs a) {
-  pdl_trigger();
-  pdl_wait();
-  if (a.ctrl->converged) return;
-  __shared__ double2 t[kMaxNc];
-  const int n = a.n, j = blockIdx.x, i = threadIdx.x;
-  if (i < n) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < n; ++k) {
-      const float2 g = a.G[i * n + k], v = a.V[k * n + j];
-      s = add_(s, mul_(make_double2(g.x, g.y), make_double2(v.x, v.y)));
-    }
-    t[i] = s;
-  }
-  __syncwarp();
-  if (i < n) {
-    double2 s = make_double2(0.0, 0.0);
-    for (int k = 0; k < n; ++k) {
-      const float2 v = a.V[k * n + i];
-      s = add_(s, mulc_(make_double2(v.x, v.y), t[k]));
-    }
-    a.A[i * n + j] = s;
-  }
+// Sums over k are split over the four warps (a quarter of k each) and added in a fixed order.
+constexpr int kRitzThreads = 128;
+
+// s_w[i] = sum over k in quarter w of f(i, k), then out[i] = s_0 + s_1 + s_2 + s_3 (warp 0).
+template <typename F>
+__device__ __forceinline__ double2 ritz_sum(int n, F f, double2 (&part)[4][kMaxNc]) {
+  const int i = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int kc = (n + 3) / 4, k0 = w * kc, k1 = min(n, k0 + kc);
+  double2 s = make_double2(0.0, 0.0);
+  if (i < n)
+    for (int k = k0; k < k1; ++k) s = add_(s, f(i, k));
+  part[w][i] = s;
+  __syncthreads();
+  return add_(add_(part[0][i], part[1][i]), add_(part[2][i], part[3][i]));
 }
 
-__global__ void __launch_bounds__(32) k_ritz64_b(const RitzArgs a) {
+__global__ void __launch_bounds__(kRitzThreads) k_ritz64_a(const RitzArgs a) {
   pdl_trigger();
   pdl_wait();
   if (a.ctrl->converged) return;
+  __shared__ float2 Vs[kMaxNc * kMaxNc];
+  __shared__ float2 Gs[kMaxNc * kMaxNc];
+  __shared__ double2 part[4][kMaxNc];
+  __shared__ double2 t[kMaxNc];
+  const int n = a.n, j = blockIdx.x, tid = threadIdx.x;
+  for (int q = tid; q < n * n; q += kRitzThreads) {
+    Vs[q] = a.V[q];
+    Gs[q] = a.G[q];
+  }
+  __syncthreads();
+  // t = G v_j
+  const double2 gv = ritz_sum(n, [&](int i, int k) {
+    const float2 g = Gs[i * n + k], v = Vs[k * n + j];
+    return mul_(make_double2(g.x, g.y), make_double2(v.x, v.y));
+  }, part);
+  if (tid < n) t[tid] = gv;
+  __syncthreads();
+  // A_ij = sum_k conj(V_ki) t_k
+  const double2 aij = ritz_sum(n, [&](int i, int k) {
+    const float2 v = Vs[k * n + i];
+    return mulc_(make_double2(v.x, v.y), t[k]);
+  }, part);
+  if (tid < n) a.A[tid * n + j] = aij;
+}
+
+__global__ void __launch_bounds__(kRitzThreads) k_ritz64_b(const RitzArgs a) {
+  pdl_trigger();
+  pdl_wait();
+  if (a.ctrl->converged) return;
+  __shared__ float2 Vs[kMaxNc * kMaxNc];
+  __shared__ double2 part[4][kMaxNc];
   __shared__ double2 e[kMaxNc];
-  const int n = a.n, j = blockIdx.x, i = threadIdx.x;
+  __shared__ double dls[kMaxNc];
+  const int n = a.n, j = blockIdx.x, tid = threadIdx.x;
+  for (int q = tid; q < n * n; q += kRitzThreads) Vs[q] = a.V[q];
   const double ajj = a.A[j * n + j].x;
-  double dl = 0.0;
-  if (i < n) {
+  if (tid < kMaxNc) {
+    const int i = tid;
     double2 c = make_double2(0.0, 0.0);
-    if (i != j) {
+    double dl = 0.0;
+    if (i < n && i != j) {
       const double2 aij = a.A[i * n + j];
       const double gap = ajj - a.A[i * n + i].x;
       const double m2 = aij.x * aij.x + aij.y * aij.y;
@@ -721,17 +746,22 @@ __global__ void __launch_bounds__(32) k_ritz64_b(const RitzArgs a) {
       }
     }
     e[i] = c;
+    dls[i] = dl;
   }
-  __syncwarp();
+  __syncthreads();
   // v'_j row i: v_ij + sum_k v_ik e_k
-  double2 v = make_double2(0.0, 0.0);
+  double2 v = ritz_sum(n, [&](int i, int k) {
+    const float2 vik = Vs[i * n + k];
+    return mul_(make_double2(vik.x, vik.y), e[k]);
+  }, part);
+  if (tid >= 32) return;
+  const int i = tid;
+  double dl = dls[i];
   if (i < n) {
-    const float2 vij = a.V[i * n + j];
-    v = make_double2(vij.x, vij.y);
-    for (int k = 0; k < n; ++k) {
-      const float2 vik = a.V[i * n + k];
-      v = add_(v, mul_(make_double2(vik.x, vik.y), e[k]));
-    }
+    const float2 vij = Vs[i * n + j];
+    v = add_(make_double2(vij.x, vij.y), v);
+  } else {
+    v = make_double2(0.0, 0.0);
   }
   double nrm = v.x * v.x + v.y * v.y;
 #pragma unroll
@@ -745,9 +775,10 @@ __global__ void __launch_bounds__(32) k_ritz64_b(const RitzArgs a) {
 }
 
 cudaError_t launch_ritz64(const RitzArgs& a, cudaStream_t st) {
-  cudaError_t e = launch_pdl(k_ritz64_a, dim3(a.n), dim3(32), 0, st, a);
+  if (a.n > kMaxNc) return cudaErrorInvalidValue;
+  cudaError_t e = launch_pdl(k_ritz64_a, dim3(a.n), dim3(kRitzThreads), 0, st, a);
   if (e != cudaSuccess) return e;
-  e = launch_pdl(k_ritz64_b, dim3(a.n), dim3(32), 0, st, a);
+  e = launch_pdl(k_ritz64_b, dim3(a.n), dim3(kRitzThreads), 0, st, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
