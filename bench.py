@@ -986,10 +986,12 @@ def run_coils_fp16(args):
     """The cardiac-shaped sequence with the coil maps stored in half precision (LPS_COILS_FP16):
     frames/s and the data-consistency kernel's time per launch against float32 maps."""
     from paper_1411_6206_gb300 import lps
-    out = plan_variants((("fp32", dict(coil_format=lps.COILS_FP32)), ("fp16", dict(coil_format=lps.COILS_FP16))),
+    out = plan_variants((("fp32", dict(coil_format=lps.COILS_FP32)), ("fp16", dict(coil_format=lps.COILS_FP16)),
+                         ("fp16_maps_and_samples", dict(coil_format=lps.COILS_FP16, data_format=lps.DATA_FP16))),
                         "data_consistency")
-    out["how"] = ("same inputs, float32 maps given to both plans (the fp16 plan rounds them); the effect of the "
-                  "rounding on the reconstruction is measured by tests/test_gpu_coils_fp16.py")
+    out["how"] = ("same inputs, float32 maps and samples given to every plan (the fp16 plans round them); the "
+                  "effect of the rounding on the reconstruction is measured by tests/test_gpu_coils_fp16.py and "
+                  "tests/test_gpu_data_fp16.py")
     return out
 
 

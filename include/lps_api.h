@@ -108,6 +108,12 @@ extern "C" {
  * squares do). Maps that are already half-representable give results equal to LPS_COILS_FP32. */
 #define LPS_COILS_FP32         0
 #define LPS_COILS_FP16         1
+/* Storage of the samples (the data y of Sec. 2, kept in hybrid space d' = F_x^H d). With
+ * LPS_DATA_FP16, lps_set_data rounds the plan's hybrid copy to binary16 (each of Re and Im to
+ * the nearest value) and keeps a half-pair copy that the per-iteration data-consistency kernels
+ * read; every kernel sees the rounded values. |Re|, |Im| of d' must stay below 65504. */
+#define LPS_DATA_FP32          0
+#define LPS_DATA_FP16          1
 
 typedef struct lps_plan lps_plan;   /* opaque; owns its device workspace */
 
@@ -138,7 +144,8 @@ typedef struct lps_params {
                               (fft_z = 0); > 1: 3D frames, nz / frame_slices columns each a
                               volume of frame_slices slices with its own 3D encode (fft_z = 1)
                               or per-slice encode (fft_z = 0); float32 path, whole volumes   */
-  int reserved[3];         /* must be zero                                                  */
+  int data_format;         /* LPS_DATA_FP32 (default) | LPS_DATA_FP16                        */
+  int reserved[2];         /* must be zero                                                  */
 } lps_params;
 
 typedef struct lps_stats {

@@ -43,6 +43,10 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
+__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -216,9 +220,17 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
   for (int c = 0; c < g.ncoil; ++c) {
     const float2* stg = (c & 1) ? stg1 : stg0;
     const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
-    if (stage_d)
-      for (int i = tid; i < m; i += NTH) cp_async8(dsm + i, dh + i);
+    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * g.ncoil + c) * g.mpad : nullptr;
+    __half2* dsmh = reinterpret_cast<__half2*>(dsm);   // half samples use half the slots' bytes
+    if (stage_d) {
+      if (dhh)
+        for (int i = tid; i < m; i += NTH) cp_async4(dsmh + i, dhh + i);
+      else
+        for (int i = tid; i < m; i += NTH) cp_async8(dsm + i, dh + i);
+    }
     const float2* dsrc = stage_d ? dsm : dh;
+    const __half2* dsrch = stage_d ? dsmh : dhh;
+    auto samp = [&](int l) -> float2 { return dhh ? __half22float2(dsrch[l]) : dsrc[l]; };
     cp_async_commit();
     if (c + 1 < g.ncoil) issue_stage(c + 1, (c & 1) ? stg0 : stg1);
     cp_async_commit();
@@ -261,7 +273,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
           const unsigned bits = rbits[kz * WB + wi];
           if ((bits >> bit) & 1u) {
             const int line = rpre[kz * WB + wi] + __popc(bits & below);
-            const float2 r = csub(v[kz], dsrc[line]);
+            const float2 r = csub(v[kz], samp(line));
             resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
             v[kz] = r;
           } else {
@@ -291,7 +303,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
         const unsigned bits = rbits[kz * WB + wi];
         if ((bits >> bit) & 1u) {
           const int line = rpre[kz * WB + wi] + __popc(bits & below);
-          const float2 r = csub(v[k], dsrc[line]);
+          const float2 r = csub(v[k], samp(line));
           resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
           v[k] = r;
         } else {
@@ -515,6 +527,8 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
     float2* src = bufA;
     float2* dst = bufB;
     const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
+    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * g.ncoil + c) * g.mpad : nullptr;
+    auto samp = [&](int l) -> float2 { return dhh ? __half22float2(dhh[l]) : dh[l]; };
     if (MODE != kDcAdjoint) {
       // P = scale * C_c * Z, then the forward transform over y (rows) and z (columns).
 #pragma unroll
@@ -546,9 +560,9 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
       const int p = a.lines[l];
       float2 r;
       if (MODE == kDcAdjoint) {
-        r = dh[l];
+        r = samp(l);
       } else {
-        r = csub(src[p], dh[l]);
+        r = csub(src[p], samp(l));
         resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
       }
       dst[p] = r;

@@ -214,6 +214,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     const __half2* Ch = HALF ? a.coils_h + (long long)c * g.N + xoff + gt : nullptr;
     auto coil = [&](int z) -> float2 { return HALF ? __half22float2(__ldg(Ch + z * xy)) : __ldg(Cc + z * xy); };
     const float2* dh = a.dhyb + ((long long)x * ncoil + c) * g.mpad;
+    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * ncoil + c) * g.mpad : nullptr;
     // column phase: v[z] = sc C_c Z at (z, y = gt), transform along z
     const bool first = c == grp;
 #pragma unroll
@@ -246,7 +247,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         li[q] = lrow[s + 16 * q];
-        dv[q] = li[q] >= 0 ? dh[li[q]] : make_float2(0.f, 0.f);
+        dv[q] = li[q] >= 0 ? (dhh ? __half22float2(dhh[li[q]]) : dh[li[q]]) : make_float2(0.f, 0.f);
       }
       dft8(w, false);   // radix 8 over j: w[q] = X[ky = s + 16q]
       // residual on the sampled lines (zero elsewhere)

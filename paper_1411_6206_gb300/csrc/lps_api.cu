@@ -250,6 +250,8 @@ int validate(const lps_params* p, Geom* gout) {
   ARG(p->recursive == 0 || p->recursive == 1, "recursive must be 0 or 1");
   ARG(p->coil_format == LPS_COILS_FP32 || p->coil_format == LPS_COILS_FP16,
       "coil_format must be LPS_COILS_FP32 or LPS_COILS_FP16");
+  ARG(p->data_format == LPS_DATA_FP32 || p->data_format == LPS_DATA_FP16,
+      "data_format must be LPS_DATA_FP32 or LPS_DATA_FP16");
   if (p->nz / fs > LPS_MAX_NC || p->nz > 128) {
     set_err("%d Casorati columns of %d slices: at most LPS_MAX_NC = %d columns and 128 slices", p->nz / fs, fs,
             LPS_MAX_NC);
@@ -310,7 +312,7 @@ int free_plan(lps_plan* P) {
   if (P->gexec) cudaGraphExecDestroy(P->gexec);
   if (P->graph) cudaGraphDestroy(P->graph);
   void* bufs[] = {P->X, P->L, P->S, P->S2, P->R, P->coils, P->dhyb, P->kstage, P->hscratch, P->istage, P->arena,
-                  P->Lnew, P->coils_h};
+                  P->Lnew, P->coils_h, P->dhyb_h};
   for (void* b : bufs)
     if (b) cudaFree(b);
   if (P->h_ctrl) cudaFreeHost(P->h_ctrl);
@@ -369,10 +371,13 @@ int ensure_lines(lps_plan* P, int m) {
   if (P->dhyb) cudaFree(P->dhyb);
   if (P->kstage) cudaFree(P->kstage);
   if (P->hscratch) cudaFree(P->hscratch);
+  if (P->dhyb_h) cudaFree(P->dhyb_h);
   P->dhyb = P->kstage = P->hscratch = nullptr;
+  P->dhyb_h = nullptr;
   const size_t hyb = (size_t)P->g.nx * P->g.ncoil * cap + 4;
   int rc;
   if ((rc = dalloc(P, &P->dhyb, hyb))) return rc;
+  if (P->p.data_format == LPS_DATA_FP16 && (rc = dalloc(P, &P->dhyb_h, hyb))) return rc;
   if ((rc = dalloc(P, &P->kstage, (size_t)P->g.ncoil * cap * P->g.nxt + 4))) return rc;
   if ((rc = dalloc(P, &P->hscratch, hyb))) return rc;
   P->m_cap = cap;
@@ -387,6 +392,7 @@ DcArgs dc_args(lps_plan* P) {
   a.coils = P->coils;
   a.coils_h = P->coils_h;
   a.dhyb = P->dhyb;
+  a.dhyb_h = P->dhyb_h;
   a.lines = P->lines;
   a.tw_y = P->tw_y;
   a.tw_z = P->tw_z;
@@ -796,6 +802,7 @@ int lps_estimate_device_bytes(const lps_params* p, size_t* bytes) {
   if (p->precision != LPS_FP32) b += N * 8;    // reprojection output
   b += (size_t)g.ncoil * N * 8;                // coils
   if (p->coil_format == LPS_COILS_FP16) b += (size_t)g.ncoil * N * 4;   // half-precision copy
+  if (p->data_format == LPS_DATA_FP16) b += ((size_t)g.nx * g.ncoil * m + 4) * 4;   // half samples
   b += 2 * ((size_t)g.nx * g.ncoil * m + 4) * 8 + ((size_t)g.nxt * g.ncoil * m + 4) * 8;   // hybrid, scratch, staging
   b += (size_t)gram_part_capacity(g) * g.nc * g.nc * 8 + 2 * g.nc * g.nc * 8;
   b += (size_t)g.nx * 4 + (size_t)g.ntiles * 16 + 2 * N / 8;
@@ -975,6 +982,9 @@ int lps_set_data(lps_plan* P, const void* kdata, int nlines) {
   a.persist = P->persist;
   a.inverse = 1;
   LK(launch_xfft(a, P->st));
+  // LPS_DATA_FP16: round the hybrid samples in place and keep the half-pair copy
+  if (P->dhyb_h)
+    LK(launch_round_half(P->dhyb, P->dhyb_h, (long long)P->g.nx * P->g.ncoil * P->g.mpad, P->st));
   P->have_data = true;
   P->state_ready = false;
   return LPS_OK;
@@ -1271,6 +1281,7 @@ int lps_adjoint(lps_plan* P, const void* kdata, void* image) {
   const bool dev = is_device_ptr(image);
   DcArgs a = dc_args(P);
   a.dhyb = P->hscratch;
+  a.dhyb_h = nullptr;   // the operator's own samples, in float32
   a.X = dev ? (float2*)image : P->istage;
   LK(launch_dc(a, kDcAdjoint, P->st));
   if (!dev) {

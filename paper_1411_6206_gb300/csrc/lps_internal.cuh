@@ -107,6 +107,7 @@ struct DcArgs {
   float2* recon;            // update: optional copy of Z = L + S
   const float2* coils;      // [ncoil][nz][nx][ny]
   const __half2* coils_h;   // the same maps in half precision (LPS_COILS_FP16), else nullptr
+  const __half2* dhyb_h;    // the hybrid samples in half precision (LPS_DATA_FP16), else nullptr
   const float2* dhyb;       // [nx][ncoil][mpad] hybrid-space samples
   float2* hyb_out;          // forward: [nx][ncoil][mpad]
   const int* lines;         // padded in-plane position kz*nyp + ky of each line

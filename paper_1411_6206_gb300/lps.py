@@ -29,6 +29,7 @@ ERR_UNSUPPORTED = -8
 
 LAYOUT_SLICES, LAYOUT_FRAMES = 0, 1
 COILS_FP32, COILS_FP16 = 0, 1
+DATA_FP32, DATA_FP16 = 0, 1
 EIG_FP32, EIG_FP64 = 0, 1
 FP32, TF32_REFINE, BF16_REFINE = 0, 1, 2
 KERNEL_CLASSES = 6
@@ -45,7 +46,8 @@ class Params(C.Structure):
                 ("lambda_p", C.c_double), ("rank_tau", C.c_double), ("tol", C.c_double),
                 ("precision", C.c_int), ("eig_precision", C.c_int), ("support_rule", C.c_int),
                 ("recursive", C.c_int), ("coil_format", C.c_int), ("nx_total", C.c_int), ("x0", C.c_int),
-                ("wavelet_dims", C.c_int), ("frame_slices", C.c_int), ("reserved", C.c_int * 3)]
+                ("wavelet_dims", C.c_int), ("frame_slices", C.c_int), ("data_format", C.c_int),
+                ("reserved", C.c_int * 2)]
 
 
 class Stats(C.Structure):

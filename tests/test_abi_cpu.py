@@ -69,6 +69,18 @@ def test_estimate_device_bytes(lps):
     assert lps.support_words(p) == N // 32
 
 
+def test_half_precision_samples_are_an_extra_copy(lps):
+    """LPS_DATA_FP16 keeps a binary16 copy of the hybrid samples: nx ncoil m 4 more bytes."""
+    hdr = open(os.path.join(ROOT, "include", "lps_api.h")).read()
+    assert re.search(r"#define LPS_DATA_FP32\s+0\b", hdr) and re.search(r"#define LPS_DATA_FP16\s+1\b", hdr)
+    kw = dict(nx=128, ny=128, nz=16, ncoil=8)
+    b32 = lps.estimate_device_bytes(lps.params_init(data_format=lps.DATA_FP32, **kw))
+    b16 = lps.estimate_device_bytes(lps.params_init(data_format=lps.DATA_FP16, **kw))
+    assert b16 > b32
+    with pytest.raises(lps.LpsError):
+        lps.plan_create(lps.params_init(data_format=2, **kw))
+
+
 def test_half_precision_coil_maps_are_an_extra_copy(lps):
     """LPS_COILS_FP16 keeps a half-precision copy of the maps next to the rounded complex64
     ones: ncoil * N * 4 more bytes; the header and the binding agree on the constants."""
