@@ -43,10 +43,6 @@ __device__ __forceinline__ void cp_async8(void* sdst, const void* gsrc) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gsrc) : "memory");
 }
-__device__ __forceinline__ void cp_async4(void* sdst, const void* gsrc) {
-  const unsigned s = (unsigned)__cvta_generic_to_shared(sdst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gsrc) : "memory");
-}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() {
@@ -220,17 +216,24 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
   for (int c = 0; c < g.ncoil; ++c) {
     const float2* stg = (c & 1) ? stg1 : stg0;
     const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
-    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * g.ncoil + c) * g.mpad : nullptr;
-    __half2* dsmh = reinterpret_cast<__half2*>(dsm);   // half samples use half the slots' bytes
-    if (stage_d) {
-      if (dhh)
-        for (int i = tid; i < m; i += NTH) cp_async4(dsmh + i, dhh + i);
-      else
-        for (int i = tid; i < m; i += NTH) cp_async8(dsm + i, dh + i);
+    // LPS_DATA_FP16: the half pairs are loaded into registers here and widened into the
+    // staging slots after the row phase (their latency hidden behind it); otherwise cp.async
+    // copies the float32 samples. Frames with more lines than slots read the rounded float32
+    // copy from L2.
+    constexpr int kHalfPer = 8;
+    const bool half_stage = stage_d && a.dhyb_h != nullptr && m <= kHalfPer * NTH;
+    __half2 hv[kHalfPer];
+    if (half_stage) {
+      const __half2* dhh = a.dhyb_h + ((long long)x * g.ncoil + c) * g.mpad;
+#pragma unroll
+      for (int u = 0; u < kHalfPer; ++u) {
+        const int i = tid + u * NTH;
+        hv[u] = i < m ? dhh[i] : __half2{};
+      }
+    } else if (stage_d) {
+      for (int i = tid; i < m; i += NTH) cp_async8(dsm + i, dh + i);
     }
     const float2* dsrc = stage_d ? dsm : dh;
-    const __half2* dsrch = stage_d ? dsmh : dhh;
-    auto samp = [&](int l) -> float2 { return dhh ? __half22float2(dsrch[l]) : dsrc[l]; };
     cp_async_commit();
     if (c + 1 < g.ncoil) issue_stage(c + 1, (c & 1) ? stg0 : stg1);
     cp_async_commit();
@@ -255,6 +258,13 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
         for (int k = 0; k < Q; ++k) Sf[z * PS + l * QP + k] = v[k];
       }
     }
+    if (half_stage) {
+#pragma unroll
+      for (int u = 0; u < kHalfPer; ++u) {
+        const int i = tid + u * NTH;
+        if (i < m) dsm[i] = __half22float2(hv[u]);
+      }
+    }
     cp_async_wait<1>();   // the samples of coil c (this thread's share)
     __syncthreads();
     // column phase: z transform, residual on the sampled lines, inverse z transform
@@ -273,7 +283,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
           const unsigned bits = rbits[kz * WB + wi];
           if ((bits >> bit) & 1u) {
             const int line = rpre[kz * WB + wi] + __popc(bits & below);
-            const float2 r = csub(v[kz], samp(line));
+            const float2 r = csub(v[kz], dsrc[line]);
             resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
             v[kz] = r;
           } else {
@@ -303,7 +313,7 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
         const unsigned bits = rbits[kz * WB + wi];
         if ((bits >> bit) & 1u) {
           const int line = rpre[kz * WB + wi] + __popc(bits & below);
-          const float2 r = csub(v[k], samp(line));
+          const float2 r = csub(v[k], dsrc[line]);
           resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
           v[k] = r;
         } else {
@@ -526,9 +536,7 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
     }
     float2* src = bufA;
     float2* dst = bufB;
-    const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;
-    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * g.ncoil + c) * g.mpad : nullptr;
-    auto samp = [&](int l) -> float2 { return dhh ? __half22float2(dhh[l]) : dh[l]; };
+    const float2* dh = a.dhyb + ((long long)x * g.ncoil + c) * g.mpad;   // the rounded copy with LPS_DATA_FP16
     if (MODE != kDcAdjoint) {
       // P = scale * C_c * Z, then the forward transform over y (rows) and z (columns).
 #pragma unroll
@@ -560,9 +568,9 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
       const int p = a.lines[l];
       float2 r;
       if (MODE == kDcAdjoint) {
-        r = samp(l);
+        r = dh[l];
       } else {
-        r = csub(src[p], samp(l));
+        r = csub(src[p], dh[l]);
         resid = fmaf(r.x, r.x, fmaf(r.y, r.y, resid));
       }
       dst[p] = r;

@@ -52,7 +52,7 @@ struct RegLayout {
 };
 
 // HALF: coil maps read as half-precision pairs (LPS_COILS_FP16), widened exactly to float32.
-template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF>
+template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF, bool DH>
 __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   using Lay = RegLayout<G, ACCS>;
   static_assert(!(ONE && ACCS), "one coil per group needs no accumulator");
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
     const __half2* Ch = HALF ? a.coils_h + (long long)c * g.N + xoff + gt : nullptr;
     auto coil = [&](int z) -> float2 { return HALF ? __half22float2(__ldg(Ch + z * xy)) : __ldg(Cc + z * xy); };
     const float2* dh = a.dhyb + ((long long)x * ncoil + c) * g.mpad;
-    const __half2* dhh = a.dhyb_h ? a.dhyb_h + ((long long)x * ncoil + c) * g.mpad : nullptr;
+    const __half2* dhh = DH ? a.dhyb_h + ((long long)x * ncoil + c) * g.mpad : nullptr;
     // column phase: v[z] = sc C_c Z at (z, y = gt), transform along z
     const bool first = c == grp;
 #pragma unroll
@@ -247,7 +247,7 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         li[q] = lrow[s + 16 * q];
-        dv[q] = li[q] >= 0 ? (dhh ? __half22float2(dhh[li[q]]) : dh[li[q]]) : make_float2(0.f, 0.f);
+        dv[q] = li[q] >= 0 ? (DH ? __half22float2(dhh[li[q]]) : dh[li[q]]) : make_float2(0.f, 0.f);
       }
       dft8(w, false);   // radix 8 over j: w[q] = X[ky = s + 16q]
       // residual on the sampled lines (zero elsewhere)
@@ -373,14 +373,14 @@ __global__ void __launch_bounds__(G * kGT, 1) k_dc_reg(const DcArgs a) {
   }
 }
 
-template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF>
+template <int G, bool FFTZ, bool ONE, bool ACCS, bool HALF, bool DH = false>
 cudaError_t launch_reg(const DcArgs& a, cudaStream_t st) {
   constexpr size_t smem = RegLayout<G, ACCS>::bytes();
   static_assert(smem <= 227 * 1024, "shared memory");
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e =
-        cudaFuncSetAttribute(k_dc_reg<G, FFTZ, ONE, ACCS, HALF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_dc_reg<G, FFTZ, ONE, ACCS, HALF, DH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
@@ -398,7 +398,7 @@ cudaError_t launch_reg(const DcArgs& a, cudaStream_t st) {
   attr[1].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 2;
-  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dc_reg<G, FFTZ, ONE, ACCS, HALF>, a);
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_dc_reg<G, FFTZ, ONE, ACCS, HALF, DH>, a);
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
@@ -418,6 +418,18 @@ cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st) {
   // dc_reg_groups: 4 or 8 coil groups; 104: four groups with their coil sums in shared memory
   // (used when there are more coils than groups). Half-precision coil maps: four groups.
   const bool accs = a.g.dc_reg_groups > 100;
+  // half-precision samples (LPS_DATA_FP16) are read as half pairs by the four-group variants
+  // with one coil per group or the coil sums in shared memory (the defaults); the others read
+  // the rounded float32 copy (the same values)
+  if (a.dhyb_h && a.g.dc_reg_groups % 100 == 4 && (a.g.ncoil <= 4 || accs)) {
+    const bool one = a.g.ncoil <= 4;
+    if (a.coils_h) {
+      if (one) return fz ? launch_reg<4, true, true, false, true, true>(a, st) : launch_reg<4, false, true, false, true, true>(a, st);
+      return fz ? launch_reg<4, true, false, true, true, true>(a, st) : launch_reg<4, false, false, true, true, true>(a, st);
+    }
+    if (one) return fz ? launch_reg<4, true, true, false, false, true>(a, st) : launch_reg<4, false, true, false, false, true>(a, st);
+    return fz ? launch_reg<4, true, false, true, false, true>(a, st) : launch_reg<4, false, false, true, false, true>(a, st);
+  }
   if (a.coils_h && a.g.dc_reg_groups % 100 == 4) {
     if (a.g.ncoil <= 4) return fz ? launch_reg<4, true, true, false, true>(a, st) : launch_reg<4, false, true, false, true>(a, st);
     if (accs) return fz ? launch_reg<4, true, false, true, true>(a, st) : launch_reg<4, false, false, true, true>(a, st);

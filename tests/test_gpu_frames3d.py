@@ -142,3 +142,27 @@ def test_refused_shapes(L):
     assert code(precision=L.BF16_REFINE) == L.ERR_UNSUPPORTED
     assert code(nz=8 * 40, frame_slices=8) == L.ERR_UNSUPPORTED   # more than 128 slices
     assert code(wavelet_dims=3, frame_slices=4, nz=16) == L.ERR_INVALID_ARG   # 3D Haar blocks would cross frames
+
+
+def test_recursion_over_two_segments(L):
+    """With recursive = 1 the second segment starts from the first segment's support and its
+    T singular values (one per frame column); the oracle reconstructs segment 2 with the prior
+    the GPU installed."""
+    from tests.abi_layout import bits_to_mallat
+    T, fs, nx, ny, nc, iters = 4, 4, 16, 32, 2, 20
+    c1 = segment(T, fs, nx, ny, nc, seed=3)
+    x2 = segment(T, fs, nx, ny, nc, seed=8)["x"]
+    d2 = c64(O.E(x2, up(c1["coils"]), c1["mask"], 1, fs))
+    pl = plan_for(L, c1, T, nx, ny, nc, max_iters=iters, recursive=1, lambda_p=0.5)
+    pl.reconstruct_frame(stats=False)
+    words = np.empty(pl.support_words(), np.uint32)
+    sig = np.empty(T)
+    L.get_support(pl.handle, words, sig)
+    prior = O.Prior(support=bits_to_mallat(words, T * fs, nx, ny, 3), sigma=sig.copy())
+    assert prior.support.any() and np.all(sig >= 0)
+    pl.set_data(dev(d2))
+    recon = torch.empty((T * fs, nx, ny), dtype=torch.complex64, device="cuda")
+    pl.reconstruct_frame(recon=recon)
+    ref = O.priori_ls(up(d2), up(c1["coils"]), c1["mask"], oracle_params(pl.params), prior)
+    assert O.nrmse(recon.cpu().numpy(), ref.recon) <= E2E_TOL
+    pl.close()
