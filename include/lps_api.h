@@ -262,6 +262,15 @@ int lps_lowrank_reproject(lps_plan* plan, const void* X, const void* S, const vo
  * or host buffer [nz][nx][ny] complex64 (a host buffer makes the call synchronous). */
 int lps_get_recon(lps_plan* plan, void* out);
 
+/* Test hook (not in the paper; exercises the failure path of the bounded waits without
+ * faulting or hanging the GPU). Arms a one-shot stall for the next lps_data_consistency call:
+ * on the staged-coil runtime-sized kernel (lps_apply_tune dc_variant 1, else LPS_ERR_STATE),
+ * every CTA waits for its first coil on an mbarrier that nothing completes, for `polls` polls
+ * (1..2^20), records the timeout, lets the coil copies it has in flight land (normal wait
+ * budget) and returns. The call then returns LPS_ERR_TIMEOUT with the error flag cleared; the
+ * plan and the context stay usable. */
+int lps_test_stall_wait(lps_plan* plan, int polls);
+
 /* ---- autotuner ---------------------------------------------------------------------
  * Not in the paper (it fixes no launch shapes): times, on the plan's resident coils, mask and
  * data, the candidate shapes of the two per-iteration kernels whose shape is a free choice,

@@ -14,7 +14,7 @@ size_t dc_smem_bytes(const Geom& g) {
   b += 2 * (size_t)g.planeP * sizeof(float2);
   if (!g.dc_direct) b += 2 * (size_t)g.plane * sizeof(float2);   // staged coil planes
   b += (size_t)(g.ny + g.nz + ((g.ny + g.nz) & 1)) * sizeof(float2);
-  b += 2 * sizeof(uint64_t);
+  b += 3 * sizeof(uint64_t);
   b += 32 * sizeof(float);
   b += (size_t)g.nz * g.nz * sizeof(float2);   // W of the iteration form
   return b;

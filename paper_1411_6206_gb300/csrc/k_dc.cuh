@@ -379,20 +379,21 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   float2* twy = coilS1 + (STAGE ? plane : 0);
   float2* twz = twy + ny;
   uint64_t* mbar = reinterpret_cast<uint64_t*>(twz + nz + ((ny + nz) & 1));
-  float* red = reinterpret_cast<float*>(mbar + 2);
+  float* red = reinterpret_cast<float*>(mbar + 3);   // mbar[2]: the stall test hook's barrier
   float2* wsh = reinterpret_cast<float2*>(red + 32);   // [nz][nz] W of the iteration form
 
   const int tid = threadIdx.x;
   const int x = blockIdx.x;
   const long long xy = (long long)nx * ny;
   const int m = a.persist->nlines;
-  int* errp = a.ctrl ? &a.ctrl->err : nullptr;
+  int* errp = a.ctrl ? &a.ctrl->err : a.err_word;
 
   for (int i = tid; i < ny; i += NTH) twy[i] = a.tw_y[i];
   for (int i = tid; i < g.zn; i += NTH) twz[i] = a.tw_z[i];
   if (STAGE && tid == 0) {
     mbar_init(&mbar[0], 1);
     mbar_init(&mbar[1], 1);
+    mbar_init(&mbar[2], 1);   // never arrived on: the stall test hook waits on it
     fence_mbar_init();
   }
   __syncthreads();
@@ -526,10 +527,21 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
     const __half2* hcoil = HALF ? a.coils_h + (long long)c * g.N + (long long)x * ny : nullptr;
     auto gc = [&](int k) -> float2 { return HALF ? __half22float2(__ldg(hcoil + go[k])) : __ldg(gcoil + go[k]); };
     if (STAGE) {
-      const bool bad = !mbar_wait_bounded(&mbar[s], (c >> 1) & 1, errp);
+      // test hook: the first coil waits on mbar[2], which nothing completes, for stall_polls
+      // polls, so that the timeout path below runs
+      const bool stall = c == 0 && a.stall_polls > 0;
+      const bool bad = stall ? !mbar_wait_bounded(&mbar[2], 0, errp, a.stall_polls)
+                             : !mbar_wait_bounded(&mbar[s], (c >> 1) & 1, errp);
       if (__syncthreads_or(bad)) {
-        // Give up on this plane; first let the other slot's copy (if any) land.
-        if (tid == 0 && (inflight & (2u >> s))) mbar_wait_bounded(&mbar[s ^ 1], ((c + 1) >> 1) & 1, nullptr);
+        // Give up on this plane; first let the copies still in flight land (normal budget).
+        if (tid == 0) {
+          if (stall) {
+            if (inflight & 1u) mbar_wait_bounded(&mbar[0], 0, nullptr);
+            if (inflight & 2u) mbar_wait_bounded(&mbar[1], 0, nullptr);
+          } else if (inflight & (2u >> s)) {
+            mbar_wait_bounded(&mbar[s ^ 1], ((c + 1) >> 1) & 1, nullptr);
+          }
+        }
         return;
       }
       if (tid == 0) inflight &= ~(1u << s);

@@ -1308,7 +1308,25 @@ int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm
   a.S = nullptr;
   a.X = dst;
   a.dc_part = P->dc_part;
+  const int stall = P->stall_polls;
+  P->stall_polls = 0;
+  if (stall) {
+    a.stall_polls = stall;
+    a.err_word = &P->ctrl->err;
+    CK(cudaMemsetAsync(&P->ctrl->err, 0, sizeof(int), P->st));
+  }
   LK(launch_dc(a, kDcUpdate, P->st));
+  if (stall) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, &P->ctrl->err, sizeof(int), cudaMemcpyDeviceToHost, P->st));
+    CK(cudaStreamSynchronize(P->st));
+    CK(cudaMemsetAsync(&P->ctrl->err, 0, sizeof(int), P->st));
+    P->state_ready = false;
+    if (err & kErrTimeout) {
+      set_err("data consistency: a bounded wait ran out (test hook)");
+      return LPS_ERR_TIMEOUT;
+    }
+  }
   if (!dev) CK(cudaMemcpyAsync(X, P->R, img, cudaMemcpyDefault, P->st));
   if (resid_norm2) {
     std::vector<float> part((size_t)P->g.nx * 4);
@@ -1321,6 +1339,17 @@ int lps_data_consistency(lps_plan* P, const void* Z, void* X, double* resid_norm
     CK(cudaStreamSynchronize(P->st));
   }
   P->state_ready = false;
+  return LPS_OK;
+}
+
+int lps_test_stall_wait(lps_plan* P, int polls) {
+  ARG(P != nullptr, "plan is NULL");
+  ARG(polls >= 1 && polls <= (1 << 20), "polls must be in 1..2^20");
+  if (!(P->g.dc_generic && !P->g.dc_direct)) {
+    set_err("the stall hook needs the staged-coil runtime-sized kernel (lps_apply_tune dc_variant 1)");
+    return LPS_ERR_STATE;
+  }
+  P->stall_polls = polls;
   return LPS_OK;
 }
 

@@ -108,6 +108,9 @@ struct DcArgs {
   const float2* coils;      // [ncoil][nz][nx][ny]
   const __half2* coils_h;   // the same maps in half precision (LPS_COILS_FP16), else nullptr
   const __half2* dhyb_h;    // the hybrid samples in half precision (LPS_DATA_FP16), else nullptr
+  int* err_word;            // error flags when ctrl is null (operator calls), else nullptr
+  int stall_polls;          // test hook (staged-coil kernel): > 0 makes the first coil wait on an
+                            // mbarrier that nothing completes, with this poll budget
   const float2* dhyb;       // [nx][ncoil][mpad] hybrid-space samples
   float2* hyb_out;          // forward: [nx][ncoil][mpad]
   const int* lines;         // padded in-plane position kz*nyp + ky of each line
@@ -315,9 +318,11 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait: returns false (and records kErrTimeout) if the phase never completes.
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err) {
-  for (long long i = 0; i < kSpinLimit; ++i) {
+// Bounded wait: returns false (and records kErrTimeout) if the phase never completes within
+// `limit` polls.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity, int* err,
+                                                  long long limit = kSpinLimit) {
+  for (long long i = 0; i < limit; ++i) {
     if (mbar_try_wait(bar, parity)) return true;
     if (i > 64) __nanosleep(64);
   }

@@ -128,6 +128,7 @@ _SIGS = {
     "lps_casorati_gram": ([_VP, _VP, _VP, _VP], C.c_int),
     "lps_lowrank_reproject": ([_VP, _VP, _VP, _VP, _VP], C.c_int),
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
+    "lps_test_stall_wait": ([_VP, C.c_int], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
     "lps_shift_prior_columns": ([_VP, C.c_int], C.c_int),
@@ -342,6 +343,12 @@ def casorati_gram(plan: int, X, S, G):
 def lowrank_reproject(plan: int, X, S, W, L):
     """L = (X - S) W over the Casorati columns (S may be None), plan precision."""
     _check(load().lps_lowrank_reproject(plan, ptr(X), ptr(S), ptr(W), ptr(L)), "lowrank_reproject")
+
+
+def test_stall_wait(plan: int, polls: int):
+    """Test hook: the next data_consistency call on the staged-coil kernel waits, once, on an
+    mbarrier that nothing completes (polls polls) and returns LPS_ERR_TIMEOUT."""
+    _check(load().lps_test_stall_wait(plan, polls), "test_stall_wait")
 
 
 def data_consistency(plan: int, Z, X) -> float:
