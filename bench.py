@@ -733,6 +733,22 @@ def run_batched(args):
     res.update({"problems": len(ws_), "frames": total, "frame_steps": T, "autotune_s": round(t_tune, 3),
                 "how": "one graph launch per frame step over all problems (inactive members return at "
                        "once); plain = each problem's frame graph launched alone, in order"})
+    # one data-consistency step (operator form) of all 64 problems: each member's own tuned kernel
+    # as graph branches against one persistent launch over the descriptor table
+    for i in range(len(ws_)):
+        B.set_active(i, True)
+    gen = torch.Generator(device=dev).manual_seed(3)
+    Z = [torch.randn((w.nz, w.nx, w.ny), dtype=torch.complex64, device=dev, generator=gen) for w in ws_]
+    X = [torch.empty_like(z) for z in Z]
+    step = {}
+    for name, pers in (("member_kernels", False), ("persistent", True)):
+        B.data_consistency(Z, X, persistent=pers)
+        step[name + "_ms"] = round(float(np.median([B.data_consistency(Z, X, persistent=pers) for _ in range(5)])), 3)
+    step["how"] = ("step (4) of every problem once: each member's tuned kernel (register-transform loop, "
+                   "compile-time or runtime-sized) as parallel graph branches, against one persistent launch "
+                   "whose CTAs take (problem, plane) items from a counter and run the runtime-sized body; "
+                   "median of 5, device time")
+    res["dc_step_all_problems"] = step
     B.close()
     return res
 

@@ -323,6 +323,15 @@ int lps_batch_size(lps_batch* batch);
 int lps_batch_plan(lps_batch* batch, int i, lps_plan** out);   /* owned by the batch */
 int lps_batch_set_active(lps_batch* batch, int i, int active);  /* default: active */
 int lps_batch_autotune(lps_batch* batch);                       /* lps_autotune per active member */
+/* Step (4) alone (operator form, X = Z - E^H(E Z - d), no Gram) on every active member, Z[i] and
+ * X[i] device images of member i ([nz][nx][ny] complex64; ignored for inactive members), and
+ * the device time of the launch in *ms (may be NULL). persistent = 0: each member's own
+ * data-consistency kernel (the one its plan runs), as parallel branches of one graph;
+ * 1: one persistent launch over the members' descriptor table, CTAs taking (member, plane) items
+ * from a counter and running the runtime-sized kernel's body (planes of at most 6144 elements,
+ * else LPS_ERR_UNSUPPORTED). Not in the paper: it measures the batched layout against a single
+ * persistent kernel. Synchronises the batch stream. */
+int lps_batch_data_consistency(lps_batch* batch, void* const* Z, void* const* X, int persistent, float* ms);
 int lps_batch_reconstruct(lps_batch* batch);
 
 /* ---- serving loop -------------------------------------------------------------------

@@ -87,6 +87,67 @@ static cudaError_t launch_dc_rt(const DcArgs& a, cudaStream_t st) {
 #undef LPS_RT_DISPATCH
 }
 
+// One persistent launch over a batch's descriptor table (operator form of the update): each CTA
+// takes (member, plane) items from an atomic counter, copies the member's arguments to shared
+// memory and runs the plane with the runtime-sized body (coil maps read from L2, up to 24
+// elements per thread, the shared memory of the largest member). No CTA waits on another.
+__global__ void __launch_bounds__(kThreads, 1) k_dc_persist(const DcArgs* __restrict__ table,
+                                                          const int* __restrict__ start, int nm, int* counter) {
+  __shared__ DcArgs sa;
+  __shared__ int item_s, member_s;
+  const int total = start[nm];
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int it = atomicAdd(counter, 1);
+      int m = 0;
+      while (m + 1 < nm && start[m + 1] <= it) ++m;
+      item_s = it;
+      member_s = m;
+    }
+    __syncthreads();
+    const int it = item_s, m = member_s;
+    if (it >= total) return;
+    const int* src = reinterpret_cast<const int*>(table + m);
+    int* dst = reinterpret_cast<int*>(&sa);
+    for (int i = threadIdx.x; i < (int)(sizeof(DcArgs) / sizeof(int)); i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    dc_plane<24, kDcUpdate, false, false, 0, 0>(sa, it - start[m]);
+    __syncthreads();
+  }
+}
+static_assert(sizeof(DcArgs) % sizeof(int) == 0, "DcArgs copied as words");
+
+// The persistent form needs planes of at most 24 * kThreads elements; smem: the largest
+// member's runtime-sized direct layout.
+bool dc_persist_fits(const Geom& g) {
+  Geom gd = g;
+  gd.dc_direct = 1;
+  return g.plane <= 24 * kThreads && dc_smem_bytes(gd) + sizeof(DcArgs) + 64 <= 227 * 1024;
+}
+
+size_t dc_persist_smem(const Geom& g) {
+  Geom gd = g;
+  gd.dc_direct = 1;
+  return dc_smem_bytes(gd);
+}
+
+cudaError_t launch_dc_persist(const DcArgs* table, const int* start, int nm, int* counter, size_t smem,
+                              cudaStream_t st) {
+  // the kernel's static shared memory (its argument copy) counts against the same 227 KB
+  cudaError_t e = cudaFuncSetAttribute(k_dc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0, sms = 0, per_sm = 0;
+  e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dc_persist, kThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidValue;
+  e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+  if (e != cudaSuccess) return e;
+  k_dc_persist<<<per_sm * sms, kThreads, smem, st>>>(table, start, nm, counter);
+  return cudaGetLastError();
+}
+
 // The update of a 128 x 16 plane goes to the register-transform kernel (k_dc_reg) unless the
 // plan selected another variant; planes of ny = 16 Q (Q = 4..10) by even nz <= 32 to k_dc with
 // the register-transform coil loop; other plane sizes with a compile-time specialisation go to

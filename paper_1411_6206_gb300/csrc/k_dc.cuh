@@ -360,8 +360,9 @@ __device__ __forceinline__ float dc_rt_coils(const DcArgs& a, const float2* __re
 // (LPS_COILS_FP16), widened exactly to float32.
 // RTZ, RTQ > 0: the coil loop of the update runs on register transforms (dc_rt_coils) for
 // planes of ny = 16 RTQ by nz = RTZ.
+// The work of one x-plane x (the body of k_dc; also run by the persistent batch kernel).
 template <int EPT, int MODE, bool STAGE, bool HALF, int RTZ = 0, int RTQ = 0>
-__global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1 : 2) k_dc(const DcArgs a) {
+__device__ __forceinline__ void dc_plane(const DcArgs& a, const int x) {
   constexpr int NTH = dc_threads(RTZ, RTQ);
   static_assert(!(HALF && (STAGE || MODE != kDcUpdate)), "half-precision coil maps: direct update only");
   static_assert(RTQ == 0 || (MODE == kDcUpdate && !STAGE && !HALF), "register transforms: direct float32 update only");
@@ -383,7 +384,6 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   float2* wsh = reinterpret_cast<float2*>(red + 32);   // [nz][nz] W of the iteration form
 
   const int tid = threadIdx.x;
-  const int x = blockIdx.x;
   const long long xy = (long long)nx * ny;
   const int m = a.persist->nlines;
   int* errp = a.ctrl ? &a.ctrl->err : a.err_word;
@@ -669,6 +669,11 @@ __global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1
   }
 }
 
+
+template <int EPT, int MODE, bool STAGE, bool HALF, int RTZ = 0, int RTQ = 0>
+__global__ void __launch_bounds__(dc_threads(RTZ, RTQ), (STAGE || RTZ >= 20) ? 1 : 2) k_dc(const DcArgs a) {
+  dc_plane<EPT, MODE, STAGE, HALF, RTZ, RTQ>(a, blockIdx.x);
+}
 
 // Elements per thread of the runtime-sized kernel's elementwise phases, rounded up to the
 // compiled values (1, 2, 4, 8, 16, 24; -1: plane too large).

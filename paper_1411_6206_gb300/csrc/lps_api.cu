@@ -742,6 +742,7 @@ int plan_frame_done(lps_plan* P) {
   return LPS_OK;
 }
 DcArgs plan_dc_args(lps_plan* P) { return dc_args(P); }
+bool plan_is_device_ptr(const void* p) { return is_device_ptr(p); }
 }  // namespace lps
 
 extern "C" {

@@ -492,4 +492,97 @@ int lps_batch_reconstruct(lps_batch* B) {
   return LPS_OK;
 }
 
+int lps_batch_data_consistency(lps_batch* B, void* const* Z, void* const* X, int persistent, float* ms) {
+  ARG(B != nullptr && Z != nullptr && X != nullptr, "NULL argument");
+  std::vector<DcArgs> tab;
+  std::vector<int> start{0};
+  size_t smem = 0;
+  int rc;
+  for (int i = 0; i < (int)B->plans.size(); ++i) {
+    if (!B->active[i]) continue;
+    lps_plan* P = B->plans[i];
+    if ((rc = plan_need_ready(P))) return rc;
+    ARG(Z[i] != nullptr && X[i] != nullptr && plan_is_device_ptr(Z[i]) && plan_is_device_ptr(X[i]),
+        "Z and X of an active member must be device pointers");
+    DcArgs a = plan_dc_args(P);
+    a.L = (const float2*)Z[i];
+    a.S = nullptr;
+    a.X = (float2*)X[i];
+    a.dc_part = P->dc_part;
+    if (persistent) {
+      if (!dc_persist_fits(a.g)) {
+        set_err("member %d: plane of %d elements does not fit the persistent form", i, a.g.plane);
+        return LPS_ERR_UNSUPPORTED;
+      }
+      smem = std::max(smem, dc_persist_smem(a.g));
+    }
+    tab.push_back(a);
+    start.push_back(start.back() + a.g.nx);
+  }
+  if (tab.empty()) return LPS_OK;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  DcArgs* dtab = nullptr;
+  int* dint = nullptr;
+  rc = LPS_OK;
+  auto fail = [&](cudaError_t e) {
+    set_err("%s", cudaGetErrorString(e));
+    cudaGetLastError();   // a failed launch leaves nothing behind for the plans' next launches
+    rc = LPS_ERR_CUDA;
+  };
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e != cudaSuccess) fail(e);
+  if (!rc && !persistent) {
+    // each member's own kernel, as parallel branches of one graph
+    e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaGraphCreate(&graph, 0);
+    for (size_t k = 0; e == cudaSuccess && k < tab.size(); ++k) {
+      cudaGraph_t child = nullptr;
+      e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        const cudaError_t el = launch_dc(tab[k], kDcUpdate, cs);
+        e = cudaStreamEndCapture(cs, &child);
+        if (e == cudaSuccess) e = el;
+      }
+      cudaGraphNode_t node;
+      if (e == cudaSuccess) e = cudaGraphAddChildGraphNode(&node, graph, nullptr, 0, child);
+      if (child) cudaGraphDestroy(child);
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, B->st);
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, B->st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, B->st);
+    if (e != cudaSuccess) fail(e);
+  } else if (!rc) {
+    const int nm = (int)tab.size();
+    e = cudaMalloc(&dtab, tab.size() * sizeof(DcArgs));
+    if (e == cudaSuccess) e = cudaMalloc(&dint, (start.size() + 1) * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dtab, tab.data(), tab.size() * sizeof(DcArgs), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(dint, start.data(), start.size() * sizeof(int), cudaMemcpyHostToDevice, B->st);
+    if (e == cudaSuccess) e = cudaEventRecord(e0, B->st);
+    if (e == cudaSuccess) e = launch_dc_persist(dtab, dint, nm, dint + start.size(), smem, B->st);
+    if (e == cudaSuccess) e = cudaEventRecord(e1, B->st);
+    if (e != cudaSuccess) fail(e);
+  }
+  if (!rc) {
+    e = cudaEventSynchronize(e1);
+    float t = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, e0, e1);
+    if (e != cudaSuccess) fail(e);
+    else if (ms) *ms = t;
+  }
+  cudaStreamSynchronize(B->st);
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  if (cs) cudaStreamDestroy(cs);
+  if (dtab) cudaFree(dtab);
+  if (dint) cudaFree(dint);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  return rc;
+}
+
 }  // extern "C"

@@ -224,6 +224,11 @@ bool dc_has_fixed(const Geom& g);
 bool dc_reg_applies(const Geom& g);
 bool dc_rt_geometry(const Geom& g);   // a register-transform instantiation exists for the plane
 bool dc_rt_applies(const Geom& g);
+// persistent batch form of the update (operator form): one launch over a descriptor table
+bool dc_persist_fits(const Geom& g);
+size_t dc_persist_smem(const Geom& g);
+cudaError_t launch_dc_persist(const DcArgs* table, const int* start, int nm, int* counter, size_t smem,
+                              cudaStream_t st);
 cudaError_t launch_dc_reg(const DcArgs& a, cudaStream_t st);
 int dc_gram_parts(const Geom& g);
 int gram_tc_parts(const Geom& g);

@@ -122,5 +122,6 @@ int plan_need_ready(lps_plan* P);         // coils, mask and data set
 int plan_upload_persist(lps_plan* P, bool with_v);
 int plan_frame_done(lps_plan* P);         // host bookkeeping after one frame of the graph ran
 DcArgs plan_dc_args(lps_plan* P);
+bool plan_is_device_ptr(const void* p);
 
 }  // namespace lps

@@ -129,6 +129,7 @@ _SIGS = {
     "lps_lowrank_reproject": ([_VP, _VP, _VP, _VP, _VP], C.c_int),
     "lps_data_consistency": ([_VP, _VP, _VP, C.POINTER(C.c_double)], C.c_int),
     "lps_test_stall_wait": ([_VP, C.c_int], C.c_int),
+    "lps_batch_data_consistency": ([_VP, C.POINTER(_VP), C.POINTER(_VP), C.c_int, C.POINTER(C.c_float)], C.c_int),
     "lps_set_profiling": ([_VP, C.c_int], C.c_int),
     "lps_get_kernel_times": ([_VP, C.POINTER(KernelTimes)], C.c_int),
     "lps_shift_prior_columns": ([_VP, C.c_int], C.c_int),
@@ -545,6 +546,18 @@ class Batch:
 
     def reconstruct(self):
         _check(load().lps_batch_reconstruct(self.handle), "batch_reconstruct")
+
+    def data_consistency(self, Z, X, persistent: bool = False) -> float:
+        """Step (4) alone on every active member (Z[i], X[i] device images, None for inactive
+        members): each member's own kernel (graph branches) or one persistent launch over the
+        batch's descriptor table. Returns the launch's device time in ms."""
+        n = len(self.members)
+        zs = (_VP * n)(*[ptr(z) if z is not None else None for z in Z])
+        xs = (_VP * n)(*[ptr(x) if x is not None else None for x in X])
+        ms = C.c_float()
+        _check(load().lps_batch_data_consistency(self.handle, zs, xs, int(bool(persistent)), C.byref(ms)),
+               "batch_data_consistency")
+        return ms.value
 
     def close(self):
         if self.handle:

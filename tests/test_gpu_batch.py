@@ -204,3 +204,41 @@ def test_mix_member_full_size_matches_oracle(L, size):
     # a gross-error guard on top of the band: a few bits per ten thousand differ in practice
     assert int(diff.sum()) <= 5e-3 * max(1, int(ref.support.sum()))
     pl.close()
+
+
+def test_batch_data_consistency_member_kernels_and_persistent_form(L):
+    """Step (4) on every active member in one call: each member's own kernel (graph branches,
+    bitwise the member's lps_data_consistency) and the persistent launch over the descriptor
+    table (the runtime-sized body), both against the oracle to the operator bound; an inactive
+    member's output is left untouched."""
+    from tests.gpu_cases import rel
+    shapes = [(8, 32, 32, 2), (12, 24, 48, 3), (14, 16, 160, 3), (16, 16, 128, 2), (5, 16, 24, 1)]
+    cs = [make_case(nz, nx, ny, nc, seed=70 + k) for k, (nz, nx, ny, nc) in enumerate(shapes)]
+    B = L.Batch([L.params_init(nx=nx, ny=ny, nz=nz, ncoil=nc) for nz, nx, ny, nc in shapes])
+    for m, c in zip(B.members, cs):
+        m.set_coils(dev(c["coils"]))
+        m.set_mask(c["mask"])
+        m.set_data(dev(c["d"]))
+    rng = np.random.default_rng(8)
+    Z = [c64(rng.standard_normal((nz, nx, ny)) + 1j * rng.standard_normal((nz, nx, ny))) for nz, nx, ny, _ in shapes]
+    Zd = [dev(z) for z in Z]
+    B.set_active(4, False)
+    outs = {}
+    for pers in (False, True):
+        X = [torch.full((nz, nx, ny), 7.0 + 0j, dtype=torch.complex64, device="cuda") for nz, nx, ny, _ in shapes]
+        ms = B.data_consistency(Zd, X, persistent=pers)
+        assert ms > 0
+        outs[pers] = [x.cpu().numpy() for x in X]
+    for k, (nz, nx, ny, nc) in enumerate(shapes):
+        if k == 4:
+            assert np.all(outs[False][k] == 7.0) and np.all(outs[True][k] == 7.0)
+            continue
+        c = cs[k]
+        R = O.E(up(Z[k]), up(c["coils"]), c["mask"]) - up(c["d"])
+        ref = up(Z[k]) - O.EH(R, up(c["coils"]), c["mask"])
+        for pers in (False, True):
+            assert rel(outs[pers][k], ref) < 1e-5, (k, pers)
+        own = torch.empty((nz, nx, ny), dtype=torch.complex64, device="cuda")
+        L.data_consistency(B.members[k].handle, Zd[k], own)
+        assert np.array_equal(outs[False][k], own.cpu().numpy())
+    B.close()
