@@ -240,7 +240,12 @@ int lps_set_state(lps_plan* plan, const void* X, const void* S, const void* L_pr
 int lps_forward(lps_plan* plan, const void* image, void* kdata);
 int lps_adjoint(lps_plan* plan, const void* kdata, void* image);
 /* Step (4) alone on the resident data: X = Z - E^H(E Z - d); *resid_norm2 = ||E Z - d||^2
- * (nullable). */
+ * (nullable).
+ * The operators (these three, lps_casorati_gram, lps_lowrank_reproject, lps_adjoint_noalloc)
+ * carry no status from the device: a bounded wait that runs out in one of their kernels (it
+ * records the timeout only in a plan's frame path, or under lps_test_stall_wait) leaves the
+ * output incomplete while the call returns LPS_OK. The frame path (lps_reconstruct_frame,
+ * lps_iterate, batches, the server) reports it as LPS_ERR_TIMEOUT. */
 int lps_data_consistency(lps_plan* plan, const void* Z, void* X, double* resid_norm2);
 
 /* Casorati Gram G = M^H M, M = X - S: the matrix whose eigendecomposition gives the

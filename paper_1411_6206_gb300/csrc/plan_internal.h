@@ -48,9 +48,9 @@ struct lps_plan {
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // device state
   float2 *X = nullptr, *L = nullptr, *S = nullptr, *R = nullptr, *coils = nullptr;
-  __half2* coils_h = nullptr;
-  __half2* dhyb_h = nullptr;
-  int stall_polls = 0;          // lps_test_stall_wait: one-shot hook for the next operator call    // LPS_DATA_FP16: half-precision copy of the (rounded) hybrid samples   // LPS_COILS_FP16: half-precision copy of the (rounded) coil maps
+  __half2* coils_h = nullptr;   // LPS_COILS_FP16: half-precision copy of the (rounded) coil maps
+  __half2* dhyb_h = nullptr;    // LPS_DATA_FP16: half-precision copy of the (rounded) hybrid samples
+  int stall_polls = 0;          // lps_test_stall_wait: one-shot hook for the next operator call
   float2* S2 = nullptr;   // second sparse-part buffer: iteration k writes S_k while S_{k-1} is read
   float2 *dhyb = nullptr, *kstage = nullptr, *hscratch = nullptr, *istage = nullptr;
   float2 *W = nullptr, *V = nullptr, *gram_part = nullptr;
